@@ -1,0 +1,386 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 total viewshed (sDEM method, arXiv 2003.02200).
+
+One step = one whole total viewshed (every direction: skew, sweep, unskew) of
+the 2000 x 2000, 180-direction workload (the paper's DEM10m-2k scale: 10 m
+step, observers 1.5 m above ground), on a seeded fractal DEM that stands in for
+the paper's dataset.  The metric is G (POV x direction x target) evaluations
+per second, counted exactly from the row maps by the library; DEMs/s is
+reported beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With N > 1 (torchrun, one process per GPU) every rank runs an independent
+replica of the workload (the method has no data-path exchange on one DEM
+here); `value` is the evaluations of all ranks over the slowest rank's time.
+`--impl reference` times the oracle (the plain CPU implementation) on the
+host cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2003_02200_gb300 import terrain  # noqa: E402
+
+METRIC = "G POV*sector*target evals/s"
+UNIT = "Geval/s"
+KERNEL_SRC = os.path.join(ROOT, "paper_2003_02200_gb300", "csrc", "tvs_kernels.cu")
+PROFILES = os.path.join(ROOT, "profiles")
+# FP32 operations one evaluation needs (slope: subtract, multiply; compare; max)
+OPS_PER_EVAL = 4
+FP32_LANES_PER_SM = 128
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", default="tvs2000", choices=sorted(terrain.WORKLOADS))
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle baseline (profiling runs)")
+    ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end run")
+    return ap.parse_args(argv)
+
+
+# ------------------------------------------------------------ distributed --
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def dist_init(backend: str):
+    import torch.distributed as dist
+    world, rank, _ = dist_env()
+    if world > 1 and not dist.is_initialized():
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return dist if world > 1 else None
+
+
+def aggregate(units: float, seconds: float, dist=None, device=None):
+    """Whole-job totals of a replicated run: units summed over ranks, time = max over ranks."""
+    if dist is None:
+        return units, seconds
+    import torch
+    t = torch.tensor([units], dtype=torch.float64, device=device)
+    s = torch.tensor([seconds], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    dist.all_reduce(s, op=dist.ReduceOp.MAX)
+    return float(t.item()), float(s.item())
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+# ------------------------------------------------------------------ clocks --
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str | None):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="tvs_clocks_", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.gpu_id:
+            cmd += ["-i", self.gpu_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    smax.append(float(parts[2]))
+                    power.append(float(parts[3]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "power_w_max": max(power),
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- helpers --
+
+def workload(name: str) -> dict:
+    return dict(terrain.WORKLOADS[name])
+
+
+def config_of(name: str, w: dict, E: int, world: int) -> dict:
+    rng = w["max_range"] if w["max_range"] > 0 else None
+    return {"workload": f"{name}: {w['rows']}x{w['cols']} DEM, {w['step']:g} m step, observer {w['h0']:g} m, "
+                        f"{w['n']} directions, range {'unlimited' if rng is None else f'{rng:g} m'}",
+            "rows": w["rows"], "cols": w["cols"], "n_sectors": w["n"], "step_m": w["step"],
+            "obs_height_m": w["h0"], "max_range_m": rng, "povs": w["rows"] * w["cols"],
+            "evals_per_dem": E, "l2": "flushed between steps (256 MiB write, outside the step events)",
+            "parallelism": "replicas" if world > 1 else "single"}
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def kernel_hash() -> str:
+    with open(KERNEL_SRC, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic(name: str) -> float | None:
+    """DRAM bytes per sweep launch from a committed ncu capture, if it was
+    taken on the current kernel source (else None)."""
+    path = os.path.join(PROFILES, f"sweep_{name}_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_sha256_16") != kernel_hash():
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def oracle_sample(w: dict, dem, seconds: float, seed: int = 7) -> dict:
+    """Time the oracle on the host cores on random cells of the workload until
+    about `seconds` of wall time is spent; return seconds per cell."""
+    import numpy as np
+
+    import oracle
+    rng = np.random.default_rng(seed)
+    cells_total = w["rows"] * w["cols"]
+    info = {}
+    done, spent, batch = 0, 0.0, 16
+    while spent < seconds and done < cells_total:
+        cells = rng.choice(cells_total, size=min(batch, cells_total), replace=False)
+        t0 = time.perf_counter()
+        oracle.total_viewshed(dem, w["step"], w["h0"], w["n"], w["max_range"], prec=64, cells=cells, info=info)
+        dt = time.perf_counter() - t0
+        done += len(cells)
+        spent += dt
+        per = dt / len(cells)
+        batch = max(16, min(4096, int((seconds - spent) / max(per, 1e-9) * 0.9)))
+    return {"sec_per_cell": spent / done, "cells": done, "threads": info.get("threads", 1),
+            "seconds": spent}
+
+
+# ------------------------------------------------------------------- ours --
+
+def run_ours(args) -> int:
+    import numpy as np
+    import torch
+
+    import paper_2003_02200_gb300 as tvs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    w = workload(args.workload)
+    dem_np = terrain.workload_dem(args.workload)
+    E = tvs.count_evals(w["rows"], w["cols"], w["n"], w["step"], w["max_range"])
+    ctx = tvs.Context(local)
+    dem = torch.from_numpy(dem_np).to(device)
+    out = torch.empty_like(dem)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+    stream = torch.cuda.current_stream(device)
+
+    def step():
+        ctx.total_viewshed_device(dem, w["step"], w["h0"], w["n"], w["max_range"], out=out, stream=stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(device)
+    props = torch.cuda.get_device_properties(device)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    sampler.start()
+    ctx.profile(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    for k in range(args.steps):
+        flush.zero_()
+        starts[k].record(stream)
+        step()
+        ends[k].record(stream)
+    torch.cuda.synchronize(device)
+    barrier(dist, device)
+    clocks = sampler.stop()
+    stats = ctx.profile_read()
+    ctx.profile(False)
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    local_s = sum(step_ms) / 1e3
+    total_evals, max_s = aggregate(float(E) * args.steps, local_s, dist, device)
+    total_steps, _ = aggregate(float(args.steps), local_s, dist, device)
+
+    # end to end through the C ABI with host buffers (pinned): H2D of the DEM
+    # and D2H of the map inside every step
+    e2e_steps = args.e2e_steps or args.steps
+    h_dem = torch.from_numpy(dem_np).pin_memory().numpy()
+    h_out = torch.empty(dem_np.shape, dtype=torch.float32).pin_memory().numpy()
+    ctx.total_viewshed(h_dem, w["step"], w["h0"], w["n"], w["max_range"], out=h_out)
+    barrier(dist, device)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ctx.total_viewshed(h_dem, w["step"], w["h0"], w["n"], w["max_range"], out=h_out)
+    e2e_local = time.perf_counter() - t0
+    e2e_evals, e2e_max = aggregate(float(E) * e2e_steps, e2e_local, dist, device)
+    ok_e2e = bool(np.all(np.isfinite(h_out)))
+
+    sweep = stats.get("sweep", {})
+    peaks = measured_peaks()
+    sm_max_mhz = peaks.get("sm_max_mhz") or (getattr(props, "clock_rate", 0) / 1e3) or 2070.0
+    peak_evals = props.multi_processor_count * FP32_LANES_PER_SM * sm_max_mhz * 1e6 / OPS_PER_EVAL
+    achieved = sweep["units"] / (sweep["total_ms"] / 1e3) if sweep.get("total_ms") else 0.0
+    traffic = profiled_traffic(args.workload)
+    launches = int(sum(v["launches"] for v in stats.values()))
+    kernels = {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / max(v["launches"], 1),
+                   "share": v["total_ms"] / max(sum(s["total_ms"] for s in stats.values()), 1e-12),
+                   "rate": (v["units"] / (v["total_ms"] / 1e3) / 1e9) if v["total_ms"] else None,
+                   "rate_unit": "G" + v["unit"] + "/s"}
+               for k, v in stats.items() if v["launches"]}
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": total_evals / max_s / 1e9, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic: seeded spectral-fractal DEM standing in for the paper's DEM10m datasets",
+        "config": config_of(args.workload, w, E, world),
+        "dems_per_s": total_steps / max_s,
+        "roofline": {"bound": "alu", "achieved": achieved / 1e9, "peak": peak_evals / 1e9, "unit": UNIT,
+                     "frac": achieved / peak_evals, "traffic": traffic,
+                     "kernel": "sweep", "peak_basis": f"{props.multi_processor_count} SMs x "
+                     f"{FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:g} MHz / {OPS_PER_EVAL} ops per eval "
+                     "(MEASURED_PEAKS sm_max_mhz)"},
+        "kernels": kernels,
+        "e2e": {"value": e2e_evals / e2e_max / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(dem_np.nbytes),
+                "d2h_bytes_per_step": int(dem_np.nbytes), "api": "tvs_total_viewshed (host buffers, pinned)",
+                "ms_per_step": e2e_local / e2e_steps * 1e3, "finite": ok_e2e},
+        "gpu_launches": launches,
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        s = oracle_sample(w, dem_np, args.cpu_seconds)
+        full_s = s["sec_per_cell"] * w["rows"] * w["cols"]
+        line["cpu_baseline"] = {"value": E / full_s / 1e9, "unit": UNIT, "cores": s["threads"], "kind": "oracle",
+                                "sample": f"{s['cells']} random cells of the workload (all {w['n']} directions "
+                                          f"each, FP64), {s['seconds']:.1f} s, extrapolated by cell count"}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+# -------------------------------------------------------------- reference --
+
+def run_reference(args) -> int:
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+
+    import oracle
+    w = workload(args.workload)
+    dem = terrain.workload_dem(args.workload)
+    E = oracle.count_evals(w["rows"], w["cols"], w["n"], w["step"], w["max_range"])
+    per_step = max(4.0, 150.0 / max(args.steps + args.warmup, 1))
+    rng = np.random.default_rng(11)
+    cells_total = w["rows"] * w["cols"]
+    info = {}
+    probe = rng.choice(cells_total, size=8, replace=False)
+    t0 = time.perf_counter()
+    oracle.total_viewshed(dem, w["step"], w["h0"], w["n"], w["max_range"], prec=64, cells=probe, info=info)
+    per_cell = (time.perf_counter() - t0) / len(probe)
+    n_cells = int(max(8, min(cells_total, per_step / max(per_cell, 1e-9))))
+    times = []
+    for k in range(args.warmup + args.steps):
+        cells = rng.choice(cells_total, size=n_cells, replace=False)
+        t0 = time.perf_counter()
+        oracle.total_viewshed(dem, w["step"], w["h0"], w["n"], w["max_range"], prec=64, cells=cells, info=info)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+    full_s = statistics.mean(times) / n_cells * cells_total
+    value = E / full_s / 1e9
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": full_s * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: seeded spectral-fractal DEM standing in for the paper's DEM10m datasets",
+        "config": config_of(args.workload, w, E, world), "dems_per_s": 1.0 / full_s,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": info.get("threads", 1), "kind": "oracle",
+                         "sample": f"each step: {n_cells} random cells (all {w['n']} directions each, FP64), "
+                                   "extrapolated to the whole DEM by cell count"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None) -> int:
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,150 @@
+/*
+ * tvs.h -- C ABI of the GB300 (sm_103a) total-viewshed library, an
+ * implementation of the sDEM method (skewed Digital Elevation Model) of
+ * Sanchez-Fernandez, Romero, Bandera and Tabik, arXiv 2003.02200.
+ *
+ * What a call computes (section 3 and 4.1 of the paper):
+ *   every DEM cell is a point of view (POV) lifted by the observer height h0;
+ *   for each of n directions theta_k = k*pi/n the DEM is relocated into a
+ *   skewed layout in which every sampled line of sight is one contiguous row
+ *   (Kernel-1, Alg. 6); every sample of every row is then a virtual POV that
+ *   walks its row forward and backward, keeping the running maximum elevation
+ *   angle (Kernel-2, Alg. 7 and 8), and the measure of its visible ring
+ *   sectors is blended back onto the DEM cells (Kernel-3, Alg. 9) and summed
+ *   over directions.  Result: the visible area of every cell, in the square of
+ *   the grid-step unit (m^2 for metres), scaled by the Pappus factor pi/(2n)
+ *   (the pi/360 of the ring-sector area equation for n = 180).
+ *
+ * Conventions shared by every entry point:
+ *   - DEM: rows x cols float32, row-major, rows north to south, columns west
+ *     to east (section 4.1); rows >= 2 and cols >= 2.
+ *   - n_sectors counts directions over 180 degrees (each direction is walked
+ *     both ways, so 180 means one-degree sectors).
+ *   - max_range_m <= 0 or +inf means unlimited; otherwise only targets within
+ *     floor(max_range_m / (step_m * sqrt(1 + t^2))) steps count.
+ *   - Every function returns TVS_OK (0) or a negative TVS_ERR_* code; the
+ *     message of the last failure on the calling thread is tvs_last_error().
+ *   - A handle is not thread-safe: one call at a time per handle.  Calls of
+ *     one handle on different CUDA streams must not overlap on the GPU (they
+ *     share the handle's device scratch).
+ */
+#ifndef TVS_H
+#define TVS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define TVS_ABI_VERSION 1
+
+#define TVS_OK            0
+#define TVS_ERR_ARG     (-1)  /* bad pointer, size, step, height, count or non-finite value */
+#define TVS_ERR_OOM     (-2)  /* the work does not fit the HBM budget, or cudaMalloc failed */
+#define TVS_ERR_CUDA    (-3)  /* CUDA runtime error (no device, launch failure, ...) */
+#define TVS_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define TVS_ERR_STATE   (-5)  /* handle in a state that cannot serve the call */
+
+typedef struct tvs_ctx* tvs_handle;
+
+/* One direction k of n (section 4.1 step 1; Alg. 6 covers 0..45 degrees and the
+ * other eighths use a D4 view of the DEM).  Host-side description. */
+typedef struct {
+    int32_t  frame;   /* 0 identity, 1 transpose, 2 transpose + mirrored columns, 3 mirrored rows */
+    int32_t  m;       /* reduced angle alpha = pi*m/(2n), 0 <= alpha <= pi/4 */
+    int32_t  H, W;    /* shape of the view; W is the walk axis */
+    int32_t  D;       /* dest(W-1): shift of the last column, in rows */
+    int32_t  R;       /* rows of the skewed layout, H + D */
+    uint64_t t_fx;    /* llround(tan(alpha) * 2^32) */
+    double   t;       /* t_fx * 2^-32 */
+    double   g;       /* 1 + t^2, the (1/cos s)^2 factor of Alg. 7 */
+    int64_t  K;       /* walk limit in steps (INT64_MAX when unlimited) */
+} tvs_direction_info;
+
+/* Per-kernel timing kept while profiling is on (CUDA events on the launch stream). */
+typedef struct {
+    char     name[32];
+    int64_t  launches;
+    double   total_ms;
+    double   units;        /* algorithmic units summed over launches (see unit) */
+    char     unit[16];     /* "evals" for the sweep, "bytes" for the memory kernels */
+} tvs_kernel_stats;
+
+/* ABI version of the loaded library (TVS_ABI_VERSION).  Host only. */
+int tvs_abi_version(void);
+
+/* Create a handle bound to CUDA device `device`.  hbm_budget_bytes caps the
+ * device scratch the handle may hold (0 = min(16 GiB, 60% of free memory)).
+ * The handle owns its scratch; the caller owns every input and output.
+ * Errors: TVS_ERR_ARG (out == NULL, bad device), TVS_ERR_CUDA (no usable GPU). */
+int tvs_create(tvs_handle* out, int device, size_t hbm_budget_bytes);
+
+/* Release the handle and its device scratch.  NULL is accepted. */
+void tvs_destroy(tvs_handle h);
+
+/* Message of the last failing call made by this thread ("" if none).  The
+ * pointer stays valid until the thread's next failing call. */
+const char* tvs_last_error(tvs_handle h);
+
+/* Total viewshed from HOST memory (Alg. 4, computed the sDEM way of section 4).
+ * dem: rows*cols float32 elevations (metres), row-major, finite.
+ * step_m > 0: grid step; obs_height_m: h0 >= 0 (finite); n_sectors >= 1.
+ * out: rows*cols float32, visible area of each cell in m^2, laid out like dem.
+ * Synchronous: on return `out` holds the result.  The library copies dem to
+ * the device and out back inside the call.
+ * Errors: TVS_ERR_ARG, TVS_ERR_OOM, TVS_ERR_CUDA. */
+int tvs_total_viewshed(tvs_handle h, const float* dem, int rows, int cols, double step_m,
+                       double obs_height_m, int n_sectors, double max_range_m, float* out);
+
+/* Same computation on DEVICE memory, ordered on `cuda_stream` (a cudaStream_t,
+ * NULL = legacy default stream).  d_dem and d_out are device pointers of
+ * rows*cols float32 on the handle's device (they may not overlap).  The call
+ * returns once the work is enqueued; d_out is complete when the stream reaches
+ * that point.  Elevations are not scanned for NaN/inf on this path (the result
+ * of a non-finite DEM is unspecified).  Scratch is (re)allocated inside the call
+ * when the job needs more than the handle holds; that allocation synchronises
+ * the device once.  Errors: TVS_ERR_ARG, TVS_ERR_OOM, TVS_ERR_CUDA. */
+int tvs_total_viewshed_device(tvs_handle h, const float* d_dem, int rows, int cols, double step_m,
+                              double obs_height_m, int n_sectors, double max_range_m, float* d_out,
+                              void* cuda_stream);
+
+/* Direction table entry k of n for a rows x cols DEM (host only, no GPU). */
+int tvs_direction(int n_sectors, int k, int rows, int cols, double step_m, double max_range_m,
+                  tvs_direction_info* info);
+
+/* Work count of a job: the number of (virtual POV, direction, target) visits,
+ * sum over directions, skewed rows and their usable samples of
+ * min(L_fwd, K) + min(L_bwd, K).  Host only; returns a negative code on bad args. */
+int64_t tvs_count_evals(int rows, int cols, int n_sectors, double step_m, double max_range_m);
+
+/* Row map of direction k computed by the device kernel that the sweep uses,
+ * copied to host arrays: dest[j], frac[j] for j < W (integer row shift and
+ * 32-bit fraction of j*t), jlo[p], jhi[p] for p < R (usable columns of skewed
+ * row p, whose base row is p - D; jlo > jhi when empty) and *R.  dest and frac
+ * need max(rows, cols) entries, jlo and jhi rows + cols entries.  Synchronous. */
+int tvs_debug_rowmap(tvs_handle h, int rows, int cols, int n_sectors, int k, int32_t* dest,
+                     uint32_t* frac, int32_t* jlo, int32_t* jhi, int32_t* R);
+
+/* Skew + sweep of a single direction k on a HOST DEM, returning the per-sample
+ * visible measure cv (forward + backward, squared steps, an exact integer) of
+ * every skewed row: cv[p * W + j] for p < R, j < W, -1 where the sample is not
+ * usable.  cv needs (rows + cols) * max(rows, cols) entries.  Synchronous. */
+int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, double step_m,
+                           double obs_height_m, int n_sectors, double max_range_m, int k,
+                           int32_t* cv, int32_t* R, int32_t* W);
+
+/* Turn per-kernel timing on (1) or off (0); turning it on clears the counters.
+ * While on, each launch is bracketed by CUDA events on its stream. */
+int tvs_profile_enable(tvs_handle h, int on);
+
+/* Read the per-kernel counters (synchronises the recorded events).  Writes up
+ * to max entries to stats and their number to *count. */
+int tvs_profile_read(tvs_handle h, tvs_kernel_stats* stats, int max, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TVS_H */

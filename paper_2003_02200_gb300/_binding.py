@@ -1,0 +1,219 @@
+"""ctypes binding of libtvs.so (include/tvs.h).  Argument marshalling only:
+every step of the computation runs in the library's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import re
+import threading
+
+import numpy as np
+
+from . import _build
+
+_lock = threading.Lock()
+_lib = None
+
+TVS_OK = 0
+TVS_ERR_ARG = -1
+TVS_ERR_OOM = -2
+TVS_ERR_CUDA = -3
+TVS_ERR_TIMEOUT = -4
+TVS_ERR_STATE = -5
+_ERRNAMES = {-1: "TVS_ERR_ARG", -2: "TVS_ERR_OOM", -3: "TVS_ERR_CUDA", -4: "TVS_ERR_TIMEOUT",
+             -5: "TVS_ERR_STATE"}
+
+
+class TvsError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class DirectionInfo(C.Structure):
+    _fields_ = [("frame", C.c_int32), ("m", C.c_int32), ("H", C.c_int32), ("W", C.c_int32),
+                ("D", C.c_int32), ("R", C.c_int32), ("t_fx", C.c_uint64), ("t", C.c_double),
+                ("g", C.c_double), ("K", C.c_int64)]
+
+
+class KernelStats(C.Structure):
+    _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
+                ("units", C.c_double), ("unit", C.c_char * 16)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def declared_functions() -> list[str]:
+    """Names of the functions include/tvs.h declares."""
+    with open(os.path.join(_build.INCLUDE, "tvs.h")) as f:
+        text = f.read()
+    return re.findall(r"^\s*(?:const\s+)?[a-z_0-9]+\**\s+\**\s*(tvs_[a-z_0-9]+)\s*\(", text, re.M)
+
+
+def load(build_if_missing: bool = True) -> C.CDLL:
+    """Load libtvs.so (building it first if allowed).  Raises if unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if not os.path.exists(path) or not _build.up_to_date():
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is missing or stale; build it with "
+                                   "paper_2003_02200_gb300.build()")
+            _build.build()
+        lib = C.CDLL(path)
+        vp, i32p, i64p = C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int64)
+        sig = {
+            "tvs_abi_version": ([], C.c_int),
+            "tvs_create": ([C.POINTER(vp), C.c_int, C.c_size_t], C.c_int),
+            "tvs_destroy": ([vp], None),
+            "tvs_last_error": ([vp], C.c_char_p),
+            "tvs_total_viewshed": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                    C.c_double, vp], C.c_int),
+            "tvs_total_viewshed_device": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                           C.c_double, vp, vp], C.c_int),
+            "tvs_direction": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                               C.POINTER(DirectionInfo)], C.c_int),
+            "tvs_count_evals": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double], C.c_int64),
+            "tvs_debug_rowmap": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, i32p], C.c_int),
+            "tvs_debug_direction_cv": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                        C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
+            "tvs_profile_enable": ([vp, C.c_int], C.c_int),
+            "tvs_profile_read": ([vp, C.POINTER(KernelStats), C.c_int, C.POINTER(C.c_int)], C.c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _ = i64p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int) -> None:
+    if rc != TVS_OK:
+        raise TvsError(rc, load().tvs_last_error(None).decode())
+
+
+def _dem(dem) -> np.ndarray:
+    a = np.ascontiguousarray(dem, dtype=np.float32)
+    if a.ndim != 2:
+        raise ValueError("dem must be a 2-D array")
+    return a
+
+
+def direction(n_sectors: int, k: int, rows: int, cols: int, step_m: float = 1.0,
+              max_range_m: float = 0.0) -> dict:
+    info = DirectionInfo()
+    _check(load().tvs_direction(n_sectors, k, rows, cols, step_m, max_range_m, C.byref(info)))
+    return {f: getattr(info, f) for f, _ in DirectionInfo._fields_}
+
+
+def count_evals(rows: int, cols: int, n_sectors: int, step_m: float = 1.0, max_range_m: float = 0.0) -> int:
+    E = load().tvs_count_evals(rows, cols, n_sectors, step_m, max_range_m)
+    if E < 0:
+        _check(int(E))
+    return int(E)
+
+
+class Context:
+    """A library handle bound to one CUDA device (tvs_create / tvs_destroy)."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0):
+        self._lib = load()
+        h = C.c_void_p()
+        _check(self._lib.tvs_create(C.byref(h), device, hbm_budget_bytes))
+        self._h = h
+        self.device = device
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.tvs_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if not self._h:
+            raise RuntimeError("context is closed")
+        return self._h
+
+    def total_viewshed(self, dem, step_m: float, obs_height_m: float, n_sectors: int = 180,
+                       max_range_m: float = 0.0, out: np.ndarray | None = None) -> np.ndarray:
+        """tvs_total_viewshed on host arrays: returns the visible area (m^2) per cell."""
+        a = _dem(dem)
+        if out is None:
+            out = np.empty_like(a)
+        if out.shape != a.shape or out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float32 array shaped like dem")
+        _check(self._lib.tvs_total_viewshed(self.handle, a.ctypes.data, a.shape[0], a.shape[1], step_m,
+                                            obs_height_m, n_sectors, max_range_m, out.ctypes.data))
+        return out
+
+    def total_viewshed_device(self, dem, step_m: float, obs_height_m: float, n_sectors: int = 180,
+                              max_range_m: float = 0.0, out=None, stream=None):
+        """tvs_total_viewshed_device on torch CUDA tensors, ordered on `stream`
+        (default: torch's current stream).  Returns `out`."""
+        import torch
+        if not (isinstance(dem, torch.Tensor) and dem.is_cuda and dem.dtype == torch.float32
+                and dem.dim() == 2 and dem.is_contiguous()):
+            raise ValueError("dem must be a contiguous 2-D float32 CUDA tensor")
+        if out is None:
+            out = torch.empty_like(dem)
+        if out.shape != dem.shape or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+            raise ValueError("out must be a contiguous float32 CUDA tensor shaped like dem")
+        if stream is None:
+            stream = torch.cuda.current_stream(dem.device)
+        _check(self._lib.tvs_total_viewshed_device(self.handle, dem.data_ptr(), dem.shape[0], dem.shape[1],
+                                                   step_m, obs_height_m, n_sectors, max_range_m,
+                                                   out.data_ptr(), stream.cuda_stream))
+        return out
+
+    def debug_rowmap(self, rows: int, cols: int, n_sectors: int, k: int) -> dict:
+        big = max(rows, cols)
+        dest = np.empty(big, np.int32)
+        frac = np.empty(big, np.uint32)
+        jlo = np.empty(rows + cols, np.int32)
+        jhi = np.empty(rows + cols, np.int32)
+        R = C.c_int32(0)
+        _check(self._lib.tvs_debug_rowmap(self.handle, rows, cols, n_sectors, k, dest.ctypes.data,
+                                          frac.ctypes.data, jlo.ctypes.data, jhi.ctypes.data, C.byref(R)))
+        W = direction(n_sectors, k, rows, cols)["W"]
+        return dict(dest=dest[:W], frac=frac[:W], jlo=jlo[: R.value], jhi=jhi[: R.value], R=R.value)
+
+    def debug_direction_cv(self, dem, step_m: float, obs_height_m: float, n_sectors: int,
+                           max_range_m: float, k: int) -> np.ndarray:
+        a = _dem(dem)
+        rows, cols = a.shape
+        buf = np.empty((rows + cols) * max(rows, cols), np.int32)
+        R = C.c_int32(0)
+        W = C.c_int32(0)
+        _check(self._lib.tvs_debug_direction_cv(self.handle, a.ctypes.data, rows, cols, step_m, obs_height_m,
+                                                n_sectors, max_range_m, k, buf.ctypes.data, C.byref(R),
+                                                C.byref(W)))
+        return buf[: R.value * W.value].reshape(R.value, W.value)
+
+    def profile(self, on: bool) -> None:
+        _check(self._lib.tvs_profile_enable(self.handle, 1 if on else 0))
+
+    def profile_read(self) -> dict:
+        arr = (KernelStats * 8)()
+        cnt = C.c_int(0)
+        _check(self._lib.tvs_profile_read(self.handle, arr, 8, C.byref(cnt)))
+        return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
+                                           units=arr[i].units, unit=arr[i].unit.decode())
+                for i in range(cnt.value)}

@@ -1,0 +1,604 @@
+// tvs_kernels.cu -- sm_103a kernels of the sDEM total viewshed.
+//
+//   rowmap : usable column range [jlo, jhi] of every skewed row (section 4.1
+//            step 1(b): the limits of the skewed structure).
+//   skew   : DEM -> skewed layout, one writer per sample (Kernel-1, Alg. 6,
+//            written as a gather instead of the paper's two-way scatter).
+//   sweep  : every usable sample of every skewed row walks its row forward and
+//            backward (Kernel-2, Alg. 7 and 8); the hot loop.
+//   unskew : blends the per-sample measures back onto DEM cells and sums the
+//            directions (Kernel-3, Alg. 9), with the Pappus / step^2 scale of
+//            Alg. 1 applied once at the end.
+#include "tvs_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+namespace tvs {
+
+namespace {
+
+__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+
+__device__ __forceinline__ int dest_of(unsigned long long t_fx, int j)
+{
+    return (int)(((unsigned long long)j * t_fx) >> 32);
+}
+
+// ---------------------------------------------------------------- rowmap --
+// Skewed row p holds the line with base row b = p - D: sample j sits at view
+// row b + j*t (t = t_fx / 2^32) and is usable iff 0 <= b + j*t <= H - 1,
+// i.e. j*t_fx >= -b*2^32 and j*t_fx <= (H-1-b)*2^32 (exact integers).
+__global__ void rowmap_kernel(const DirDev* __restrict__ dirs, int* __restrict__ rowlo,
+                              int* __restrict__ rowhi)
+{
+    const DirDev d = dirs[blockIdx.y];
+    for (int p = blockIdx.x * blockDim.x + threadIdx.x; p < d.R; p += gridDim.x * blockDim.x) {
+        const long long b = (long long)p - d.D;
+        long long lo, hi;
+        if (d.t_fx == 0ull) {
+            lo = 0;
+            hi = (b >= 0 && b <= d.H - 1) ? d.W - 1 : -1;
+        } else {
+            lo = 0;
+            if (b < 0) {
+                const unsigned long long num = (unsigned long long)(-b) << 32;
+                lo = (long long)((num + d.t_fx - 1ull) / d.t_fx);
+            }
+            const long long top = (long long)d.H - 1 - b;
+            hi = top < 0 ? -1 : (long long)(((unsigned long long)top << 32) / d.t_fx);
+            if (hi > d.W - 1) hi = d.W - 1;
+        }
+        if (lo > hi) { lo = 0; hi = -1; }
+        rowlo[d.row_off + p] = (int)lo;
+        rowhi[d.row_off + p] = (int)hi;
+    }
+}
+
+__global__ void colmap_kernel(const DirDev* __restrict__ dir, int* __restrict__ dest,
+                              unsigned* __restrict__ frac)
+{
+    const DirDev d = *dir;
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < d.W; j += gridDim.x * blockDim.x) {
+        const unsigned long long y = (unsigned long long)j * d.t_fx;
+        dest[j] = (int)(y >> 32);
+        frac[j] = (unsigned)(y & 0xFFFFFFFFull);
+    }
+}
+
+// ------------------------------------------------------------------ skew --
+// CTA = one SKEW_TP x SKEW_TJ tile of one direction's skewed slab.  The view
+// rows the tile blends (at most SKEW_TP + SKEW_TJ + 1 of them) are staged in
+// shared memory: for the identity / row-mirrored views they are DEM row
+// segments (coalesced along the row), for the transposed views DEM column
+// segments are read along DEM rows (coalesced) and transposed on the way into
+// shared memory (row pitch SKEW_TJ + 1: no bank conflicts either way).
+constexpr int SKEW_ROWS = SKEW_TP + SKEW_TJ + 3;
+constexpr int SKEW_PITCH = SKEW_TJ + 1;
+
+__global__ void __launch_bounds__(256) skew_kernel(const float* __restrict__ dem, int cols,
+                                                   const DirDev* __restrict__ dirs,
+                                                   float* __restrict__ sdem)
+{
+    __shared__ float S[SKEW_ROWS * SKEW_PITCH];
+    const DirDev d = dirs[blockIdx.y];
+    const int tiles_j = (d.W + SKEW_TJ - 1) / SKEW_TJ;
+    const int tiles_p = (d.R + SKEW_TP - 1) / SKEW_TP;
+    if ((int)blockIdx.x >= tiles_j * tiles_p) return;
+    const int pt = blockIdx.x / tiles_j, jt = blockIdx.x - pt * tiles_j;
+    const int p0 = pt * SKEW_TP, j0 = jt * SKEW_TJ;
+    const int p1 = min(p0 + SKEW_TP, d.R) - 1;
+    const int j1 = min(j0 + SKEW_TJ, d.W) - 1;
+    const int nj = j1 - j0 + 1;
+    int amin = p0 - d.D + dest_of(d.t_fx, j0);
+    int amax = p1 - d.D + dest_of(d.t_fx, j1) + 1;
+    amin = max(amin, 0);
+    amax = min(amax, d.H - 1);
+    if (amin > amax) return;
+    const int na = amax - amin + 1;
+
+    if (d.frame == 0 || d.frame == 3) {
+        const bool vec = ((cols & 3) == 0) && nj == SKEW_TJ;
+        if (vec) {
+            // 8 lanes x 16 B per 128 B row segment, 4 row segments per warp instruction
+            for (int idx = threadIdx.x; idx < na * (SKEW_TJ / 4); idx += blockDim.x) {
+                const int r = idx / (SKEW_TJ / 4), c4 = (idx - r * (SKEW_TJ / 4)) * 4;
+                const int a = amin + r;
+                const int drow = d.frame == 0 ? a : d.H - 1 - a;
+                const float4 v = *reinterpret_cast<const float4*>(dem + (long long)drow * cols + j0 + c4);
+                float* s = S + r * SKEW_PITCH + c4;
+                s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+            }
+        } else {
+            for (int idx = threadIdx.x; idx < na * SKEW_TJ; idx += blockDim.x) {
+                const int r = idx / SKEW_TJ, c = idx - r * SKEW_TJ;
+                const int a = amin + r;
+                const int drow = d.frame == 0 ? a : d.H - 1 - a;
+                if (c < nj) S[r * SKEW_PITCH + c] = dem[(long long)drow * cols + j0 + c];
+            }
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < nj * na; idx += blockDim.x) {
+            const int c = idx / na, r = idx - c * na;
+            const int j = j0 + c;
+            const int drow = d.frame == 1 ? j : d.W - 1 - j;
+            S[r * SKEW_PITCH + c] = dem[(long long)drow * cols + amin + r];
+        }
+    }
+    __syncthreads();
+
+    const int c = threadIdx.x % SKEW_TJ;
+    const int j = j0 + c;
+    if (j > j1) return;
+    const unsigned long long y = (unsigned long long)j * d.t_fx;
+    const int dest = (int)(y >> 32);
+    const unsigned fr = (unsigned)(y & 0xFFFFFFFFull);
+    // Blend weights of Alg. 6 in single precision: r = frac * 2^-32.
+    const float r = __fmul_rn(__uint2float_rn(fr), 0x1p-32f);
+    const float wa = __fsub_rn(1.0f, r);
+    float* out = sdem + d.slab + j;
+    for (int pp = threadIdx.x / SKEW_TJ; pp < SKEW_TP; pp += blockDim.x / SKEW_TJ) {
+        const int p = p0 + pp;
+        if (p > p1) break;
+        const int a = p - d.D + dest;
+        const bool ok = a >= 0 && (fr == 0u ? a <= d.H - 1 : a + 1 <= d.H - 1);
+        if (!ok) continue;
+        const float va = S[(a - amin) * SKEW_PITCH + c];
+        float z = va;
+        if (fr != 0u) {
+            const float vb = S[(a + 1 - amin) * SKEW_PITCH + c];
+            z = __fadd_rn(__fmul_rn(wa, va), __fmul_rn(r, vb));
+        }
+        out[(long long)p * d.Wp] = z;
+    }
+}
+
+// ----------------------------------------------------------------- sweep --
+struct SweepParams {
+    const DirDev* dirs;
+    const int* item_start;
+    const float* sdem;
+    const int* rowlo;
+    const int* rowhi;
+    int* cv_fwd;       // forward measure of every sample (slab layout)
+    int* cv_bwd;       // backward measure of every sample (slab layout)
+    unsigned* counter;
+    int ndir;
+    int total_items;
+    int inv_len;     // entries of the duplicated 1/d table (float2 each, multiple of 2)
+    int istart_len;  // ints of the item-start table (multiple of 4)
+    int half;        // floats of one staged row (multiple of 4)
+    float h0;
+};
+
+__device__ __forceinline__ float fset_gt(float a, float b)
+{
+    // 1.0f if a > b (strict; false for NaN), else 0.0f
+    float v;
+    asm("set.gt.f32.f32 %0, %1, %2;" : "=f"(v) : "f"(a), "f"(b));
+    return v;
+}
+
+// U steps of one lane's P POVs.  POV q at step u (distance d = e + 1 + u)
+// sees target w[q + u + 1]; its slope is (target - h_q) * (1/d) in single
+// precision, it is visible iff that slope is strictly above the running
+// maximum M_q, and a visible target adds 2d + 1 to the POV's measure.  Two
+// POVs share one packed multiply and one packed accumulate; the comparison and
+// the maximum are scalar.  `cpair` holds 2d + 1 of the first step (or zero for
+// steps a range-limited walk must not count, see sweep_lane).
+template <int P, int U, bool MASKED>
+__device__ __forceinline__ void sweep_block(const float* w, const float2* iv2, const float* h, float* M,
+                                            float2* acc2, float cb, int nvalid)
+{
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        float c = cb + 2.0f * (float)u;
+        if (MASKED) c = u < nvalid ? c : 0.0f;
+        const float2 cpair = make_float2(c, c);
+#pragma unroll
+        for (int q = 0; q < P; q += 2) {
+            const float2 d = make_float2(__fsub_rn(w[q + u + 1], h[q]), __fsub_rn(w[q + u + 2], h[q + 1]));
+            const float2 t = __fmul2_rn(d, iv2[u]);
+            const float2 v = make_float2(fset_gt(t.x, M[q]), fset_gt(t.y, M[q + 1]));
+            acc2[q / 2] = __ffma2_rn(v, cpair, acc2[q / 2]);
+            M[q] = fmaxf(M[q], t.x);
+            M[q + 1] = fmaxf(M[q + 1], t.y);
+        }
+    }
+}
+
+// One lane of a warp item: forward walks of two groups of P consecutive POVs
+// of the staged row F (group s and its mirror G-1-s, so that every lane walks
+// about one row length in total).  F holds the row (or the reversed row for
+// backward walks) with -inf at its last sample and after it: the last target
+// of a walk never adds area (its segment closes there), so it may be a
+// sentinel that is never visible.  A walk's measure is
+// cv = 1 + sum_{d=1}^{n-1} v_d (2d + 1) for n >= 1 targets, which is Alg. 8's
+// sum of d^2 - open^2 over its closed segments plus the segment still open at
+// the end (closed at the last target).
+template <int P, int U>
+__device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const float2* __restrict__ inv2,
+                                           int* __restrict__ cvrow, int L, int slot, int K, float h0, bool rev)
+{
+    const float NEG = neg_inf();
+    const int G = (L + P - 1) / P;
+    const int nslots = (G + 1) / 2;
+    if (slot >= nslots) return;
+    const int gsel[2] = {slot, G - 1 - slot};
+    const int ng = gsel[0] == gsel[1] ? 1 : 2;
+    const int klim = K - 1;          // last target distance that still adds area
+
+    float h[P], M[P];
+    float2 acc2[P / 2];
+    float first[P];                  // measure sums of group 0 once group 1 starts
+    int x0 = gsel[0] * P;
+    int rowlim = L - 2 - x0;         // last target adding area, POV q = 0
+    int dlim = min(klim, rowlim);
+    bool klimited = klim < rowlim;
+    bool second = false;
+#pragma unroll
+    for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; first[q] = 0.f; }
+#pragma unroll
+    for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+    int e = 0;
+    for (;;) {
+        if (e >= dlim) {
+            if (second || ng == 1) break;
+#pragma unroll
+            for (int q = 0; q < P; q += 2) { first[q] = acc2[q / 2].x; first[q + 1] = acc2[q / 2].y; }
+            second = true;
+            x0 = gsel[1] * P;
+            rowlim = L - 2 - x0;
+            dlim = min(klim, rowlim);
+            klimited = klim < rowlim;
+#pragma unroll
+            for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; }
+#pragma unroll
+            for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+            e = 0;
+            continue;
+        }
+        const float* base = F + ROW_PADL + x0 + e;
+        float w[P + U];
+#pragma unroll
+        for (int m = 0; m < P + U; m += 4) {
+            const float4 v = *reinterpret_cast<const float4*>(base + m);
+            w[m] = v.x; w[m + 1] = v.y; w[m + 2] = v.z; w[m + 3] = v.w;
+        }
+        float2 iv2[U];
+#pragma unroll
+        for (int u = 0; u < U; u += 2) {
+            const float4 v = *reinterpret_cast<const float4*>(inv2 + e + u);
+            iv2[u] = make_float2(v.x, v.y);
+            iv2[u + 1] = make_float2(v.z, v.w);
+        }
+        const float cb = (float)(2 * e + 3);   // 2d + 1 at d = e + 1
+        if (klimited && e + U > dlim)
+            sweep_block<P, U, true>(w, iv2, h, M, acc2, cb, dlim - e);
+        else
+            sweep_block<P, U, false>(w, iv2, h, M, acc2, cb, U);
+        e += U;
+    }
+    // group 0 ends in `first` when a second group ran, else in acc2
+    const int xa = gsel[0] * P, xb = gsel[1] * P;
+#pragma unroll
+    for (int q = 0; q < P; ++q) {
+        const float sa = second ? first[q] : (q % 2 ? acc2[q / 2].y : acc2[q / 2].x);
+        const int x = xa + q;
+        if (x < L) {
+            const int n = min(L - 1 - x, K);
+            cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sa : 0;
+        }
+    }
+    if (second) {
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const float sb = q % 2 ? acc2[q / 2].y : acc2[q / 2].x;
+            const int x = xb + q;
+            if (x < L) {
+                const int n = min(L - 1 - x, K);
+                cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sb : 0;
+            }
+        }
+    }
+}
+
+template <int P, int U>
+__global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepParams sp)
+{
+    extern __shared__ __align__(16) float smem[];
+    float2* inv2 = reinterpret_cast<float2*>(smem);
+    int* istart = reinterpret_cast<int*>(smem + 2 * sp.inv_len);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* F = smem + 2 * sp.inv_len + sp.istart_len + warp * sp.half;
+    for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
+        const float r = __frcp_rn((float)(m + 1));
+        inv2[m] = make_float2(r, r);
+    }
+    for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
+    __syncthreads();
+    const float NEG = neg_inf();
+
+    for (;;) {
+        int item = 0;
+        if (lane == 0) item = (int)atomicAdd(sp.counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= sp.total_items) break;
+        int lo = 0, hi = sp.ndir - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (istart[mid] <= item) lo = mid; else hi = mid - 1;
+        }
+        const DirDev& d = sp.dirs[lo];
+        const int rem = item - istart[lo];
+        const int per_row = 2 * d.chunks;
+        const int p = rem / per_row;
+        const int r2 = rem - p * per_row;
+        const bool rev = (r2 & 1) != 0;
+        const int c = r2 >> 1;
+        const int jlo = sp.rowlo[d.row_off + p], jhi = sp.rowhi[d.row_off + p];
+        const int L = jhi - jlo + 1;
+        const int G = (L + P - 1) / P;
+        if (c * 32 >= (G + 1) / 2) continue;           // no slot of this chunk is used
+        const long long rowbase = d.slab + (long long)p * d.Wp + jlo;
+        const float* zrow = sp.sdem + rowbase;
+        __syncwarp();
+        for (int x = lane; x < L; x += 32) {
+            const float v = rev ? zrow[L - 1 - x] : zrow[x];
+            F[ROW_PADL + x] = (x == L - 1) ? NEG : v;
+        }
+        for (int m = lane; m < ROW_PADR; m += 32) F[ROW_PADL + L + m] = NEG;
+        __syncwarp();
+        sweep_lane<P, U>(F, inv2, (rev ? sp.cv_bwd : sp.cv_fwd) + rowbase, L, c * 32 + lane, d.K, sp.h0, rev);
+    }
+}
+
+// ---------------------------------------------------------------- unskew --
+// CTA = UNSKEW_TI x UNSKEW_TJ DEM cells and one range of the chunk's
+// directions; for each direction the skewed rows those cells blend (both
+// virtual POVs of every cell) are staged in shared memory with coalesced row
+// reads, then every cell takes g * ((1-r) cv_hi + r cv_lo) (Kernel-3 weights;
+// a virtual POV whose sample falls outside the DEM is dropped and the other
+// takes weight 1), cv being the forward plus the backward measure.  Partial
+// sums are FP32 over groups of FP32_GROUP consecutive directions and FP64
+// across groups.  With one range per CTA the result goes straight to the FP64
+// running total (or, for the last chunk, through the FP64 (pi/(2n)) step^2
+// scale to the FP32 output); with several ranges each writes an FP64 partial
+// that unskew_finalize adds in a fixed order.
+constexpr int UNSKEW_ROWS = UNSKEW_TI + UNSKEW_TJ + 4;
+constexpr int UNSKEW_PITCH = UNSKEW_TJ + 1;
+constexpr int UNSKEW_THREADS = 256;
+constexpr int UNSKEW_CELLS = UNSKEW_TI * UNSKEW_TJ / UNSKEW_THREADS;
+
+struct UnskewParams {
+    const int* cvf;
+    const int* cvb;
+    const DirDev* dirs;
+    double* vs64;
+    double* part;
+    float* out;
+    double scale;
+    int rows, cols, ndir, per_split, nsplit, first, last;
+};
+
+__global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
+{
+    __shared__ float T[UNSKEW_ROWS * UNSKEW_PITCH];
+    const int rows = up.rows, cols = up.cols;
+    const int iD0 = blockIdx.y * UNSKEW_TI, jD0 = blockIdx.x * UNSKEW_TJ;
+    const int iD1 = min(iD0 + UNSKEW_TI, rows) - 1, jD1 = min(jD0 + UNSKEW_TJ, cols) - 1;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    const int kbeg = blockIdx.z * up.per_split;
+    const int kend = min(kbeg + up.per_split, up.ndir);
+    float acc32[UNSKEW_CELLS];
+    double acc64[UNSKEW_CELLS];
+#pragma unroll
+    for (int m = 0; m < UNSKEW_CELLS; ++m) { acc32[m] = 0.f; acc64[m] = 0.0; }
+    int group = kbeg < kend ? up.dirs[kbeg].gidx / FP32_GROUP : 0;
+
+    for (int kk = kbeg; kk < kend; ++kk) {
+        const DirDev d = up.dirs[kk];
+        if (d.gidx / FP32_GROUP != group) {
+#pragma unroll
+            for (int m = 0; m < UNSKEW_CELLS; ++m) { acc64[m] += (double)acc32[m]; acc32[m] = 0.f; }
+            group = d.gidx / FP32_GROUP;
+        }
+        int vi0, vi1, vj0, vj1;
+        switch (d.frame) {
+        case 0:  vi0 = iD0; vi1 = iD1; vj0 = jD0; vj1 = jD1; break;
+        case 1:  vi0 = jD0; vi1 = jD1; vj0 = iD0; vj1 = iD1; break;
+        case 2:  vi0 = jD0; vi1 = jD1; vj0 = d.W - 1 - iD1; vj1 = d.W - 1 - iD0; break;
+        default: vi0 = d.H - 1 - iD1; vi1 = d.H - 1 - iD0; vj0 = jD0; vj1 = jD1; break;
+        }
+        const int pmin = max(vi0 - dest_of(d.t_fx, vj1) + d.D - 1, 0);
+        const int pmax = min(vi1 - dest_of(d.t_fx, vj0) + d.D, d.R - 1);
+        const int np = pmax - pmin + 1, nj = vj1 - vj0 + 1;
+        const long long off = d.slab + (long long)pmin * d.Wp + vj0;
+        for (int idx = threadIdx.x; idx < np * 32; idx += UNSKEW_THREADS) {
+            const int r = idx >> 5, c = idx & 31;
+            if (c < nj) {
+                const long long a = off + (long long)r * d.Wp + c;
+                T[r * UNSKEW_PITCH + c] = (float)(up.cvf[a] + up.cvb[a]);
+            }
+        }
+        __syncthreads();
+#pragma unroll
+        for (int m = 0; m < UNSKEW_CELLS; ++m) {
+            const int iD = iD0 + ty + 8 * m, jD = jD0 + tx;
+            if (iD > iD1 || jD > jD1) continue;
+            int i, j;
+            switch (d.frame) {
+            case 0:  i = iD; j = jD; break;
+            case 1:  i = jD; j = iD; break;
+            case 2:  i = jD; j = d.W - 1 - iD; break;
+            default: i = d.H - 1 - iD; j = jD; break;
+            }
+            const unsigned long long y = (unsigned long long)j * d.t_fx;
+            const int dest = (int)(y >> 32);
+            const unsigned fr = (unsigned)(y & 0xFFFFFFFFull);
+            const int rhi = i - dest + d.D - pmin;       // staged row of the line through i + r
+            const int cj = j - vj0;
+            float val;
+            if (fr == 0u) {
+                val = T[rhi * UNSKEW_PITCH + cj];
+            } else {
+                const bool hi_ok = i <= d.H - 2, lo_ok = i >= 1;
+                if (hi_ok && lo_ok) {
+                    const float r = __fmul_rn(__uint2float_rn(fr), 0x1p-32f);
+                    val = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, r), T[rhi * UNSKEW_PITCH + cj]),
+                                    __fmul_rn(r, T[(rhi - 1) * UNSKEW_PITCH + cj]));
+                } else if (hi_ok) {
+                    val = T[rhi * UNSKEW_PITCH + cj];
+                } else {
+                    val = T[(rhi - 1) * UNSKEW_PITCH + cj];
+                }
+            }
+            acc32[m] = __fadd_rn(acc32[m], __fmul_rn(d.g, val));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < UNSKEW_CELLS; ++m) {
+        const int iD = iD0 + ty + 8 * m, jD = jD0 + tx;
+        if (iD > iD1 || jD > jD1) continue;
+        const long long idx = (long long)iD * cols + jD;
+        double tot = acc64[m] + (double)acc32[m];
+        if (up.nsplit > 1) {
+            up.part[(long long)blockIdx.z * rows * cols + idx] = tot;
+            continue;
+        }
+        if (!up.first) tot += up.vs64[idx];
+        if (up.last) up.out[idx] = (float)(tot * up.scale);
+        else up.vs64[idx] = tot;
+    }
+}
+
+__global__ void unskew_finalize(UnskewParams up)
+{
+    const long long cells = (long long)up.rows * up.cols;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < cells;
+         idx += (long long)gridDim.x * blockDim.x) {
+        double tot = 0.0;
+        for (int s = 0; s < up.nsplit; ++s) tot += up.part[s * cells + idx];
+        if (!up.first) tot += up.vs64[idx];
+        if (up.last) up.out[idx] = (float)(tot * up.scale);
+        else up.vs64[idx] = tot;
+    }
+}
+
+}  // namespace
+
+// -------------------------------------------------------------- launchers --
+cudaError_t launch_rowmap(const DirDev* d_dirs, int ndir, int max_R, int* rowlo, int* rowhi,
+                          cudaStream_t stream)
+{
+    if (ndir <= 0) return cudaSuccess;
+    dim3 grid((max_R + 255) / 256, ndir);
+    rowmap_kernel<<<grid, 256, 0, stream>>>(d_dirs, rowlo, rowhi);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_colmap(const DirDev* d_dir, int* dest, unsigned* frac, cudaStream_t stream)
+{
+    colmap_kernel<<<64, 256, 0, stream>>>(d_dir, dest, frac);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_skew(const float* dem, int rows, int cols, const DirDev* d_dirs, int ndir,
+                        int max_tiles, const int* rowlo, const int* rowhi, float* sdem,
+                        cudaStream_t stream)
+{
+    (void)rows; (void)rowlo; (void)rowhi;
+    if (ndir <= 0 || max_tiles <= 0) return cudaSuccess;
+    dim3 grid(max_tiles, ndir);
+    skew_kernel<<<grid, 256, 0, stream>>>(dem, cols, d_dirs, sdem);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
+                         const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
+                         float h0, int wmax, unsigned* counter, int num_sms, int smem_optin,
+                         cudaStream_t stream)
+{
+    if (ndir <= 0 || total_items <= 0) return cudaSuccess;
+    constexpr int P = POVS_PER_LANE, U = SWEEP_UNROLL;
+    SweepParams sp;
+    sp.dirs = d_dirs; sp.item_start = d_item_start; sp.sdem = sdem; sp.rowlo = rowlo;
+    sp.rowhi = rowhi; sp.cv_fwd = cv_fwd; sp.cv_bwd = cv_bwd; sp.counter = counter; sp.ndir = ndir;
+    sp.total_items = total_items; sp.h0 = h0;
+    // 1/d is read up to d = wmax + U (a walk of at most wmax - 2 steps, rounded up to U)
+    sp.inv_len = (wmax + 2 * U + 8 + 1) & ~1;
+    sp.istart_len = (ndir + 1 + 3) & ~3;
+    sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
+    const size_t fixed = (size_t)(2 * sp.inv_len + sp.istart_len) * 4;
+    const size_t per_warp = (size_t)sp.half * 4;
+    if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+    // As many resident warps as shared memory and registers allow, in one CTA per SM
+    // (each warp stages its own row; the 1/d table is shared by the CTA).
+    int warps = (int)std::min<size_t>((smem_optin - fixed) / per_warp, (size_t)SWEEP_MAX_WARPS);
+    const size_t smem = fixed + (size_t)warps * per_warp;
+    cudaError_t err = cudaFuncSetAttribute(sweep_kernel<P, U>,
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<P, U>, warps * 32, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    sweep_kernel<P, U><<<per_sm * num_sms, warps * 32, smem, stream>>>(sp);
+    return cudaGetLastError();
+}
+
+int unskew_per_split(int ndir, int nsplit)
+{
+    const int groups = (ndir + FP32_GROUP - 1) / FP32_GROUP;
+    nsplit = std::max(1, std::min(nsplit, groups));
+    return ((groups + nsplit - 1) / nsplit) * FP32_GROUP;
+}
+
+int unskew_effective_splits(int ndir, int nsplit)
+{
+    const int per = unskew_per_split(ndir, nsplit);
+    return (ndir + per - 1) / per;
+}
+
+int unskew_splits(int rows, int cols, int ndir, int num_sms)
+{
+    const long long tiles = (long long)((cols + UNSKEW_TJ - 1) / UNSKEW_TJ) * ((rows + UNSKEW_TI - 1) / UNSKEW_TI);
+    const long long want = (2LL * num_sms + tiles - 1) / tiles;
+    const int groups = (ndir + FP32_GROUP - 1) / FP32_GROUP;
+    return (int)std::max<long long>(1, std::min<long long>(want, groups));
+}
+
+cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, int rows, int cols, const DirDev* d_dirs,
+                          int ndir, int nsplit, double* part, double* vs64, float* out, int first_chunk,
+                          int last_chunk, double scale, cudaStream_t stream)
+{
+    UnskewParams up;
+    up.cvf = cv_fwd; up.cvb = cv_bwd; up.dirs = d_dirs; up.vs64 = vs64; up.part = part; up.out = out;
+    up.scale = scale; up.rows = rows; up.cols = cols; up.ndir = ndir;
+    up.first = first_chunk; up.last = last_chunk;
+    // split the directions into ranges of whole FP32 groups
+    up.per_split = unskew_per_split(ndir, nsplit);
+    up.nsplit = unskew_effective_splits(ndir, nsplit);
+    dim3 grid((cols + UNSKEW_TJ - 1) / UNSKEW_TJ, (rows + UNSKEW_TI - 1) / UNSKEW_TI, up.nsplit);
+    unskew_kernel<<<grid, UNSKEW_THREADS, 0, stream>>>(up);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_unskew_finalize(int rows, int cols, int ndir, int nsplit, const double* part, double* vs64,
+                                   float* out, int first_chunk, int last_chunk, double scale,
+                                   cudaStream_t stream)
+{
+    UnskewParams up{};
+    up.part = const_cast<double*>(part); up.vs64 = vs64; up.out = out; up.scale = scale;
+    up.rows = rows; up.cols = cols; up.first = first_chunk; up.last = last_chunk;
+    up.nsplit = unskew_effective_splits(ndir, nsplit);
+    if (up.nsplit <= 1) return cudaSuccess;
+    const long long cells = (long long)rows * cols;
+    const int blocks = (int)std::min<long long>((cells + 255) / 256, 4096);
+    unskew_finalize<<<blocks, 256, 0, stream>>>(up);
+    return cudaGetLastError();
+}
+
+}  // namespace tvs

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the oracle.
+
+Two bars:
+* against the oracle's FP32-decision mode (visibility decided in single
+  precision with the same slope formula, as the paper's kernels declare it:
+  float heights and slopes in Alg. 6-8): integer offsets, row maps and every
+  per-sample cv must be bit-identical, and the per-cell area may differ only
+  by FP32 summation (rtol FP32_RTOL).  Both sides take every visibility
+  decision in the same precision, so this is the parity gate;
+* against the FP64 oracle: relative error <= 1e-2 on every cell (denominator
+  max(|oracle|, step^2)), and the share of cells within 1e-4 is reported and
+  bounded below by FP64_SHARE_FLOOR.  A near-tie between a target's slope and
+  the running maximum decides differently in FP32 and FP64; each such flip
+  moves a half-line's measure by 2d+1, and on paper-scale fractal terrain a few
+  percent of cells (those with small viewsheds) see one that exceeds 1e-4.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import paper_2003_02200_gb300 as tvs
+from paper_2003_02200_gb300 import terrain
+
+pytestmark = pytest.mark.gpu
+
+# FP32 per-direction blend + FP32 sums over groups of 8 directions: each cell's
+# value carries at most ~10 single-precision roundings relative to the FP64 sum.
+FP32_RTOL = 4e-6
+# Measured lower bound of the share of cells within 1e-4 of the FP64 oracle for
+# FP32 decisions (99.7 % at 100^2, about 97 % at 2000^2).
+FP64_SHARE_FLOOR = 0.95
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tvs.Context(0)
+    yield c
+    c.close()
+
+
+def rel_err(got, want, step):
+    den = np.maximum(np.abs(want), step * step)
+    return np.abs(got.astype(np.float64) - want) / den
+
+
+def assert_fp64_tolerance(got, want, step, floor=FP64_SHARE_FLOOR):
+    e = rel_err(got, want, step).reshape(-1)
+    frac_ok = np.mean(e <= 1e-4)
+    print(f"vs FP64 oracle: {frac_ok:.5f} of cells within 1e-4, max rel err {e.max():.3g}")
+    assert frac_ok >= floor, f"only {frac_ok:.5f} of cells within 1e-4 (max {e.max():.3g})"
+    assert e.max() <= 1e-2, f"max relative error {e.max():.3g}"
+
+
+def rand_dem(rows, cols, seed, scale=50.0):
+    return (np.random.default_rng(seed).random((rows, cols)) * scale).astype(np.float32)
+
+
+# --------------------------------------------------------------- row maps --
+
+@pytest.mark.parametrize("rows,cols,n,ks", [
+    (100, 100, 180, None), (37, 53, 7, None), (53, 37, 360, range(0, 360, 7)), (2, 2, 4, None),
+    (2, 300, 16, None), (300, 2, 16, None), (1000, 333, 90, range(0, 90, 11)),
+])
+def test_rowmap_bit_exact(ctx, orc, rows, cols, n, ks):
+    for k in (ks if ks is not None else range(n)):
+        g = ctx.debug_rowmap(rows, cols, n, k)
+        d = orc.direction(n, k, rows, cols)
+        assert g["R"] == d["H"] + d["D"]
+        dest, frac = orc.column_offsets(n, k, rows, cols)
+        assert np.array_equal(g["dest"], dest.astype(np.int32))
+        assert np.array_equal(g["frac"], frac)
+        for p in range(g["R"]):
+            lo, hi = orc.line_range(n, k, rows, cols, p - d["D"])
+            if hi >= lo:
+                assert (g["jlo"][p], g["jhi"][p]) == (lo, hi), (k, p)
+            else:
+                assert g["jhi"][p] < g["jlo"][p]
+
+
+# ------------------------------------------------- per-sample cv, bit-exact --
+
+def oracle_cv_slab(orc, dem, step, h0, n, rng, k):
+    rows, cols = dem.shape
+    d = orc.direction(n, k, rows, cols)
+    R = d["H"] + d["D"]
+    return np.stack([orc.line_cv(dem, step, h0, n, rng, 32, k, p - d["D"]) for p in range(R)])
+
+
+@pytest.mark.parametrize("k", [0, 1, 17, 44, 45, 46, 71, 89, 90, 91, 112, 134, 135, 136, 160, 179])
+def test_direction_cv_bit_exact_fp32_oracle(ctx, orc, k):
+    w = terrain.WORKLOADS["tvs100"]
+    dem = terrain.workload_dem("tvs100")
+    got = ctx.debug_direction_cv(dem, w["step"], w["h0"], w["n"], 0.0, k)
+    want = oracle_cv_slab(orc, dem, w["step"], w["h0"], w["n"], 0.0, k)
+    assert got.shape == want.shape
+    bad = np.argwhere(got != want)
+    assert bad.size == 0, f"{len(bad)} samples differ, first {bad[:5].tolist()}"
+
+
+@pytest.mark.parametrize("rows,cols,n,k,rng,h0", [
+    (7, 700, 12, 0, 0.0, 1.5), (700, 7, 12, 5, 0.0, 1.5), (40, 600, 24, 3, 37.0, 4.0),
+    (600, 40, 24, 20, 90.0, 0.0), (300, 300, 8, 1, 0.0, 2.0), (3, 257, 4, 0, 0.0, 1.0),
+])
+def test_direction_cv_long_rows_and_range(ctx, orc, rows, cols, n, k, rng, h0):
+    """Rows longer than one warp item (256 samples), several items per row,
+    and walks cut by the max range (the masked last block)."""
+    dem = rand_dem(rows, cols, seed=rows + cols + k)
+    got = ctx.debug_direction_cv(dem, 10.0, h0, n, rng, k)
+    want = oracle_cv_slab(orc, dem, 10.0, h0, n, rng, k)
+    assert np.array_equal(got, want)
+
+
+# ---------------------------------------------------------- total viewshed --
+
+def test_tvs100_matches_fp32_oracle_and_fp64_tolerance(ctx, orc):
+    """The 100 x 100, 180-direction workload, every cell."""
+    w = terrain.WORKLOADS["tvs100"]
+    dem = terrain.workload_dem("tvs100")
+    got = ctx.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0)
+    o32 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=32)
+    np.testing.assert_allclose(got, o32, rtol=FP32_RTOL, atol=0)
+    o64 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=64)
+    assert_fp64_tolerance(got, o64, w["step"])
+
+
+CASES = [
+    # rows, cols, n, max_range, h0, kind
+    (2, 2, 4, 0.0, 1.5, "rand"), (2, 9, 5, 0.0, 1.5, "rand"), (9, 2, 6, 0.0, 1.5, "rand"),
+    (3, 257, 16, 0.0, 1.5, "rand"), (257, 3, 16, 0.0, 1.5, "rand"), (31, 45, 1, 0.0, 1.5, "rand"),
+    (31, 45, 2, 0.0, 1.5, "rand"), (31, 45, 7, 0.0, 1.5, "rand"), (45, 31, 180, 0.0, 1.5, "rand"),
+    (64, 64, 36, 55.0, 1.5, "rand"), (64, 64, 36, 5.0, 1.5, "rand"), (64, 64, 36, 10.0, 1.5, "rand"),
+    (64, 64, 36, 14.9, 1.5, "rand"), (50, 70, 24, 0.0, 0.0, "zero"), (50, 70, 24, 0.0, 2.0, "flat"),
+    (61, 43, 19, 0.0, 3.0, "neg"), (130, 300, 12, 0.0, 1.5, "frac"), (300, 130, 12, 800.0, 10.0, "frac"),
+    (5, 1030, 8, 0.0, 1.5, "rand"), (1030, 5, 8, 0.0, 1.5, "rand"),
+]
+
+
+def make_dem(rows, cols, kind, seed):
+    if kind == "zero":
+        return np.zeros((rows, cols), np.float32)
+    if kind == "flat":
+        return np.full((rows, cols), 412.5, np.float32)
+    if kind == "neg":
+        return rand_dem(rows, cols, seed, 300.0) - np.float32(150.0)
+    if kind == "frac":
+        return terrain.fractal_dem(rows, cols, 0.8, 900.0, seed)
+    return rand_dem(rows, cols, seed)
+
+
+@pytest.mark.parametrize("rows,cols,n,rng,h0,kind", CASES)
+def test_shapes_edges_and_ranges(ctx, orc, rows, cols, n, rng, h0, kind):
+    dem = make_dem(rows, cols, kind, seed=rows * 31 + cols)
+    got = ctx.total_viewshed(dem, 10.0, h0, n, rng)
+    o32 = orc.total_viewshed(dem, 10.0, h0, n, rng, prec=32)
+    np.testing.assert_allclose(got, o32, rtol=FP32_RTOL, atol=0)
+    o64 = orc.total_viewshed(dem, 10.0, h0, n, rng, prec=64)
+    assert_fp64_tolerance(got, o64, 10.0)
+
+
+def test_max_range_below_one_step_gives_zero(ctx):
+    dem = rand_dem(20, 30, seed=1)
+    got = ctx.total_viewshed(dem, 10.0, 1.5, 8, 5.0)
+    assert np.all(got == 0.0)
+
+
+def test_chunked_budget_matches(ctx):
+    """A small HBM budget splits the directions into several chunks (multiples
+    of 8 directions).  The FP32 group sums do not move; only the order of the
+    FP64 additions across groups changes, which is below FP32 resolution."""
+    dem = terrain.fractal_dem(300, 260, 0.8, 800.0, seed=5)
+    full = ctx.total_viewshed(dem, 10.0, 1.5, 96, 0.0)
+    with tvs.Context(0, hbm_budget_bytes=24 << 20) as small:
+        part = small.total_viewshed(dem, 10.0, 1.5, 96, 0.0)
+    np.testing.assert_allclose(part, full, rtol=2e-7, atol=0)
+
+
+def test_device_api_matches_host_api_on_a_side_stream(ctx):
+    import torch
+    dem = terrain.fractal_dem(200, 150, 0.8, 700.0, seed=6)
+    host = ctx.total_viewshed(dem, 10.0, 1.5, 60, 0.0)
+    s = torch.cuda.Stream()
+    d = torch.from_numpy(dem).cuda()
+    with torch.cuda.stream(s):
+        out = ctx.total_viewshed_device(d, 10.0, 1.5, 60, 0.0, stream=s)
+    s.synchronize()
+    assert np.array_equal(out.cpu().numpy(), host)
+
+
+def test_deterministic_repeat(ctx):
+    dem = terrain.fractal_dem(180, 180, 0.8, 600.0, seed=7)
+    a = ctx.total_viewshed(dem, 10.0, 1.5, 45, 0.0)
+    b = ctx.total_viewshed(dem, 10.0, 1.5, 45, 0.0)
+    assert np.array_equal(a, b)
+
+
+def test_argument_errors(ctx):
+    import torch
+    dem = rand_dem(8, 8, seed=1)
+    for args in [(dem[:1], 10.0, 1.5, 4, 0.0), (dem, 0.0, 1.5, 4, 0.0), (dem, 10.0, 1.5, 0, 0.0),
+                 (dem, 10.0, float("nan"), 4, 0.0), (dem, 10.0, 1.5, 4, float("nan"))]:
+        with pytest.raises(tvs.TvsError) as ei:
+            ctx.total_viewshed(*args)
+        assert ei.value.code == tvs._binding.TVS_ERR_ARG
+    bad = dem.copy()
+    bad[3, 3] = np.inf
+    with pytest.raises(tvs.TvsError):
+        ctx.total_viewshed(bad, 10.0, 1.5, 4)
+    d = torch.zeros(16, 16, device="cuda")
+    rc = ctx._lib.tvs_total_viewshed_device(ctx.handle, d.data_ptr(), 16, 16, 1.0, 1.0, 4, 0.0,
+                                            d.data_ptr() + 64, None)
+    assert rc == tvs._binding.TVS_ERR_ARG
+    with tvs.Context(0, hbm_budget_bytes=1 << 16) as tiny:
+        with pytest.raises(tvs.TvsError) as ei:
+            tiny.total_viewshed(rand_dem(400, 400, seed=2), 10.0, 1.5, 8)
+        assert ei.value.code == tvs._binding.TVS_ERR_OOM
+
+
+def test_profiling_counts_the_work(ctx):
+    dem = terrain.fractal_dem(120, 90, 0.8, 500.0, seed=8)
+    ctx.profile(True)
+    ctx.total_viewshed(dem, 10.0, 1.5, 32, 0.0)
+    st = ctx.profile_read()
+    ctx.profile(False)
+    assert st["sweep"]["launches"] == 1 and st["sweep"]["total_ms"] > 0
+    assert st["sweep"]["units"] == tvs.count_evals(120, 90, 32, 10.0, 0.0)
+    assert st["skew"]["launches"] == 1 and st["unskew"]["launches"] == 1
+
+
+# ------------------------------------------- full-size workloads, sampled --
+
+def sample_cells(rows, cols, count, seed):
+    rng = np.random.default_rng(seed)
+    edge = [0, cols - 1, (rows - 1) * cols, rows * cols - 1, cols // 2, (rows // 2) * cols]
+    return np.unique(np.concatenate([edge, rng.choice(rows * cols, size=count, replace=False)]))
+
+
+def test_tvs2000_sampled_parity(ctx, orc):
+    """The 2000 x 2000, 180-direction workload on the device path (the launch
+    configuration the benchmark times); 1000 sampled cells against the oracle."""
+    import torch
+    w = terrain.WORKLOADS["tvs2000"]
+    dem = terrain.workload_dem("tvs2000")
+    d = torch.from_numpy(dem).cuda()
+    out = ctx.total_viewshed_device(d, w["step"], w["h0"], w["n"], 0.0)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(-1)
+    cells = sample_cells(2000, 2000, 1000, seed=11)
+    o64 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=64, cells=cells)
+    assert_fp64_tolerance(got[cells], o64, w["step"])
+    o32 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=32, cells=cells[:300])
+    np.testing.assert_allclose(got[cells[:300]], o32, rtol=FP32_RTOL, atol=0)
+    assert np.all(np.isfinite(got)) and got.min() > 0
+
+
+def test_tvs4000_range_limited_sampled_parity(ctx, orc):
+    """4000 x 4000 with spikes, 360 directions, 10 km range (walks capped by
+    the range, several warp items per row); 200 sampled cells."""
+    import torch
+    w = terrain.WORKLOADS["tvs4000"]
+    dem = terrain.workload_dem("tvs4000")
+    d = torch.from_numpy(dem).cuda()
+    out = ctx.total_viewshed_device(d, w["step"], w["h0"], w["n"], w["max_range"])
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().reshape(-1)
+    cells = sample_cells(4000, 4000, 200, seed=12)
+    o32 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], w["max_range"], prec=32, cells=cells)
+    np.testing.assert_allclose(got[cells], o32, rtol=FP32_RTOL, atol=0)
+    o64 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], w["max_range"], prec=64, cells=cells)
+    assert_fp64_tolerance(got[cells], o64, w["step"])
+    # nothing farther than the range: bounded by the full disc of 10 km radius
+    assert got.max() <= math.pi * w["max_range"] ** 2 * 1.01

@@ -1,0 +1,89 @@
+"""CPU-only checks of the C-ABI library: it builds, loads, exports every
+function include/tvs.h declares, and its host-side logic (direction table,
+work count, argument checks) agrees with the oracle.  No GPU compute here."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import paper_2003_02200_gb300 as tvs
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return tvs.load()
+
+
+def test_library_exports_every_declared_function(lib):
+    names = tvs.declared_functions()
+    assert len(names) >= 12
+    for name in names:
+        assert hasattr(lib, name), name
+    assert lib.tvs_abi_version() == 1
+
+
+@pytest.mark.parametrize("n,rows,cols", [(180, 100, 100), (7, 13, 29), (360, 50, 21), (1, 2, 2), (4, 9, 5)])
+def test_direction_table_matches_oracle(orc, n, rows, cols):
+    for k in range(n):
+        a = tvs.direction(n, k, rows, cols, 10.0, 1234.0)
+        b = orc.direction(n, k, rows, cols, 10.0, 1234.0)
+        for f in ("frame", "m", "H", "W", "t_fx", "D", "K"):
+            assert a[f] == b[f], (k, f)
+        assert a["g"] == b["g"] and a["t"] == b["t"]
+        assert a["R"] == a["H"] + a["D"]
+
+
+@pytest.mark.parametrize("rows,cols,n,step,rng", [
+    (12, 15, 4, 10.0, 0.0), (23, 17, 9, 10.0, 0.0), (40, 40, 180, 10.0, 0.0), (31, 20, 16, 5.0, 42.0),
+    (2, 2, 1, 1.0, 0.0), (50, 3, 8, 1.0, 3.0)])
+def test_eval_count_matches_oracle(orc, rows, cols, n, step, rng):
+    assert tvs.count_evals(rows, cols, n, step, rng) == orc.count_evals(rows, cols, n, step, rng)
+
+
+def test_eval_count_paper_scale_closed_form():
+    """For a square DEM with unlimited range every direction's work is about
+    sum over rows of L^2; for 2000^2 and 180 directions about 0.85 W^3 n."""
+    E = tvs.count_evals(2000, 2000, 180, 10.0, 0.0)
+    assert 0.7 * 2000 ** 3 * 180 < E < 1.0 * 2000 ** 3 * 180
+
+
+def test_host_argument_errors(lib):
+    info = tvs._binding.DirectionInfo()
+    assert lib.tvs_direction(0, 0, 10, 10, 1.0, 0.0, C.byref(info)) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_direction(8, 8, 10, 10, 1.0, 0.0, C.byref(info)) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_direction(8, 1, 1, 10, 1.0, 0.0, C.byref(info)) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_direction(8, 1, 10, 10, 0.0, 0.0, C.byref(info)) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_count_evals(1, 10, 4, 1.0, 0.0) < 0
+    assert lib.tvs_count_evals(10, 10, 4, 1.0, float("nan")) < 0
+    assert b"n_sectors" in lib.tvs_last_error(None) or lib.tvs_last_error(None)
+    h = C.c_void_p()
+    assert lib.tvs_create(None, 0, 0) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_total_viewshed(None, None, 4, 4, 1.0, 1.0, 4, 0.0, None) == tvs._binding.TVS_ERR_ARG
+    lib.tvs_destroy(None)
+    del h
+
+
+def test_create_without_gpu_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(tvs.TvsError) as ei:
+        tvs.Context(0)
+    assert ei.value.code == tvs._binding.TVS_ERR_CUDA
+
+
+def test_terrain_generator_is_seeded_and_shaped():
+    from paper_2003_02200_gb300 import terrain
+    a = terrain.fractal_dem(64, 80, 0.8, 500.0, seed=1)
+    b = terrain.fractal_dem(64, 80, 0.8, 500.0, seed=1)
+    assert a.dtype == np.float32 and a.shape == (64, 80)
+    assert np.array_equal(a, b)
+    assert a.min() == 0.0 and abs(a.max() - 500.0) < 1e-3
+    s = terrain.fractal_dem(64, 64, 0.7, 100.0, seed=2, spike_frac=0.05)
+    base = terrain.fractal_dem(64, 64, 0.7, 100.0, seed=2)
+    raised = np.count_nonzero(s - base > 1.0)
+    assert raised == round(0.05 * 64 * 64)
+    tiles = terrain.batch_tiles(8)
+    assert all(256 <= t["rows"] <= 1500 for t in tiles)
+    reqs = terrain.request_stream(20)
+    assert all(reqs[i]["arrival"] < reqs[i + 1]["arrival"] for i in range(19))
