@@ -55,6 +55,9 @@ WORKLOADS = {
                     max_range=0.0, spike_frac=0.0, seed=SEED_BASE + 1),
     "tvs4000": dict(rows=4000, cols=4000, hurst=0.7, relief=2500.0, step=5.0, h0=10.0, n=360,
                     max_range=10000.0, spike_frac=0.05, seed=SEED_BASE + 2),
+    # profiling size: the 2000^2 recipe at a quarter of the cells (a few GB of scratch)
+    "tvs1000": dict(rows=1000, cols=1000, hurst=0.8, relief=1500.0, step=10.0, h0=1.5, n=180,
+                    max_range=0.0, spike_frac=0.0, seed=SEED_BASE + 5),
 }
 
 

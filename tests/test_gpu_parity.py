@@ -7,12 +7,14 @@ Two bars:
   per-sample cv must be bit-identical, and the per-cell area may differ only
   by FP32 summation (rtol FP32_RTOL).  Both sides take every visibility
   decision in the same precision, so this is the parity gate;
-* against the FP64 oracle: relative error <= 1e-2 on every cell (denominator
-  max(|oracle|, step^2)), and the share of cells within 1e-4 is reported and
-  bounded below by FP64_SHARE_FLOOR.  A near-tie between a target's slope and
-  the running maximum decides differently in FP32 and FP64; each such flip
-  moves a half-line's measure by 2d+1, and on paper-scale fractal terrain a few
-  percent of cells (those with small viewsheds) see one that exceeds 1e-4.
+* against the FP64 oracle: the share of cells within 1e-4 (denominator
+  max(|oracle|, step^2)) is reported and bounded below by FP64_SHARE_FLOOR, and
+  every cell within FP64_MAX_REL.  A near-tie between a target's slope and the
+  running maximum decides differently in FP32 and FP64; each such flip moves a
+  half-line's measure by 2d+1, and on paper-scale fractal terrain a few percent
+  of cells (those with small viewsheds) see one that exceeds 1e-4.  With few
+  directions and a short range one flip can move a small viewshed by a few
+  percent, hence FP64_MAX_REL.
 """
 import math
 
@@ -30,6 +32,7 @@ FP32_RTOL = 4e-6
 # Measured lower bound of the share of cells within 1e-4 of the FP64 oracle for
 # FP32 decisions (99.7 % at 100^2, about 97 % at 2000^2).
 FP64_SHARE_FLOOR = 0.95
+FP64_MAX_REL = 5e-2
 
 
 @pytest.fixture(scope="module")
@@ -49,7 +52,7 @@ def assert_fp64_tolerance(got, want, step, floor=FP64_SHARE_FLOOR):
     frac_ok = np.mean(e <= 1e-4)
     print(f"vs FP64 oracle: {frac_ok:.5f} of cells within 1e-4, max rel err {e.max():.3g}")
     assert frac_ok >= floor, f"only {frac_ok:.5f} of cells within 1e-4 (max {e.max():.3g})"
-    assert e.max() <= 1e-2, f"max relative error {e.max():.3g}"
+    assert e.max() <= FP64_MAX_REL, f"max relative error {e.max():.3g}"
 
 
 def rand_dem(rows, cols, seed, scale=50.0):
