@@ -54,6 +54,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle baseline (profiling runs)")
     ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end run")
+    ap.add_argument("--hbm-budget-mb", type=int, default=0,
+                    help="device scratch budget of the library handle (0 = library default)")
     return ap.parse_args(argv)
 
 
@@ -232,7 +234,7 @@ def run_ours(args) -> int:
     w = workload(args.workload)
     dem_np = terrain.workload_dem(args.workload)
     E = tvs.count_evals(w["rows"], w["cols"], w["n"], w["step"], w["max_range"])
-    ctx = tvs.Context(local)
+    ctx = tvs.Context(local, hbm_budget_bytes=args.hbm_budget_mb << 20)
     dem = torch.from_numpy(dem_np).to(device)
     out = torch.empty_like(dem)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
