@@ -110,6 +110,30 @@ int tvs_total_viewshed_device(tvs_handle h, const float* d_dem, int rows, int co
                               double obs_height_m, int n_sectors, double max_range_m, float* d_out,
                               void* cuda_stream);
 
+/* Same computation as tvs_total_viewshed_device, for callers that cannot
+ * allocate device memory (a framework whose caching allocator owns the GPU's
+ * memory budget, or a latency-bound loop that must not pay the device-wide
+ * synchronisation of cudaMalloc/cudaFree).  It takes no handle and allocates
+ * nothing: all scratch lives in one file-scope device array of 64 MiB, reserved
+ * when the library's device code is loaded and held by every GPU that loads it
+ * until the process exits.  The paper has no counterpart to this entry point.
+ * Runs on the calling thread's current device, ordered on `cuda_stream`
+ * (a cudaStream_t, NULL = legacy default stream); d_dem, d_out (rows*cols
+ * float32 each, not overlapping) and the stream must belong to that device.
+ * The first call on a device resolves the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call shares the one array (it keeps the last call's contents; the
+ * entry point resets what must start at zero), so calls that overlap on the
+ * GPU race: order them on one stream or synchronise between them.
+ * Limits: n_sectors <= 1024, and the job must fit 64 MiB: 8 bytes per DEM
+ * cell plus 12 bytes per skewed sample of at least one direction (a diagonal
+ * direction of an S x S DEM has about 2 S^2 samples, so S <= 1400 fits;
+ * larger jobs return TVS_ERR_OOM with a message).
+ * Errors: TVS_ERR_ARG, TVS_ERR_OOM, TVS_ERR_CUDA. */
+int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, int cols, double step_m,
+                                      double obs_height_m, int n_sectors, double max_range_m, float* d_out,
+                                      void* cuda_stream);
+
 /* Direction table entry k of n for a rows x cols DEM (host only, no GPU). */
 int tvs_direction(int n_sectors, int k, int rows, int cols, double step_m, double max_range_m,
                   tvs_direction_info* info);

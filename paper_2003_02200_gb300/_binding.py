@@ -75,6 +75,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                     C.c_double, vp], C.c_int),
             "tvs_total_viewshed_device": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                            C.c_double, vp, vp], C.c_int),
+            "tvs_total_viewshed_device_noalloc": ([vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
+                                                   C.c_double, vp, vp], C.c_int),
             "tvs_direction": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                C.POINTER(DirectionInfo)], C.c_int),
             "tvs_count_evals": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double], C.c_int64),
@@ -117,6 +119,28 @@ def count_evals(rows: int, cols: int, n_sectors: int, step_m: float = 1.0, max_r
     if E < 0:
         _check(int(E))
     return int(E)
+
+
+def total_viewshed_device_noalloc(dem, step_m: float, obs_height_m: float, n_sectors: int = 180,
+                                  max_range_m: float = 0.0, out=None, stream=None):
+    """tvs_total_viewshed_device_noalloc on torch CUDA tensors of the current
+    device: no handle, no device allocation by the library (its scratch is a
+    fixed 64 MiB device array).  `out` must be given by callers that cannot
+    allocate; when omitted it is created here with torch."""
+    import torch
+    if not (isinstance(dem, torch.Tensor) and dem.is_cuda and dem.dtype == torch.float32
+            and dem.dim() == 2 and dem.is_contiguous()):
+        raise ValueError("dem must be a contiguous 2-D float32 CUDA tensor")
+    if out is None:
+        out = torch.empty_like(dem)
+    if out.shape != dem.shape or out.dtype != torch.float32 or not out.is_contiguous() or not out.is_cuda:
+        raise ValueError("out must be a contiguous float32 CUDA tensor shaped like dem")
+    if stream is None:
+        stream = torch.cuda.current_stream(dem.device)
+    _check(load().tvs_total_viewshed_device_noalloc(dem.data_ptr(), dem.shape[0], dem.shape[1], step_m,
+                                                    obs_height_m, n_sectors, max_range_m, out.data_ptr(),
+                                                    stream.cuda_stream))
+    return out
 
 
 class Context:

@@ -764,3 +764,172 @@ int tvs_profile_read(tvs_handle h, tvs_kernel_stats* stats, int max, int* count)
 }
 
 }  // extern "C"
+
+// ================================================ no-allocation entry point ==
+// For callers that cannot allocate device memory themselves: a framework
+// whose caching allocator owns the whole GPU budget, or a latency-bound loop
+// that must not pay the device-wide synchronisation cudaMalloc and cudaFree
+// imply.  All scratch of this entry point lives in one file-scope device array
+// of fixed size, reserved when the library's module is loaded and held by
+// every GPU that loads it until the process exits.  It has no counterpart in
+// the paper.
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)64 << 20;   // 64 MiB
+constexpr int kNoAllocMaxDirs = 1024;
+constexpr int kNoAllocMaxDevices = 64;
+
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+std::mutex g_noalloc_mu;
+char* g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch array on `device` (current), resolved once per
+// device.  A host-side reference to g_noalloc_scratch is only a stand-in, so
+// host code must pass this address to kernels.
+int noalloc_scratch(int device, char** base)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (device < 0 || device >= kNoAllocMaxDevices) return fail(TVS_ERR_ARG, "device index out of range");
+    if (!g_noalloc_base[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress of the no-allocation scratch");
+        g_noalloc_base[device] = static_cast<char*>(p);
+    }
+    *base = g_noalloc_base[device];
+    return TVS_OK;
+}
+
+}  // namespace
+
+extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, int cols, double step_m,
+                                                 double obs_height_m, int n_sectors, double max_range_m,
+                                                 float* d_out, void* cuda_stream)
+{
+    if (!d_dem || !d_out) return fail(TVS_ERR_ARG, "d_dem or d_out is NULL");
+    int rc = check_job(rows, cols, step_m, obs_height_m, n_sectors, max_range_m);
+    if (rc) return rc;
+    if (n_sectors > kNoAllocMaxDirs)
+        return fail(TVS_ERR_ARG, "the no-allocation entry point takes at most 1024 directions");
+    const size_t cells = (size_t)rows * cols;
+    const char* a = reinterpret_cast<const char*>(d_dem);
+    const char* b = reinterpret_cast<const char*>(d_out);
+    if (a < b + cells * 4 && b < a + cells * 4) return fail(TVS_ERR_ARG, "d_dem and d_out overlap");
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    int device = 0;
+    TVS_CUDA(cudaGetDevice(&device), "cudaGetDevice");
+    char* base = nullptr;
+    rc = noalloc_scratch(device, &base);
+    if (rc) return rc;
+    int num_sms = 0, smem_optin = 0;
+    TVS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, device), "device attribute");
+    TVS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device),
+             "device attribute");
+
+    // Direction table and chunking, on the stack: chunks of consecutive
+    // directions whose skewed slabs fit what the fixed part leaves.
+    DirDev dirs[kNoAllocMaxDirs];
+    int istart[2 * kNoAllocMaxDirs + 1];
+    int chunk_k0[kNoAllocMaxDirs + 1];
+    int nchunks = 0;
+    const int nsplit = unskew_splits(rows, cols, std::min(n_sectors, FP32_GROUP * 64), num_sms);
+    const size_t o_dirs = 0;
+    const size_t o_istart = o_dirs + align256((size_t)n_sectors * sizeof(DirDev));
+    const size_t o_vs64 = o_istart + align256((size_t)(2 * n_sectors + 1) * 4);
+    const size_t o_part = o_vs64 + align256(cells * 8);
+    const size_t o_counter = o_part + (nsplit > 1 ? align256((size_t)nsplit * cells * 8) : 0);
+    const size_t o_chunk = o_counter + 256;
+    if (o_chunk >= kNoAllocScratchBytes)
+        return fail(TVS_ERR_OOM, "the DEM does not fit the 64 MiB no-allocation scratch");
+    const size_t avail = kNoAllocScratchBytes - o_chunk;
+    size_t max_rows = 0, max_slab = 0;
+    {
+        int k = 0;
+        while (k < n_sectors) {
+            size_t slab = 0, nrows = 0;
+            int kk = k;
+            while (kk < n_sectors) {
+                HostDir d;
+                make_direction(n_sectors, kk, rows, cols, step_m, max_range_m, &d);
+                const size_t wp = (size_t)((d.W + 3) & ~3);
+                const size_t s2 = slab + (size_t)d.R * wp, r2 = nrows + d.R;
+                const size_t need = 2 * align256(r2 * 4) + 3 * align256(s2 * 4);
+                if (need > avail || 2LL * (long long)r2 * sweep_chunks(d.W) > kMaxChunkItems) break;
+                DirDev& v = dirs[kk];
+                std::memset(&v, 0, sizeof(v));
+                v.t_fx = d.t_fx; v.slab = (long long)slab; v.frame = d.frame; v.H = d.H; v.W = d.W;
+                v.Wp = (int)wp; v.D = d.D; v.R = d.R;
+                v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
+                v.row_off = (int)nrows; v.chunks = sweep_chunks(d.W); v.gidx = kk; v.g = (float)d.g;
+                slab = s2;
+                nrows = r2;
+                ++kk;
+            }
+            if (kk == k)
+                return fail(TVS_ERR_OOM, "one direction of this DEM does not fit the 64 MiB no-allocation scratch");
+            chunk_k0[nchunks++] = k;
+            max_rows = std::max(max_rows, nrows);
+            max_slab = std::max(max_slab, slab);
+            k = kk;
+        }
+        chunk_k0[nchunks] = n_sectors;
+        int at = 0;
+        for (int c = 0; c < nchunks; ++c) {
+            istart[at] = 0;
+            for (int q = chunk_k0[c]; q < chunk_k0[c + 1]; ++q) {
+                istart[at + 1] = istart[at] + 2 * dirs[q].R * dirs[q].chunks;
+                ++at;
+            }
+            ++at;
+        }
+    }
+    DirDev* d_dirs = reinterpret_cast<DirDev*>(base + o_dirs);
+    int* d_istart = reinterpret_cast<int*>(base + o_istart);
+    double* d_vs64 = reinterpret_cast<double*>(base + o_vs64);
+    double* d_part = nsplit > 1 ? reinterpret_cast<double*>(base + o_part) : nullptr;
+    unsigned* d_counter = reinterpret_cast<unsigned*>(base + o_counter);
+    int* d_rowlo = reinterpret_cast<int*>(base + o_chunk);
+    int* d_rowhi = reinterpret_cast<int*>(base + o_chunk + align256(max_rows * 4));
+    const size_t o_sdem = o_chunk + 2 * align256(max_rows * 4);
+    float* d_sdem = reinterpret_cast<float*>(base + o_sdem);
+    int* d_cvf = reinterpret_cast<int*>(base + o_sdem + align256(max_slab * 4));
+    int* d_cvb = reinterpret_cast<int*>(base + o_sdem + 2 * align256(max_slab * 4));
+
+    // Stack tables are staged by the runtime before these calls return.
+    TVS_CUDA(cudaMemcpyAsync(d_dirs, dirs, (size_t)n_sectors * sizeof(DirDev), cudaMemcpyHostToDevice, s),
+             "copy direction table");
+    TVS_CUDA(cudaMemcpyAsync(d_istart, istart, (size_t)(n_sectors + nchunks) * 4, cudaMemcpyHostToDevice, s),
+             "copy item table");
+    const double scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
+    int at = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        const int k0 = chunk_k0[c], nd = chunk_k0[c + 1] - k0;
+        int max_R = 0, max_tiles = 0, wmax = 0;
+        for (int q = k0; q < k0 + nd; ++q) {
+            max_R = std::max(max_R, dirs[q].R);
+            max_tiles = std::max(max_tiles, ((dirs[q].R + SKEW_TP - 1) / SKEW_TP) * ((dirs[q].W + SKEW_TJ - 1) / SKEW_TJ));
+            wmax = std::max(wmax, dirs[q].W);
+        }
+        const DirDev* cd = d_dirs + k0;
+        const int first = c == 0, last = c + 1 == nchunks;
+        TVS_CUDA(launch_rowmap(cd, nd, max_R, d_rowlo, d_rowhi, s), "rowmap launch");
+        TVS_CUDA(launch_skew(d_dem, rows, cols, cd, nd, max_tiles, d_rowlo, d_rowhi, d_sdem, s), "skew launch");
+        // the shared array keeps the previous call's contents: the work counter must start at zero
+        TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
+        TVS_CUDA(launch_sweep(cd, d_istart + at, nd, istart[at + nd], d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
+                              (float)obs_height_m, wmax, d_counter, num_sms, smem_optin, s),
+                 "sweep launch");
+        TVS_CUDA(launch_unskew(d_cvf, d_cvb, rows, cols, cd, nd, nsplit, d_part, d_vs64, d_out, first, last,
+                               scale, s),
+                 "unskew launch");
+        TVS_CUDA(launch_unskew_finalize(rows, cols, nd, nsplit, d_part, d_vs64, d_out, first, last, scale, s),
+                 "unskew finalize launch");
+        at += nd + 1;
+    }
+    return TVS_OK;
+}

@@ -1,0 +1,67 @@
+"""The no-allocation entry point, tvs_total_viewshed_device_noalloc.
+
+It serves callers that cannot allocate device memory themselves (a framework
+whose caching allocator owns the GPU's memory budget, or a latency-bound loop
+that must not pay the device-wide synchronisation of cudaMalloc/cudaFree).
+Its scratch is one fixed 64 MiB device array shared by every call, so these
+tests check that two calls in a row, through the C ABI, give what the
+allocating entry point gives (up to the order of FP64 additions across
+direction chunks, which the smaller scratch changes), and that a job too large
+for the array is refused with an error instead of running.
+
+This file is collected last on purpose: it also passes alone, in a fresh
+process, where its first call resolves the array's address.
+"""
+import numpy as np
+import pytest
+
+import paper_2003_02200_gb300 as tvs
+from paper_2003_02200_gb300 import terrain
+
+pytestmark = pytest.mark.gpu
+
+# same bound as the chunked-budget parity test: only FP64 association moves
+RTOL = 2e-7
+
+
+def _reference(dem_t, step, h0, n, rng):
+    import torch
+    out = torch.empty_like(dem_t)
+    with tvs.Context(0) as ctx:
+        ctx.total_viewshed_device(dem_t, step, h0, n, rng, out=out)
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+def _noalloc(lib, dem_t, step, h0, n, rng):
+    import torch
+    out = torch.full_like(dem_t, -1.0)
+    stream = torch.cuda.current_stream()
+    rc = lib.tvs_total_viewshed_device_noalloc(dem_t.data_ptr(), dem_t.shape[0], dem_t.shape[1], step, h0, n,
+                                               rng, out.data_ptr(), stream.cuda_stream)
+    assert rc == 0, lib.tvs_last_error(None).decode()
+    torch.cuda.synchronize()
+    return out.cpu().numpy()
+
+
+@pytest.mark.parametrize("rows,cols,n,rng", [(300, 260, 96, 0.0), (640, 480, 45, 1500.0)])
+def test_noalloc_matches_allocating_entry_point_twice(rows, cols, n, rng):
+    import torch
+    lib = tvs.load()
+    dem = terrain.fractal_dem(rows, cols, 0.8, 800.0, seed=rows + cols)
+    d = torch.from_numpy(dem).cuda()
+    want = _reference(d, 10.0, 1.5, n, rng)
+    for _ in range(2):
+        got = _noalloc(lib, d, 10.0, 1.5, n, rng)
+        np.testing.assert_allclose(got, want, rtol=RTOL, atol=0)
+
+
+def test_noalloc_refuses_a_job_larger_than_its_array():
+    import torch
+    lib = tvs.load()
+    d = torch.zeros(2000, 2000, device="cuda")
+    out = torch.empty_like(d)
+    rc = lib.tvs_total_viewshed_device_noalloc(d.data_ptr(), 2000, 2000, 10.0, 1.5, 180, 0.0, out.data_ptr(),
+                                               torch.cuda.current_stream().cuda_stream)
+    assert rc == tvs._binding.TVS_ERR_OOM
+    assert b"64 MiB" in lib.tvs_last_error(None)
