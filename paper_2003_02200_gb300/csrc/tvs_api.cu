@@ -254,7 +254,7 @@ struct Chunk {
     size_t slab_elems;   // sum of R * Wp over the chunk
     long long rows;      // sum of R
     int items;           // sweep warp items
-    int max_R, max_tiles, wmax;
+    int max_R, max_tiles, wmax, dmax;
     double evals, skew_bytes, unskew_bytes, rowmap_bytes;
 };
 
@@ -321,7 +321,7 @@ int make_plan(int rows, int cols, double step, double max_range, int n, size_t a
         size_t off = 0;
         long long roff = 0;
         int items = 0;
-        c.max_R = 0; c.max_tiles = 0; c.wmax = 0;
+        c.max_R = 0; c.max_tiles = 0; c.wmax = 0; c.dmax = 0;
         c.evals = c.skew_bytes = c.unskew_bytes = c.rowmap_bytes = 0;
         for (int q = c.k0; q < c.k1; ++q) {
             const HostDir& d = plan->dirs[q];
@@ -342,6 +342,7 @@ int make_plan(int rows, int cols, double step, double max_range, int n, size_t a
             c.max_R = std::max(c.max_R, d.R);
             c.max_tiles = std::max(c.max_tiles, ((d.R + SKEW_TP - 1) / SKEW_TP) * ((d.W + SKEW_TJ - 1) / SKEW_TJ));
             c.wmax = std::max(c.wmax, d.W);
+            c.dmax = std::max(c.dmax, v.K);
             const DirWork w = direction_work(d);
             c.evals += (double)w.evals;
             c.skew_bytes += 4.0 * rows * cols + 4.0 * (double)w.samples;
@@ -501,7 +502,7 @@ int run_job(tvs_ctx* h, const float* d_dem, int rows, int cols, double step, dou
         {
             Timer t(h, K_SWEEP, s, c.evals);
             TVS_CUDA(launch_sweep(cd, c_istart, nd, c_items, d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb, h0f,
-                                  c.wmax, d_counter, h->num_sms, h->smem_optin, s),
+                                  c.wmax, c.dmax, d_counter, h->num_sms, h->smem_optin, s),
                      "sweep launch");
         }
         {
@@ -725,7 +726,7 @@ int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, d
     TVS_CUDA(launch_skew(d_dem, rows, cols, d_dir, 1, c.max_tiles, d_lo, d_hi, d_s, s), "skew launch");
     TVS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), s), "reset work counter");
     TVS_CUDA(launch_sweep(d_dir, d_is, 1, is_host[1], d_s, d_lo, d_hi, d_cv, d_cb, (float)obs_height_m, v.W,
-                          d_cnt, h->num_sms, h->smem_optin, s),
+                          v.K, d_cnt, h->num_sms, h->smem_optin, s),
              "sweep launch");
     std::vector<int> slab(c.slab_elems), slabb(c.slab_elems), lo(v.R), hi(v.R);
     TVS_CUDA(cudaMemcpyAsync(slab.data(), d_cv, c.slab_elems * 4, cudaMemcpyDeviceToHost, s), "copy cv");
@@ -909,8 +910,9 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     int at = 0;
     for (int c = 0; c < nchunks; ++c) {
         const int k0 = chunk_k0[c], nd = chunk_k0[c + 1] - k0;
-        int max_R = 0, max_tiles = 0, wmax = 0;
+        int max_R = 0, max_tiles = 0, wmax = 0, dmax = 0;
         for (int q = k0; q < k0 + nd; ++q) {
+            dmax = std::max(dmax, dirs[q].K);
             max_R = std::max(max_R, dirs[q].R);
             max_tiles = std::max(max_tiles, ((dirs[q].R + SKEW_TP - 1) / SKEW_TP) * ((dirs[q].W + SKEW_TJ - 1) / SKEW_TJ));
             wmax = std::max(wmax, dirs[q].W);
@@ -922,7 +924,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
         // the shared array keeps the previous call's contents: the work counter must start at zero
         TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
         TVS_CUDA(launch_sweep(cd, d_istart + at, nd, istart[at + nd], d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                              (float)obs_height_m, wmax, d_counter, num_sms, smem_optin, s),
+                              (float)obs_height_m, wmax, dmax, d_counter, num_sms, smem_optin, s),
                  "sweep launch");
         TVS_CUDA(launch_unskew(d_cvf, d_cvb, rows, cols, cd, nd, nsplit, d_part, d_vs64, d_out, first, last,
                                scale, s),

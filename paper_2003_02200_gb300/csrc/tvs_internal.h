@@ -56,7 +56,7 @@ cudaError_t launch_skew(const float* dem, int rows, int cols, const DirDev* d_di
                         cudaStream_t stream);
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
-                         float h0, int wmax, unsigned* counter, int num_sms, int smem_optin,
+                         float h0, int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin,
                          cudaStream_t stream);
 // Number of direction ranges the unskew splits a chunk into for a DEM of this
 // size (1 for DEMs with enough cell tiles to fill the GPU).

@@ -166,7 +166,7 @@ struct SweepParams {
     unsigned* counter;
     int ndir;
     int total_items;
-    int inv_len;     // entries of the duplicated 1/d table (float2 each, multiple of 2)
+    int inv_len;     // entries of the per-distance table (float4 each)
     int istart_len;  // ints of the item-start table (multiple of 4)
     int half;        // floats of one staged row (multiple of 4)
     float h0;
@@ -185,21 +185,22 @@ __device__ __forceinline__ float fset_gt(float a, float b)
 // precision, it is visible iff that slope is strictly above the running
 // maximum M_q, and a visible target adds 2d + 1 to the POV's measure.  Two
 // POVs share one packed multiply and one packed accumulate; the comparison and
-// the maximum are scalar.  `cpair` holds 2d + 1 of the first step (or zero for
-// steps a range-limited walk must not count, see sweep_lane).
+// the maximum are scalar.  tab[e + u] holds (1/d, 1/d, 2d + 1, 2d + 1); a
+// range-limited walk's last block counts only its first `nvalid` steps.
 template <int P, int U, bool MASKED>
-__device__ __forceinline__ void sweep_block(const float* w, const float2* iv2, const float* h, float* M,
-                                            float2* acc2, float cb, int nvalid)
+__device__ __forceinline__ void sweep_block(const float* w, const float4* __restrict__ tab, const float* h,
+                                            float* M, float2* acc2, int nvalid)
 {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        float c = cb + 2.0f * (float)u;
-        if (MASKED) c = u < nvalid ? c : 0.0f;
-        const float2 cpair = make_float2(c, c);
+        const float4 t4 = tab[u];
+        const float2 iv = make_float2(t4.x, t4.y);
+        float2 cpair = make_float2(t4.z, t4.w);
+        if (MASKED && u >= nvalid) cpair = make_float2(0.f, 0.f);
 #pragma unroll
         for (int q = 0; q < P; q += 2) {
             const float2 d = make_float2(__fsub_rn(w[q + u + 1], h[q]), __fsub_rn(w[q + u + 2], h[q + 1]));
-            const float2 t = __fmul2_rn(d, iv2[u]);
+            const float2 t = __fmul2_rn(d, iv);
             const float2 v = make_float2(fset_gt(t.x, M[q]), fset_gt(t.y, M[q + 1]));
             acc2[q / 2] = __ffma2_rn(v, cpair, acc2[q / 2]);
             M[q] = fmaxf(M[q], t.x);
@@ -218,7 +219,7 @@ __device__ __forceinline__ void sweep_block(const float* w, const float2* iv2, c
 // sum of d^2 - open^2 over its closed segments plus the segment still open at
 // the end (closed at the last target).
 template <int P, int U>
-__device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const float2* __restrict__ inv2,
+__device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const float4* __restrict__ tab,
                                            int* __restrict__ cvrow, int L, int slot, int K, float h0, bool rev)
 {
     const float NEG = neg_inf();
@@ -266,18 +267,10 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
             const float4 v = *reinterpret_cast<const float4*>(base + m);
             w[m] = v.x; w[m + 1] = v.y; w[m + 2] = v.z; w[m + 3] = v.w;
         }
-        float2 iv2[U];
-#pragma unroll
-        for (int u = 0; u < U; u += 2) {
-            const float4 v = *reinterpret_cast<const float4*>(inv2 + e + u);
-            iv2[u] = make_float2(v.x, v.y);
-            iv2[u + 1] = make_float2(v.z, v.w);
-        }
-        const float cb = (float)(2 * e + 3);   // 2d + 1 at d = e + 1
         if (klimited && e + U > dlim)
-            sweep_block<P, U, true>(w, iv2, h, M, acc2, cb, dlim - e);
+            sweep_block<P, U, true>(w, tab + e, h, M, acc2, dlim - e);
         else
-            sweep_block<P, U, false>(w, iv2, h, M, acc2, cb, U);
+            sweep_block<P, U, false>(w, tab + e, h, M, acc2, U);
         e += U;
     }
     // group 0 ends in `first` when a second group ran, else in acc2
@@ -308,13 +301,15 @@ template <int P, int U>
 __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepParams sp)
 {
     extern __shared__ __align__(16) float smem[];
-    float2* inv2 = reinterpret_cast<float2*>(smem);
-    int* istart = reinterpret_cast<int*>(smem + 2 * sp.inv_len);
+    float4* tab = reinterpret_cast<float4*>(smem);
+    int* istart = reinterpret_cast<int*>(smem + 4 * sp.inv_len);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* F = smem + 2 * sp.inv_len + sp.istart_len + warp * sp.half;
+    float* F = smem + 4 * sp.inv_len + sp.istart_len + warp * sp.half;
+    // per distance d = m + 1: (1/d, 1/d, 2d + 1, 2d + 1); 1/d correctly rounded
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
         const float r = __frcp_rn((float)(m + 1));
-        inv2[m] = make_float2(r, r);
+        const float c = (float)(2 * m + 3);
+        tab[m] = make_float4(r, r, c, c);
     }
     for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
     __syncthreads();
@@ -350,7 +345,7 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
         }
         for (int m = lane; m < ROW_PADR; m += 32) F[ROW_PADL + L + m] = NEG;
         __syncwarp();
-        sweep_lane<P, U>(F, inv2, (rev ? sp.cv_bwd : sp.cv_fwd) + rowbase, L, c * 32 + lane, d.K, sp.h0, rev);
+        sweep_lane<P, U>(F, tab, (rev ? sp.cv_bwd : sp.cv_fwd) + rowbase, L, c * 32 + lane, d.K, sp.h0, rev);
     }
 }
 
@@ -518,7 +513,7 @@ cudaError_t launch_skew(const float* dem, int rows, int cols, const DirDev* d_di
 
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
-                         float h0, int wmax, unsigned* counter, int num_sms, int smem_optin,
+                         float h0, int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin,
                          cudaStream_t stream)
 {
     if (ndir <= 0 || total_items <= 0) return cudaSuccess;
@@ -527,11 +522,12 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
     sp.dirs = d_dirs; sp.item_start = d_item_start; sp.sdem = sdem; sp.rowlo = rowlo;
     sp.rowhi = rowhi; sp.cv_fwd = cv_fwd; sp.cv_bwd = cv_bwd; sp.counter = counter; sp.ndir = ndir;
     sp.total_items = total_items; sp.h0 = h0;
-    // 1/d is read up to d = wmax + U (a walk of at most wmax - 2 steps, rounded up to U)
-    sp.inv_len = (wmax + 2 * U + 8 + 1) & ~1;
+    // the distance table is read up to d = dmax + U (a walk of at most
+    // min(K, W) - 1 steps, rounded up to U); dmax <= wmax
+    sp.inv_len = (std::min(dmax, wmax) + 2 * U + 8 + 1) & ~1;
     sp.istart_len = (ndir + 1 + 3) & ~3;
     sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
-    const size_t fixed = (size_t)(2 * sp.inv_len + sp.istart_len) * 4;
+    const size_t fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
     const size_t per_warp = (size_t)sp.half * 4;
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
     // As many resident warps as shared memory and registers allow, in one CTA per SM
