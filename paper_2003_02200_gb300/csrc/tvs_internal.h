@@ -8,11 +8,21 @@ namespace tvs {
 
 // Warp work item of the sweep: 32 lanes x POVS_PER_LANE consecutive samples.
 // Each lane walks two groups of POVS_PER_LANE consecutive samples (a group and
-// its mirror), so a warp item covers 64 groups of one skewed row.
-constexpr int POVS_PER_LANE = 4;
-constexpr int SWEEP_UNROLL = 16;
+// its mirror), so a warp item covers 64 groups of one skewed row.  The tile
+// constants can be set at compile time (-DTVS_POVS_PER_LANE=8, ...).
+#ifndef TVS_POVS_PER_LANE
+#define TVS_POVS_PER_LANE 8
+#endif
+#ifndef TVS_SWEEP_UNROLL
+#define TVS_SWEEP_UNROLL 24
+#endif
+#ifndef TVS_SWEEP_MAX_WARPS
+#define TVS_SWEEP_MAX_WARPS 16
+#endif
+constexpr int POVS_PER_LANE = TVS_POVS_PER_LANE;
+constexpr int SWEEP_UNROLL = TVS_SWEEP_UNROLL;
 constexpr int WARP_POVS = 64 * POVS_PER_LANE;
-constexpr int SWEEP_MAX_WARPS = 20;
+constexpr int SWEEP_MAX_WARPS = TVS_SWEEP_MAX_WARPS;
 // Left pad of a staged row (floats); a multiple of 4.
 constexpr int ROW_PADL = 16;
 // Right pad: the last window of a block reads up to P + U floats past a target.

@@ -297,6 +297,49 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
     }
 }
 
+// A sweep work item: (direction, skewed row, chunk of lane slots, walk direction).
+struct ItemRow {
+    long long rowbase;   // slab offset of the row's first usable sample
+    int L, c, K;
+    bool rev;
+};
+
+// Decodes item into its row; false when the chunk has no used lane slot.
+template <int P>
+__device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* istart, int item, ItemRow* it)
+{
+    int lo = 0, hi = sp.ndir - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (istart[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const DirDev& d = sp.dirs[lo];
+    const int rem = item - istart[lo];
+    const int per_row = 2 * d.chunks;
+    const int p = rem / per_row;
+    const int r2 = rem - p * per_row;
+    it->rev = (r2 & 1) != 0;
+    it->c = r2 >> 1;
+    const int jlo = sp.rowlo[d.row_off + p], jhi = sp.rowhi[d.row_off + p];
+    it->L = jhi - jlo + 1;
+    it->K = d.K;
+    it->rowbase = d.slab + (long long)p * d.Wp + jlo;
+    const int G = (it->L + P - 1) / P;
+    return it->L > 0 && it->c * 32 < (G + 1) / 2;
+}
+
+// L2 prefetch of the n floats at p with one bulk request: start rounded down
+// and end rounded up to 16 bytes, which stays inside the row's slab (rows
+// start 16-byte aligned and are padded to a multiple of 4 floats).
+__device__ __forceinline__ void prefetch_row_l2(const float* p, int n)
+{
+    const unsigned long long a = reinterpret_cast<unsigned long long>(p) & ~15ull;
+    const unsigned long long end = (reinterpret_cast<unsigned long long>(p + n) + 15ull) & ~15ull;
+    const unsigned size = (unsigned)(end - a);
+    if (size == 0) return;
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(a), "r"(size) : "memory");
+}
+
 template <int P, int U>
 __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepParams sp)
 {
@@ -315,37 +358,50 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
     __syncthreads();
     const float NEG = neg_inf();
 
+    // Lane 0 claims the next item while the warp works on the current one and
+    // prefetches that item's skewed row into L2 (the slabs do not fit L2, so
+    // otherwise every row is staged from HBM at the start of its item).
+    int next = 0;
+    if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
+    next = __shfl_sync(0xffffffffu, next, 0);
     for (;;) {
-        int item = 0;
-        if (lane == 0) item = (int)atomicAdd(sp.counter, 1u);
-        item = __shfl_sync(0xffffffffu, item, 0);
+        const int item = next;
         if (item >= sp.total_items) break;
-        int lo = 0, hi = sp.ndir - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (istart[mid] <= item) lo = mid; else hi = mid - 1;
+        ItemRow it;
+        if (!decode_item<P>(sp, istart, item, &it)) {
+            if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
+            next = __shfl_sync(0xffffffffu, next, 0);
+            continue;
         }
-        const DirDev& d = sp.dirs[lo];
-        const int rem = item - istart[lo];
-        const int per_row = 2 * d.chunks;
-        const int p = rem / per_row;
-        const int r2 = rem - p * per_row;
-        const bool rev = (r2 & 1) != 0;
-        const int c = r2 >> 1;
-        const int jlo = sp.rowlo[d.row_off + p], jhi = sp.rowhi[d.row_off + p];
-        const int L = jhi - jlo + 1;
-        const int G = (L + P - 1) / P;
-        if (c * 32 >= (G + 1) / 2) continue;           // no slot of this chunk is used
-        const long long rowbase = d.slab + (long long)p * d.Wp + jlo;
-        const float* zrow = sp.sdem + rowbase;
+        const float* zrow = sp.sdem + it.rowbase;
+        const int L = it.L;
         __syncwarp();
-        for (int x = lane; x < L; x += 32) {
-            const float v = rev ? zrow[L - 1 - x] : zrow[x];
-            F[ROW_PADL + x] = (x == L - 1) ? NEG : v;
+        // stage the row (or the reversed row): batches of loads, then stores
+        constexpr int B = 8;
+        for (int x0 = lane; x0 < L; x0 += 32 * B) {
+            float v[B];
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int x = x0 + 32 * b;
+                v[b] = x < L ? (it.rev ? zrow[L - 1 - x] : zrow[x]) : 0.f;
+            }
+#pragma unroll
+            for (int b = 0; b < B; ++b) {
+                const int x = x0 + 32 * b;
+                if (x < L) F[ROW_PADL + x] = (x == L - 1) ? NEG : v[b];
+            }
         }
         for (int m = lane; m < ROW_PADR; m += 32) F[ROW_PADL + L + m] = NEG;
-        __syncwarp();
-        sweep_lane<P, U>(F, tab, (rev ? sp.cv_bwd : sp.cv_fwd) + rowbase, L, c * 32 + lane, d.K, sp.h0, rev);
+        if (lane == 0) {
+            next = (int)atomicAdd(sp.counter, 1u);
+            ItemRow nx;
+            if (next < sp.total_items && decode_item<P>(sp, istart, next, &nx))
+                prefetch_row_l2(sp.sdem + nx.rowbase, nx.L);
+        }
+        next = __shfl_sync(0xffffffffu, next, 0);
+        __syncwarp();   // the staged row is visible to every lane
+        sweep_lane<P, U>(F, tab, (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase, L, it.c * 32 + lane, it.K,
+                         sp.h0, it.rev);
     }
 }
 
