@@ -134,6 +134,78 @@ int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, int cols, do
                                       double obs_height_m, int n_sectors, double max_range_m, float* d_out,
                                       void* cuda_stream);
 
+/* One DEM of a batch: device buffers of rows*cols float32 each (they may not
+ * overlap) and the same parameters as tvs_total_viewshed_device. */
+typedef struct {
+    const float* d_dem;
+    float* d_out;
+    int rows, cols;
+    double step_m;
+    double obs_height_m;
+    int n_sectors;
+    double max_range_m;
+} tvs_job;
+
+/* Total viewsheds of njobs DEMs of any sizes and parameters in one pass
+ * (section 4.1 applied to each DEM): the (DEM, direction) pairs of all jobs are
+ * planned together into chunks that fit the handle's HBM budget, and each chunk
+ * runs one launch per kernel for all of its DEMs, so small DEMs share the GPU
+ * instead of running one after another.  Each job's result equals what
+ * tvs_total_viewshed_device gives for it, up to the order of FP64 additions
+ * across chunks.  Stream-ordered like tvs_total_viewshed_device.
+ * Errors: TVS_ERR_ARG (a bad job: the message names its index), TVS_ERR_OOM,
+ * TVS_ERR_CUDA. */
+int tvs_total_viewshed_batch(tvs_handle h, const tvs_job* jobs, int njobs, void* cuda_stream);
+
+/* A prepared batch: the plan of a fixed set of jobs (same buffers, same
+ * parameters every time), its own device scratch (hbm_budget_bytes, 0 = the
+ * handle's budget), its tables uploaded once, and its launch sequence captured
+ * once in a CUDA graph.  tvs_batch_launch replays the graph on a stream; the
+ * caller may change the contents of the jobs' d_dem between launches, not the
+ * pointers or parameters.  Launches of one prepared batch must not overlap on
+ * the GPU (they share its scratch).  tvs_batch_destroy is NULL-safe. */
+typedef struct tvs_batch* tvs_batch_handle;
+
+typedef struct {
+    int32_t  jobs;
+    int32_t  chunks;            /* chunks of (DEM, direction) pairs */
+    int32_t  kernels_per_launch;
+    int32_t  pad_;
+    double   evals;             /* evaluations of one launch (the work count) */
+    double   scratch_bytes;
+} tvs_batch_info;
+
+int tvs_batch_create(tvs_handle h, const tvs_job* jobs, int njobs, size_t hbm_budget_bytes,
+                     tvs_batch_handle* out);
+int tvs_batch_launch(tvs_batch_handle b, void* cuda_stream);
+int tvs_batch_get_info(tvs_batch_handle b, tvs_batch_info* info);
+void tvs_batch_destroy(tvs_batch_handle b);
+
+/* Launch choices of a handle (no effect on results, only on speed).
+ * small_pov_below_w: skewed rows of directions whose walk axis is shorter
+ *   than this are swept with 4 POVs per lane group, longer ones with 8
+ *   (default 768);
+ * sweep_max_warps: warps per sweep CTA, 0 = as many as shared memory allows,
+ *   at most 16 (default 0);
+ * unskew_ctas_per_sm: a chunk whose DEMs have fewer cell tiles than this many
+ *   per SM splits its directions into ranges across CTAs (default 2). */
+typedef struct {
+    int32_t small_pov_below_w;
+    int32_t sweep_max_warps;
+    int32_t unskew_ctas_per_sm;
+    int32_t pad_;
+} tvs_tuning;
+
+int tvs_get_tuning(tvs_handle h, tvs_tuning* t);
+int tvs_set_tuning(tvs_handle h, const tvs_tuning* t);
+
+/* Autotuner: times candidate tunings on the caller's jobs (each candidate
+ * runs the whole batch once to warm up and once timed with CUDA events on the
+ * handle's stream), searching one choice at a time, keeps the fastest in the
+ * handle and returns it in *best and its batch time in *best_ms (both
+ * optional).  The jobs' outputs are overwritten.  Synchronous. */
+int tvs_autotune(tvs_handle h, const tvs_job* jobs, int njobs, tvs_tuning* best, double* best_ms);
+
 /* Direction table entry k of n for a rows x cols DEM (host only, no GPU). */
 int tvs_direction(int n_sectors, int k, int rows, int cols, double step_m, double max_range_m,
                   tvs_direction_info* info);

@@ -36,6 +36,22 @@ class DirectionInfo(C.Structure):
                 ("g", C.c_double), ("K", C.c_int64)]
 
 
+class TvsJob(C.Structure):
+    _fields_ = [("d_dem", C.c_void_p), ("d_out", C.c_void_p), ("rows", C.c_int), ("cols", C.c_int),
+                ("step_m", C.c_double), ("obs_height_m", C.c_double), ("n_sectors", C.c_int),
+                ("max_range_m", C.c_double)]
+
+
+class BatchInfo(C.Structure):
+    _fields_ = [("jobs", C.c_int32), ("chunks", C.c_int32), ("kernels_per_launch", C.c_int32),
+                ("pad_", C.c_int32), ("evals", C.c_double), ("scratch_bytes", C.c_double)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("small_pov_below_w", C.c_int32), ("sweep_max_warps", C.c_int32),
+                ("unskew_ctas_per_sm", C.c_int32), ("pad_", C.c_int32)]
+
+
 class KernelStats(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
                 ("units", C.c_double), ("unit", C.c_char * 16)]
@@ -77,6 +93,14 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                            C.c_double, vp, vp], C.c_int),
             "tvs_total_viewshed_device_noalloc": ([vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                                    C.c_double, vp, vp], C.c_int),
+            "tvs_total_viewshed_batch": ([vp, C.POINTER(TvsJob), C.c_int, vp], C.c_int),
+            "tvs_batch_create": ([vp, C.POINTER(TvsJob), C.c_int, C.c_size_t, C.POINTER(vp)], C.c_int),
+            "tvs_batch_launch": ([vp, vp], C.c_int),
+            "tvs_batch_get_info": ([vp, C.POINTER(BatchInfo)], C.c_int),
+            "tvs_batch_destroy": ([vp], None),
+            "tvs_get_tuning": ([vp, C.POINTER(Tuning)], C.c_int),
+            "tvs_set_tuning": ([vp, C.POINTER(Tuning)], C.c_int),
+            "tvs_autotune": ([vp, C.POINTER(TvsJob), C.c_int, C.POINTER(Tuning), C.POINTER(C.c_double)], C.c_int),
             "tvs_direction": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                C.POINTER(DirectionInfo)], C.c_int),
             "tvs_count_evals": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double], C.c_int64),
@@ -143,6 +167,59 @@ def total_viewshed_device_noalloc(dem, step_m: float, obs_height_m: float, n_sec
     return out
 
 
+def _job_array(jobs):
+    """jobs: sequence of dicts with torch CUDA tensors dem, out and step_m,
+    obs_height_m, n_sectors, max_range_m (defaults 180 directions, unlimited)."""
+    import torch
+    arr = (TvsJob * len(jobs))()
+    for i, j in enumerate(jobs):
+        dem, out = j["dem"], j["out"]
+        for t in (dem, out):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32 and t.dim() == 2
+                    and t.is_contiguous()):
+                raise ValueError(f"job {i}: dem and out must be contiguous 2-D float32 CUDA tensors")
+        if out.shape != dem.shape:
+            raise ValueError(f"job {i}: out must be shaped like dem")
+        arr[i] = TvsJob(dem.data_ptr(), out.data_ptr(), dem.shape[0], dem.shape[1], float(j["step_m"]),
+                        float(j["obs_height_m"]), int(j.get("n_sectors", 180)), float(j.get("max_range_m", 0.0)))
+    return arr
+
+
+class Batch:
+    """A prepared batch (tvs_batch_create): fixed jobs, own scratch, launch
+    sequence captured once in a CUDA graph and replayed by launch()."""
+
+    def __init__(self, ctx: "Context", jobs, hbm_budget_bytes: int = 0):
+        self._lib = load()
+        self._jobs = list(jobs)          # keeps the tensors alive
+        arr = _job_array(self._jobs)
+        h = C.c_void_p()
+        _check(self._lib.tvs_batch_create(ctx.handle, arr, len(arr), hbm_budget_bytes, C.byref(h)))
+        self._b = h
+
+    def launch(self, stream=None) -> None:
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(self._lib.tvs_batch_launch(self._b, stream.cuda_stream))
+
+    def info(self) -> dict:
+        i = BatchInfo()
+        _check(self._lib.tvs_batch_get_info(self._b, C.byref(i)))
+        return {f: getattr(i, f) for f, _ in BatchInfo._fields_ if f != "pad_"}
+
+    def close(self) -> None:
+        if getattr(self, "_b", None):
+            self._lib.tvs_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Context:
     """A library handle bound to one CUDA device (tvs_create / tvs_destroy)."""
 
@@ -206,6 +283,36 @@ class Context:
                                                    step_m, obs_height_m, n_sectors, max_range_m,
                                                    out.data_ptr(), stream.cuda_stream))
         return out
+
+    def total_viewshed_batch(self, jobs, stream=None) -> None:
+        """tvs_total_viewshed_batch: jobs as for Batch; results land in each job's out."""
+        import torch
+        arr = _job_array(jobs)
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        _check(self._lib.tvs_total_viewshed_batch(self.handle, arr, len(arr), stream.cuda_stream))
+
+    def get_tuning(self) -> dict:
+        t = Tuning()
+        _check(self._lib.tvs_get_tuning(self.handle, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "pad_"}
+
+    def set_tuning(self, **kw) -> None:
+        cur = self.get_tuning()
+        cur.update(kw)
+        t = Tuning(cur["small_pov_below_w"], cur["sweep_max_warps"], cur["unskew_ctas_per_sm"], 0)
+        _check(self._lib.tvs_set_tuning(self.handle, C.byref(t)))
+
+    def autotune(self, jobs) -> tuple[dict, float]:
+        """tvs_autotune on the given jobs; returns (best tuning, best batch ms)."""
+        arr = _job_array(jobs)
+        t = Tuning()
+        ms = C.c_double(0.0)
+        _check(self._lib.tvs_autotune(self.handle, arr, len(arr), C.byref(t), C.byref(ms)))
+        return {f: getattr(t, f) for f, _ in Tuning._fields_ if f != "pad_"}, ms.value
+
+    def prepare_batch(self, jobs, hbm_budget_bytes: int = 0) -> Batch:
+        return Batch(self, jobs, hbm_budget_bytes)
 
     def debug_rowmap(self, rows: int, cols: int, n_sectors: int, k: int) -> dict:
         big = max(rows, cols)

@@ -102,14 +102,6 @@ void host_row_range(const HostDir& d, int p, int* lo, int* hi)
     *hi = (int)h;
 }
 
-// Warp items per skewed row and walk direction: a row of W samples has
-// ceil(W / P) groups, paired into ceil(groups / 2) lane slots, 32 per item.
-int sweep_chunks(int W)
-{
-    const int groups = (W + POVS_PER_LANE - 1) / POVS_PER_LANE;
-    return ((groups + 1) / 2 + 31) / 32;
-}
-
 long long sum_min(long long L, long long K)
 {
     // sum_{x=0}^{L-1} min(x, K)
@@ -155,6 +147,15 @@ enum KernelId { K_ROWMAP = 0, K_SKEW, K_SWEEP, K_UNSKEW, K_FINAL, K_COUNT };
 const char* kKernelName[K_COUNT] = {"rowmap", "skew", "sweep", "unskew", "unskew_finalize"};
 const char* kKernelUnit[K_COUNT] = {"bytes", "bytes", "evals", "bytes", "bytes"};
 
+// Tunable launch choices (see tvs_tuning in tvs.h).
+struct Tuning {
+    int small_pov_below_w = 768;   // walk axes shorter than this use SMALL_POV groups
+    int sweep_max_warps = 0;       // 0 = as many as shared memory allows (up to SWEEP_MAX_WARPS)
+    int unskew_ctas_per_sm = 2;    // split a chunk's directions below this many unskew CTAs per SM
+};
+
+int pov_for(const Tuning& tn, int W) { return W < tn.small_pov_below_w ? SMALL_POV : LARGE_POV; }
+
 struct Pending {
     int kernel;
     cudaEvent_t start, stop;
@@ -174,6 +175,7 @@ struct tvs_ctx {
     char* pinned = nullptr;          // pinned staging of the per-call table upload
     size_t pinned_bytes = 0;
     cudaEvent_t pinned_done = nullptr;  // the last upload from `pinned` has been read
+    Tuning tuning;
     bool profiling = false;
     std::vector<Pending> pending;
     tvs_kernel_stats stats[K_COUNT];
@@ -189,7 +191,7 @@ struct Timer {
     cudaEvent_t a = nullptr, b = nullptr;
     Timer(tvs_ctx* h_, int k, cudaStream_t s_, double u) : h(h_), kernel(k), s(s_), units(u)
     {
-        if (h->profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
+        if (h && h->profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
             cudaEventRecord(a, s);
     }
     ~Timer()
@@ -248,84 +250,133 @@ int ensure_scratch(tvs_ctx* h, size_t bytes)
     return TVS_OK;
 }
 
-// One planned chunk of directions [k0, k1).
+// A DEM of a call: device pointers and parameters.
+struct JobSpec {
+    const float* dem;
+    float* out;
+    int rows, cols, n;
+    double step, h0, max_range;
+};
+
+// A planned chunk: the consecutive (job, direction) instances [i0, i1).
 struct Chunk {
-    int k0, k1;
-    size_t slab_elems;   // sum of R * Wp over the chunk
-    long long rows;      // sum of R
-    int items;           // sweep warp items
+    int i0, i1;
+    size_t slab_elems;       // sum of R * Wp over the chunk
+    long long rows;          // sum of R
+    int items;               // sweep warp items
     int max_R, max_tiles, wmax, dmax;
-    double evals, skew_bytes, unskew_bytes, rowmap_bytes;
+    int cj_beg, ncj;         // the chunk's entries of the chunk-job table
+    int total_tiles, max_split;
+    long long total_cells, part_elems;
+    int istart_at;           // offset of the chunk's item table
+    double evals, skew_bytes, unskew_bytes, rowmap_bytes, final_bytes;
 };
 
-struct Plan {
-    std::vector<HostDir> dirs;
-    std::vector<DirDev> dev;        // per direction, slab / row offsets relative to its chunk
+struct BatchPlan {
+    std::vector<JobSpec> jobs;
+    std::vector<int> inst_job, inst_k;   // per instance
+    std::vector<HostDir> hdirs;          // per instance
+    std::vector<DirDev> dirs;            // per instance (slab / row offsets relative to its chunk)
     std::vector<Chunk> chunks;
-    size_t max_slab = 0;            // largest chunk slab (elements)
-    long long max_rows = 0;         // largest chunk row count
-    int max_items1 = 0;             // largest chunk direction count + 1
-    int istart_total = 0;           // sum over chunks of (directions + 1)
+    std::vector<ChunkJob> cj;            // every chunk's job entries, chunk after chunk
+    std::vector<int> istart;             // every chunk's item table
+    std::vector<long long> vs64_off;     // per job, -1 when the job lives in one chunk
+    long long vs64_elems = 0;
+    size_t max_slab = 0;
+    long long max_rows = 0, max_part = 0;
+    double evals = 0;
 };
 
-size_t chunk_bytes(size_t slab, long long rows, int ndir)
+size_t chunk_bytes(size_t slab, long long rows, int ninst)
 {
     // skewed heights + forward measures + backward measures, row tables, item table
-    return align256(slab * 4) * 3 + align256((size_t)rows * 4) * 2 + align256((size_t)(ndir + 1) * 4);
+    return align256(slab * 4) * 3 + align256((size_t)rows * 4) * 2 + align256((size_t)(ninst + 1) * 4);
 }
 
-// Split the n directions into consecutive chunks whose scratch fits `avail`
-// bytes; chunk sizes are kept multiples of FP32_GROUP so that the FP32 group
-// sums (and so the result bits) do not depend on the chunking.
-int make_plan(int rows, int cols, double step, double max_range, int n, size_t avail, Plan* plan,
-              int only_k = -1)
+// Upper bound of the FP64 partials of a split unskew: splits only happen when
+// a chunk's jobs have fewer than 2 cell tiles per SM, so the partials cover at
+// most about 4 tiles of 1024 cells per SM.
+size_t part_bound(int num_sms) { return align256((size_t)(4 * num_sms + 4) * UNSKEW_TI * UNSKEW_TJ * 8); }
+
+// Plans the instances of `jobs` (job after job, directions in order) into
+// chunks whose scratch fits `avail` bytes.  Cuts fall on multiples of
+// FP32_GROUP directions of a job where possible, so a job's FP32 group sums do
+// not depend on the chunking.  only_k >= 0 keeps only direction only_k of a
+// single job (test hook).
+int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, const Tuning& tn, BatchPlan* plan,
+               int only_k = -1)
 {
-    plan->dirs.resize(n);
-    plan->dev.resize(n);
-    for (int k = 0; k < n; ++k) {
-        int rc = make_direction(n, k, rows, cols, step, max_range, &plan->dirs[k]);
-        if (rc) return fail(rc, "bad direction arguments");
+    plan->jobs = jobs;
+    for (int j = 0; j < (int)jobs.size(); ++j) {
+        const JobSpec& J = jobs[j];
+        for (int k = 0; k < J.n; ++k) {
+            if (only_k >= 0 && k != only_k) continue;
+            HostDir d;
+            if (make_direction(J.n, k, J.rows, J.cols, J.step, J.max_range, &d))
+                return fail(TVS_ERR_ARG, "bad direction arguments");
+            plan->hdirs.push_back(d);
+            plan->inst_job.push_back(j);
+            plan->inst_k.push_back(k);
+        }
     }
-    int k = only_k >= 0 ? only_k : 0;
-    const int kend = only_k >= 0 ? only_k + 1 : n;
-    while (k < kend) {
-        Chunk c{};
-        c.k0 = k;
-        size_t slab = 0;
-        long long nrows = 0;
-        int kk = k;
-        int last_ok = -1;
-        long long items_acc = 0;
-        size_t slab_ok = 0;
-        long long rows_ok = 0;
-        while (kk < kend) {
-            const HostDir& d = plan->dirs[kk];
+    const int ninst = (int)plan->hdirs.size();
+    plan->dirs.resize(ninst);
+    int i = 0;
+    while (i < ninst) {
+        size_t slab = 0, slab_ok = 0;
+        long long nrows = 0, rows_ok = 0, items = 0;
+        int ii = i, last_ok = -1;
+        while (ii < ninst) {
+            const HostDir& d = plan->hdirs[ii];
             const size_t wp = (size_t)((d.W + 3) & ~3);
             const size_t s2 = slab + (size_t)d.R * wp;
             const long long r2 = nrows + d.R;
-            const long long it2 = items_acc + 2LL * d.R * sweep_chunks(d.W);
-            if (kk > k && (chunk_bytes(s2, r2, kk - k + 1) > avail || kk - k >= kMaxChunkDirs ||
+            const long long it2 = items + 2LL * d.R * sweep_chunks(d.W, pov_for(tn, d.W));
+            if (ii > i && (chunk_bytes(s2, r2, ii - i + 1) > avail || ii - i >= kMaxChunkDirs ||
                            it2 > kMaxChunkItems))
                 break;
-            items_acc = it2;
             slab = s2;
             nrows = r2;
-            ++kk;
-            if ((kk - k) % FP32_GROUP == 0 || kk == kend) { last_ok = kk; slab_ok = slab; rows_ok = nrows; }
+            items = it2;
+            ++ii;
+            const int kk = plan->inst_k[ii - 1], jj = plan->inst_job[ii - 1];
+            if ((kk + 1) % FP32_GROUP == 0 || kk + 1 == jobs[jj].n || ii == ninst) {
+                last_ok = ii; slab_ok = slab; rows_ok = nrows;
+            }
         }
-        if (kk == k) return fail(TVS_ERR_OOM, "one direction does not fit the HBM budget");
-        if (chunk_bytes(slab, nrows, kk - k) > avail)
+        if (chunk_bytes(slab, nrows, ii - i) > avail)
             return fail(TVS_ERR_OOM, "one direction does not fit the HBM budget");
-        if (last_ok > k && kk < kend) { kk = last_ok; slab = slab_ok; nrows = rows_ok; }
-        c.k1 = kk;
+        if (last_ok > i && ii < ninst) { ii = last_ok; slab = slab_ok; nrows = rows_ok; }
+        Chunk c{};
+        c.i0 = i;
+        c.i1 = ii;
+        plan->chunks.push_back(c);
+        i = ii;
+    }
+    const int njobs = (int)jobs.size();
+    std::vector<int> first_chunk(njobs, -1), last_chunk(njobs, -1);
+    for (int q = 0; q < (int)plan->chunks.size(); ++q)
+        for (int t = plan->chunks[q].i0; t < plan->chunks[q].i1; ++t) {
+            const int j = plan->inst_job[t];
+            if (first_chunk[j] < 0) first_chunk[j] = q;
+            last_chunk[j] = q;
+        }
+    plan->vs64_off.assign(njobs, -1);
+    for (int j = 0; j < njobs; ++j)
+        if (first_chunk[j] >= 0 && first_chunk[j] != last_chunk[j]) {
+            plan->vs64_off[j] = plan->vs64_elems;
+            plan->vs64_elems += (long long)jobs[j].rows * jobs[j].cols;
+        }
+    for (int q = 0; q < (int)plan->chunks.size(); ++q) {
+        Chunk& c = plan->chunks[q];
         size_t off = 0;
         long long roff = 0;
-        int items = 0;
-        c.max_R = 0; c.max_tiles = 0; c.wmax = 0; c.dmax = 0;
-        c.evals = c.skew_bytes = c.unskew_bytes = c.rowmap_bytes = 0;
-        for (int q = c.k0; q < c.k1; ++q) {
-            const HostDir& d = plan->dirs[q];
-            DirDev& v = plan->dev[q];
+        c.istart_at = (int)plan->istart.size();
+        plan->istart.push_back(0);
+        for (int t = c.i0; t < c.i1; ++t) {
+            const HostDir& d = plan->hdirs[t];
+            const JobSpec& J = jobs[plan->inst_job[t]];
+            DirDev& v = plan->dirs[t];
             std::memset(&v, 0, sizeof(v));
             v.t_fx = d.t_fx;
             v.slab = (long long)off;
@@ -333,194 +384,239 @@ int make_plan(int rows, int cols, double step, double max_range, int n, size_t a
             v.D = d.D; v.R = d.R;
             v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
             v.row_off = (int)roff;
-            v.chunks = sweep_chunks(d.W);
-            v.gidx = q;
+            v.pov = pov_for(tn, d.W);
+            v.chunks = sweep_chunks(d.W, v.pov);
+            v.gidx = plan->inst_k[t];
+            v.job = plan->inst_job[t];
             v.g = (float)d.g;
+            v.h0 = (float)J.h0;
             off += (size_t)d.R * v.Wp;
             roff += d.R;
-            items += 2 * d.R * v.chunks;
+            c.items += 2 * d.R * v.chunks;
+            plan->istart.push_back(c.items);
             c.max_R = std::max(c.max_R, d.R);
             c.max_tiles = std::max(c.max_tiles, ((d.R + SKEW_TP - 1) / SKEW_TP) * ((d.W + SKEW_TJ - 1) / SKEW_TJ));
             c.wmax = std::max(c.wmax, d.W);
             c.dmax = std::max(c.dmax, v.K);
             const DirWork w = direction_work(d);
             c.evals += (double)w.evals;
-            c.skew_bytes += 4.0 * rows * cols + 4.0 * (double)w.samples;
-            c.unskew_bytes += 4.0 * (double)w.samples;
+            c.skew_bytes += 4.0 * J.rows * J.cols + 4.0 * (double)w.samples;
+            c.unskew_bytes += 8.0 * (double)w.samples;
             c.rowmap_bytes += 8.0 * d.R;
         }
         c.slab_elems = off;
         c.rows = roff;
-        c.items = items;
+        plan->evals += c.evals;
         plan->max_slab = std::max(plan->max_slab, off);
         plan->max_rows = std::max(plan->max_rows, roff);
-        plan->max_items1 = std::max(plan->max_items1, c.k1 - c.k0 + 1);
-        plan->istart_total += c.k1 - c.k0 + 1;
-        plan->chunks.push_back(c);
-        k = kk;
-    }
-    const size_t nch = plan->chunks.size();
-    for (size_t q = 0; q < nch; ++q) {
-        Chunk& c = plan->chunks[q];
-        const double cells = (double)rows * cols;
-        c.unskew_bytes += (q == 0 ? 0.0 : 8.0 * cells) + (q + 1 == nch ? 4.0 * cells : 8.0 * cells);
+        // the chunk's jobs, in instance order (a job's instances are contiguous)
+        c.cj_beg = (int)plan->cj.size();
+        long long tiles = 0;
+        for (int t = c.i0; t < c.i1;) {
+            int u = t;
+            while (u < c.i1 && plan->inst_job[u] == plan->inst_job[t]) ++u;
+            tiles += unskew_tiles(jobs[plan->inst_job[t]].rows, jobs[plan->inst_job[t]].cols);
+            t = u;
+        }
+        c.total_tiles = (int)tiles;
+        int tile_beg = 0;
+        long long cell_beg = 0;
+        for (int t = c.i0; t < c.i1;) {
+            int u = t;
+            const int j = plan->inst_job[t];
+            while (u < c.i1 && plan->inst_job[u] == j) ++u;
+            const JobSpec& J = jobs[j];
+            ChunkJob e{};
+            e.job = j;
+            e.dbeg = t - c.i0;
+            e.dcnt = u - t;
+            e.tile_beg = tile_beg;
+            e.tiles_x = unskew_tiles_x(J.cols);
+            e.first = first_chunk[j] == q;
+            e.last = last_chunk[j] == q;
+            const int want = unskew_splits(tiles, e.dcnt, num_sms, tn.unskew_ctas_per_sm);
+            e.per_split = unskew_per_split(e.dcnt, want);
+            e.nsplit = unskew_effective_splits(e.dcnt, want);
+            e.cell_beg = cell_beg;
+            const long long cells = (long long)J.rows * J.cols;
+            e.part_off = -1;
+            if (e.nsplit > 1) { e.part_off = c.part_elems; c.part_elems += e.nsplit * cells; }
+            c.max_split = std::max(c.max_split, e.nsplit);
+            c.total_cells += cells;
+            c.final_bytes += e.nsplit > 1 ? 8.0 * cells * (e.nsplit + 1) : 0.0;
+            c.unskew_bytes += (e.first ? 0.0 : 8.0 * cells) + (e.last ? 4.0 * cells : 8.0 * cells);
+            tile_beg += unskew_tiles(J.rows, J.cols);
+            cell_beg += cells;
+            plan->cj.push_back(e);
+            t = u;
+        }
+        c.ncj = (int)plan->cj.size() - c.cj_beg;
+        plan->max_part = std::max(plan->max_part, c.part_elems);
     }
     return TVS_OK;
 }
 
-// Scratch layout of a job (offsets in bytes from h->ws).
+// Scratch layout of a planned batch (byte offsets).  The header (directions,
+// jobs, chunk-job entries, item tables) is one contiguous block, uploaded with
+// one copy.
 struct Layout {
-    size_t dem, out, dirs, istart, rowlo, rowhi, sdem, cvf, cvb, vs64, part, counter, total;
+    size_t hdr, dirs, jobs, cj, istart, hdr_bytes;
+    size_t io_dem, io_out, counter, vs64, part, rowlo, rowhi, sdem, cvf, cvb, total;
 };
 
-Layout make_layout(const Plan& plan, int n, int rows, int cols, bool host_io, bool need_vs64, int nsplit)
+Layout make_layout(const BatchPlan& plan, bool host_io)
 {
     Layout L{};
     size_t o = 0;
-    const size_t cells = (size_t)rows * cols;
-    L.dem = o;     if (host_io) o += align256(cells * 4);
-    L.out = o;     if (host_io) o += align256(cells * 4);
-    L.dirs = o;    o += align256((size_t)n * sizeof(DirDev));
-    L.istart = o;  o += align256((size_t)plan.istart_total * 4);
+    L.hdr = o;
+    L.dirs = o;    o += align256(plan.dirs.size() * sizeof(DirDev));
+    L.jobs = o;    o += align256(plan.jobs.size() * sizeof(JobDev));
+    L.cj = o;      o += align256(plan.cj.size() * sizeof(ChunkJob));
+    L.istart = o;  o += align256(plan.istart.size() * 4);
+    L.hdr_bytes = o - L.hdr;
+    const size_t cells = host_io ? (size_t)plan.jobs[0].rows * plan.jobs[0].cols : 0;
+    L.io_dem = o;  o += align256(cells * 4);
+    L.io_out = o;  o += align256(cells * 4);
+    L.counter = o; o += 256;
+    L.vs64 = o;    o += align256((size_t)plan.vs64_elems * 8);
+    L.part = o;    o += align256((size_t)plan.max_part * 8);
     L.rowlo = o;   o += align256((size_t)plan.max_rows * 4);
     L.rowhi = o;   o += align256((size_t)plan.max_rows * 4);
     L.sdem = o;    o += align256(plan.max_slab * 4);
     L.cvf = o;     o += align256(plan.max_slab * 4);
     L.cvb = o;     o += align256(plan.max_slab * 4);
-    L.vs64 = o;    if (need_vs64) o += align256(cells * 8);
-    L.part = o;    if (nsplit > 1) o += align256((size_t)nsplit * cells * 8);
-    L.counter = o; o += 256;
     L.total = o;
     return L;
 }
 
-size_t fixed_bytes(int n, int rows, int cols, bool host_io, int num_sms)
+// Bytes a batch needs besides its chunks' slabs (header, host copies of a
+// single job, FP64 totals of every job, partials bound, counter).
+size_t fixed_bytes(const std::vector<JobSpec>& jobs, bool host_io, int num_sms)
 {
-    const size_t cells = (size_t)rows * cols;
-    const int nsplit = unskew_splits(rows, cols, n, num_sms);
-    return (host_io ? 2 * align256(cells * 4) : 0) + align256((size_t)n * sizeof(DirDev)) +
-           align256(cells * 8) + (nsplit > 1 ? align256((size_t)nsplit * cells * 8) : 0) + 4096 +
-           align256((size_t)(2 * n + 1) * 4);
+    size_t ninst = 0, cells = 0;
+    for (const JobSpec& J : jobs) { ninst += J.n; cells += (size_t)J.rows * J.cols; }
+    size_t b = align256(ninst * sizeof(DirDev)) + align256(jobs.size() * sizeof(JobDev)) +
+               align256((jobs.size() + ninst) * sizeof(ChunkJob)) + align256((2 * ninst + 1) * 4) + 4096;
+    if (host_io) b += 2 * align256((size_t)jobs[0].rows * jobs[0].cols * 4);
+    return b + align256(cells * 8) + part_bound(num_sms);
 }
 
-// Copy two host tables into device memory with one asynchronous copy from the
-// handle's pinned staging buffer.  The buffer is reused by the next call only
-// after the copy that read it has run (event), so the host never blocks on
-// the GPU work queued before the copy.
-int upload_header(tvs_ctx* h, const void* a, size_t a_bytes, const void* b, size_t b_bytes, void* d_a,
-                  void* d_b, cudaStream_t s)
+// Host image of the header for the scratch at `base`.
+void build_header(const BatchPlan& plan, const Layout& L, char* base, bool host_io, std::vector<char>* img)
 {
-    const size_t bytes = a_bytes + b_bytes;
-    if (h->pinned_done) TVS_CUDA(cudaEventSynchronize(h->pinned_done), "wait for staging buffer");
-    if (bytes > h->pinned_bytes) {
-        if (h->pinned) cudaFreeHost(h->pinned);
-        h->pinned = nullptr;
-        h->pinned_bytes = 0;
-        TVS_CUDA(cudaHostAlloc((void**)&h->pinned, bytes, cudaHostAllocDefault), "cudaHostAlloc");
-        h->pinned_bytes = bytes;
+    img->assign(L.hdr_bytes, 0);
+    std::memcpy(img->data() + (L.dirs - L.hdr), plan.dirs.data(), plan.dirs.size() * sizeof(DirDev));
+    std::vector<JobDev> jd(plan.jobs.size());
+    for (size_t j = 0; j < plan.jobs.size(); ++j) {
+        const JobSpec& J = plan.jobs[j];
+        jd[j].dem = host_io ? reinterpret_cast<const float*>(base + L.io_dem) : J.dem;
+        jd[j].out = host_io ? reinterpret_cast<float*>(base + L.io_out) : J.out;
+        jd[j].vs64 = plan.vs64_off[j] >= 0 ? reinterpret_cast<double*>(base + L.vs64) + plan.vs64_off[j] : nullptr;
+        jd[j].scale = (M_PI / (2.0 * (double)J.n)) * (J.step * J.step);
+        jd[j].rows = J.rows;
+        jd[j].cols = J.cols;
     }
-    std::memcpy(h->pinned, a, a_bytes);
-    std::memcpy(h->pinned + a_bytes, b, b_bytes);
-    // d_a and d_b are adjacent in the scratch layout only by accident; copy separately.
-    TVS_CUDA(cudaMemcpyAsync(d_a, h->pinned, a_bytes, cudaMemcpyHostToDevice, s), "copy direction table");
-    TVS_CUDA(cudaMemcpyAsync(d_b, h->pinned + a_bytes, b_bytes, cudaMemcpyHostToDevice, s), "copy item table");
-    if (!h->pinned_done) TVS_CUDA(cudaEventCreateWithFlags(&h->pinned_done, cudaEventDisableTiming), "event");
-    TVS_CUDA(cudaEventRecord(h->pinned_done, s), "record staging event");
-    return TVS_OK;
+    std::memcpy(img->data() + (L.jobs - L.hdr), jd.data(), jd.size() * sizeof(JobDev));
+    std::memcpy(img->data() + (L.cj - L.hdr), plan.cj.data(), plan.cj.size() * sizeof(ChunkJob));
+    std::memcpy(img->data() + (L.istart - L.hdr), plan.istart.data(), plan.istart.size() * 4);
 }
 
-// Enqueue the whole job: per chunk rowmap -> skew -> sweep -> unskew.
-int run_job(tvs_ctx* h, const float* d_dem, int rows, int cols, double step, double h0, int n,
-            double max_range, float* d_out, cudaStream_t s, bool host_io, const float* host_dem,
-            float* host_out)
+// Enqueue every chunk of a planned batch whose header already sits at base +
+// L.hdr: per chunk row map -> skew -> sweep -> unskew (-> finalize).
+int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* base, int num_sms, int smem_optin,
+                   int max_warps, cudaStream_t s)
 {
-    const size_t fixed = fixed_bytes(n, rows, cols, host_io, h->num_sms);
-    if (fixed >= h->budget) return fail(TVS_ERR_OOM, "the DEM does not fit the HBM budget");
-    Plan plan;
-    int rc = make_plan(rows, cols, step, max_range, n, h->budget - fixed, &plan);
-    if (rc) return rc;
-    const bool need_vs64 = plan.chunks.size() > 1;
-    int max_nd = 0;
-    for (const Chunk& c : plan.chunks) max_nd = std::max(max_nd, c.k1 - c.k0);
-    const int nsplit = unskew_splits(rows, cols, max_nd, h->num_sms);
-    const Layout L = make_layout(plan, n, rows, cols, host_io, need_vs64, nsplit);
-    rc = ensure_scratch(h, L.total);
-    if (rc) return rc;
-    char* ws = h->ws;
-    DirDev* d_dirs = reinterpret_cast<DirDev*>(ws + L.dirs);
-    int* d_istart = reinterpret_cast<int*>(ws + L.istart);
-    int* d_rowlo = reinterpret_cast<int*>(ws + L.rowlo);
-    int* d_rowhi = reinterpret_cast<int*>(ws + L.rowhi);
-    float* d_sdem = reinterpret_cast<float*>(ws + L.sdem);
-    int* d_cvf = reinterpret_cast<int*>(ws + L.cvf);
-    int* d_cvb = reinterpret_cast<int*>(ws + L.cvb);
-    double* d_vs64 = need_vs64 ? reinterpret_cast<double*>(ws + L.vs64) : nullptr;
-    double* d_part = nsplit > 1 ? reinterpret_cast<double*>(ws + L.part) : nullptr;
-    unsigned* d_counter = reinterpret_cast<unsigned*>(ws + L.counter);
-    const size_t cells = (size_t)rows * cols;
-    if (host_io) {
-        d_dem = reinterpret_cast<const float*>(ws + L.dem);
-        d_out = reinterpret_cast<float*>(ws + L.out);
-        TVS_CUDA(cudaMemcpyAsync((void*)d_dem, host_dem, cells * 4, cudaMemcpyHostToDevice, s), "copy dem");
-    }
-    // One upload per call: the direction table, then every chunk's item table.
-    std::vector<int> istart(plan.istart_total, 0);
-    std::vector<int> istart_at(plan.chunks.size(), 0);
-    {
-        int at = 0;
-        for (size_t q = 0; q < plan.chunks.size(); ++q) {
-            const Chunk& c = plan.chunks[q];
-            istart_at[q] = at;
-            for (int i = 0; i < c.k1 - c.k0; ++i) {
-                const DirDev& v = plan.dev[c.k0 + i];
-                istart[at + i + 1] = istart[at + i] + 2 * v.R * v.chunks;
-            }
-            at += c.k1 - c.k0 + 1;
-        }
-    }
-    const size_t dir_bytes = (size_t)n * sizeof(DirDev);
-    rc = upload_header(h, plan.dev.data(), dir_bytes, istart.data(), istart.size() * 4, d_dirs, d_istart, s);
-    if (rc) return rc;
-    const double scale = (M_PI / (2.0 * (double)n)) * (step * step);
-    const float h0f = (float)h0;
-    for (size_t q = 0; q < plan.chunks.size(); ++q) {
-        const Chunk& c = plan.chunks[q];
-        const int nd = c.k1 - c.k0;
-        const int* c_istart = d_istart + istart_at[q];
-        const int c_items = istart[istart_at[q] + nd];
-        const DirDev* cd = d_dirs + c.k0;
+    const DirDev* d_dirs = reinterpret_cast<const DirDev*>(base + L.dirs);
+    const JobDev* d_jobs = reinterpret_cast<const JobDev*>(base + L.jobs);
+    const ChunkJob* d_cj = reinterpret_cast<const ChunkJob*>(base + L.cj);
+    const int* d_istart = reinterpret_cast<const int*>(base + L.istart);
+    unsigned* d_counter = reinterpret_cast<unsigned*>(base + L.counter);
+    double* d_part = reinterpret_cast<double*>(base + L.part);
+    int* d_rowlo = reinterpret_cast<int*>(base + L.rowlo);
+    int* d_rowhi = reinterpret_cast<int*>(base + L.rowhi);
+    float* d_sdem = reinterpret_cast<float*>(base + L.sdem);
+    int* d_cvf = reinterpret_cast<int*>(base + L.cvf);
+    int* d_cvb = reinterpret_cast<int*>(base + L.cvb);
+    for (const Chunk& c : plan.chunks) {
+        const int nd = c.i1 - c.i0;
+        const DirDev* cd = d_dirs + c.i0;
         {
             Timer t(h, K_ROWMAP, s, c.rowmap_bytes);
             TVS_CUDA(launch_rowmap(cd, nd, c.max_R, d_rowlo, d_rowhi, s), "rowmap launch");
         }
         {
             Timer t(h, K_SKEW, s, c.skew_bytes);
-            TVS_CUDA(launch_skew(d_dem, rows, cols, cd, nd, c.max_tiles, d_rowlo, d_rowhi, d_sdem, s),
-                     "skew launch");
+            TVS_CUDA(launch_skew(d_jobs, cd, nd, c.max_tiles, d_sdem, s), "skew launch");
         }
         TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
         {
             Timer t(h, K_SWEEP, s, c.evals);
-            TVS_CUDA(launch_sweep(cd, c_istart, nd, c_items, d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb, h0f,
-                                  c.wmax, c.dmax, d_counter, h->num_sms, h->smem_optin, s),
+            TVS_CUDA(launch_sweep(cd, d_istart + c.istart_at, nd, c.items, d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
+                                  c.wmax, c.dmax, d_counter, num_sms, smem_optin, max_warps, s),
                      "sweep launch");
         }
         {
             Timer t(h, K_UNSKEW, s, c.unskew_bytes);
-            TVS_CUDA(launch_unskew(d_cvf, d_cvb, rows, cols, cd, nd, nsplit, d_part, d_vs64, d_out, q == 0,
-                                   q + 1 == plan.chunks.size(), scale, s),
+            TVS_CUDA(launch_unskew(d_cvf, d_cvb, d_jobs, cd, d_cj + c.cj_beg, c.ncj, c.total_tiles, c.max_split,
+                                   d_part, s),
                      "unskew launch");
         }
-        if (unskew_effective_splits(nd, nsplit) > 1) {
-            const double cells_b = (double)rows * cols * 8.0 * (unskew_effective_splits(nd, nsplit) + 1);
-            Timer t(h, K_FINAL, s, cells_b);
-            TVS_CUDA(launch_unskew_finalize(rows, cols, nd, nsplit, d_part, d_vs64, d_out, q == 0,
-                                            q + 1 == plan.chunks.size(), scale, s),
+        if (c.max_split > 1) {
+            Timer t(h, K_FINAL, s, c.final_bytes);
+            TVS_CUDA(launch_unskew_finalize(d_jobs, d_cj + c.cj_beg, c.ncj, c.total_cells, d_part, s),
                      "unskew finalize launch");
         }
     }
+    return TVS_OK;
+}
+
+// Copy a header image to the device through the handle's pinned staging
+// buffer.  The buffer is reused by the next call only after the copy that
+// read it has run (event), so the host never blocks on earlier GPU work.
+int upload_header(tvs_ctx* h, const std::vector<char>& img, void* dst, cudaStream_t s)
+{
+    if (h->pinned_done) TVS_CUDA(cudaEventSynchronize(h->pinned_done), "wait for staging buffer");
+    if (img.size() > h->pinned_bytes) {
+        if (h->pinned) cudaFreeHost(h->pinned);
+        h->pinned = nullptr;
+        h->pinned_bytes = 0;
+        TVS_CUDA(cudaHostAlloc((void**)&h->pinned, img.size(), cudaHostAllocDefault), "cudaHostAlloc");
+        h->pinned_bytes = img.size();
+    }
+    std::memcpy(h->pinned, img.data(), img.size());
+    TVS_CUDA(cudaMemcpyAsync(dst, h->pinned, img.size(), cudaMemcpyHostToDevice, s), "copy tables");
+    if (!h->pinned_done) TVS_CUDA(cudaEventCreateWithFlags(&h->pinned_done, cudaEventDisableTiming), "event");
+    TVS_CUDA(cudaEventRecord(h->pinned_done, s), "record staging event");
+    return TVS_OK;
+}
+
+// Plan, size the scratch and enqueue a batch on the handle.  With host_io the
+// single job's DEM is copied in from host memory and its map copied back.
+int run_batch(tvs_ctx* h, const std::vector<JobSpec>& jobs, cudaStream_t s, bool host_io, const float* host_dem,
+              float* host_out)
+{
+    const size_t fixed = fixed_bytes(jobs, host_io, h->num_sms);
+    if (fixed >= h->budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
+    BatchPlan plan;
+    int rc = plan_batch(jobs, h->budget - fixed, h->num_sms, h->tuning, &plan);
+    if (rc) return rc;
+    const Layout L = make_layout(plan, host_io);
+    rc = ensure_scratch(h, L.total);
+    if (rc) return rc;
+    char* base = h->ws;
+    std::vector<char> img;
+    build_header(plan, L, base, host_io, &img);
     if (host_io) {
-        TVS_CUDA(cudaMemcpyAsync(host_out, d_out, cells * 4, cudaMemcpyDeviceToHost, s), "copy out");
+        const size_t bytes = (size_t)jobs[0].rows * jobs[0].cols * 4;
+        TVS_CUDA(cudaMemcpyAsync(base + L.io_dem, host_dem, bytes, cudaMemcpyHostToDevice, s), "copy dem");
+    }
+    rc = upload_header(h, img, base + L.hdr, s);
+    if (rc) return rc;
+    rc = enqueue_chunks(h, plan, L, base, h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, s);
+    if (rc) return rc;
+    if (host_io) {
+        const size_t bytes = (size_t)jobs[0].rows * jobs[0].cols * 4;
+        TVS_CUDA(cudaMemcpyAsync(host_out, base + L.io_out, bytes, cudaMemcpyDeviceToHost, s), "copy out");
         TVS_CUDA(cudaStreamSynchronize(s), "synchronize");
     }
     return TVS_OK;
@@ -603,8 +699,9 @@ int tvs_total_viewshed(tvs_handle h, const float* dem, int rows, int cols, doubl
     for (size_t q = 0; q < cells; ++q)
         if (!std::isfinite(dem[q])) return fail(TVS_ERR_ARG, "dem holds a non-finite value");
     DeviceGuard g(h->device);
-    return run_job(h, nullptr, rows, cols, step_m, obs_height_m, n_sectors, max_range_m, nullptr,
-                   h->stream, true, dem, out);
+    const std::vector<JobSpec> jobs{JobSpec{nullptr, nullptr, rows, cols, n_sectors, step_m, obs_height_m,
+                                            max_range_m}};
+    return run_batch(h, jobs, h->stream, true, dem, out);
 }
 
 int tvs_total_viewshed_device(tvs_handle h, const float* d_dem, int rows, int cols, double step_m,
@@ -620,8 +717,9 @@ int tvs_total_viewshed_device(tvs_handle h, const float* d_dem, int rows, int co
     const char* b = reinterpret_cast<const char*>(d_out);
     if (a < b + bytes && b < a + bytes) return fail(TVS_ERR_ARG, "d_dem and d_out overlap");
     DeviceGuard g(h->device);
-    return run_job(h, d_dem, rows, cols, step_m, obs_height_m, n_sectors, max_range_m, d_out,
-                   reinterpret_cast<cudaStream_t>(cuda_stream), false, nullptr, nullptr);
+    const std::vector<JobSpec> jobs{JobSpec{d_dem, d_out, rows, cols, n_sectors, step_m, obs_height_m,
+                                            max_range_m}};
+    return run_batch(h, jobs, reinterpret_cast<cudaStream_t>(cuda_stream), false, nullptr, nullptr);
 }
 
 int tvs_direction(int n_sectors, int k, int rows, int cols, double step_m, double max_range_m,
@@ -694,39 +792,37 @@ int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, d
     if (rc) return rc;
     if (k < 0 || k >= n_sectors) return fail(TVS_ERR_ARG, "k out of range");
     DeviceGuard g(h->device);
-    Plan plan;
-    rc = make_plan(rows, cols, step_m, max_range_m, n_sectors, (size_t)1 << 62, &plan, k);
+    const std::vector<JobSpec> jobs{JobSpec{nullptr, nullptr, rows, cols, n_sectors, step_m, obs_height_m,
+                                            max_range_m}};
+    BatchPlan plan;
+    rc = plan_batch(jobs, (size_t)1 << 62, h->num_sms, h->tuning, &plan, k);
     if (rc) return rc;
     const Chunk& c = plan.chunks[0];
-    const DirDev& v = plan.dev[k];
-    const size_t cells = (size_t)rows * cols;
-    const size_t o_dem = 0, o_dir = align256(cells * 4), o_is = o_dir + align256(sizeof(DirDev));
-    const size_t o_lo = o_is + 256, o_hi = o_lo + align256((size_t)v.R * 4);
-    const size_t o_s = o_hi + align256((size_t)v.R * 4), o_cv = o_s + align256(c.slab_elems * 4);
-    const size_t o_cb = o_cv + align256(c.slab_elems * 4);
-    const size_t o_cnt = o_cb + align256(c.slab_elems * 4), total = o_cnt + 256;
-    rc = ensure_scratch(h, total);
+    const DirDev& v = plan.dirs[0];
+    const Layout L = make_layout(plan, true);
+    rc = ensure_scratch(h, L.total);
     if (rc) return rc;
     char* ws = h->ws;
     cudaStream_t s = h->stream;
-    float* d_dem = reinterpret_cast<float*>(ws + o_dem);
-    DirDev* d_dir = reinterpret_cast<DirDev*>(ws + o_dir);
-    int* d_is = reinterpret_cast<int*>(ws + o_is);
-    int* d_lo = reinterpret_cast<int*>(ws + o_lo);
-    int* d_hi = reinterpret_cast<int*>(ws + o_hi);
-    float* d_s = reinterpret_cast<float*>(ws + o_s);
-    int* d_cv = reinterpret_cast<int*>(ws + o_cv);
-    int* d_cb = reinterpret_cast<int*>(ws + o_cb);
-    unsigned* d_cnt = reinterpret_cast<unsigned*>(ws + o_cnt);
-    const int is_host[2] = {0, 2 * v.R * v.chunks};
-    TVS_CUDA(cudaMemcpyAsync(d_dem, dem, cells * 4, cudaMemcpyHostToDevice, s), "copy dem");
-    TVS_CUDA(cudaMemcpyAsync(d_dir, &v, sizeof(v), cudaMemcpyHostToDevice, s), "copy direction");
-    TVS_CUDA(cudaMemcpyAsync(d_is, is_host, sizeof(is_host), cudaMemcpyHostToDevice, s), "copy items");
+    std::vector<char> img;
+    build_header(plan, L, ws, true, &img);
+    const size_t cells = (size_t)rows * cols;
+    TVS_CUDA(cudaMemcpyAsync(ws + L.io_dem, dem, cells * 4, cudaMemcpyHostToDevice, s), "copy dem");
+    rc = upload_header(h, img, ws + L.hdr, s);
+    if (rc) return rc;
+    const DirDev* d_dir = reinterpret_cast<const DirDev*>(ws + L.dirs);
+    const JobDev* d_jobs = reinterpret_cast<const JobDev*>(ws + L.jobs);
+    int* d_lo = reinterpret_cast<int*>(ws + L.rowlo);
+    int* d_hi = reinterpret_cast<int*>(ws + L.rowhi);
+    float* d_s = reinterpret_cast<float*>(ws + L.sdem);
+    int* d_cv = reinterpret_cast<int*>(ws + L.cvf);
+    int* d_cb = reinterpret_cast<int*>(ws + L.cvb);
+    unsigned* d_cnt = reinterpret_cast<unsigned*>(ws + L.counter);
     TVS_CUDA(launch_rowmap(d_dir, 1, v.R, d_lo, d_hi, s), "rowmap launch");
-    TVS_CUDA(launch_skew(d_dem, rows, cols, d_dir, 1, c.max_tiles, d_lo, d_hi, d_s, s), "skew launch");
+    TVS_CUDA(launch_skew(d_jobs, d_dir, 1, c.max_tiles, d_s, s), "skew launch");
     TVS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), s), "reset work counter");
-    TVS_CUDA(launch_sweep(d_dir, d_is, 1, is_host[1], d_s, d_lo, d_hi, d_cv, d_cb, (float)obs_height_m, v.W,
-                          v.K, d_cnt, h->num_sms, h->smem_optin, s),
+    TVS_CUDA(launch_sweep(d_dir, reinterpret_cast<const int*>(ws + L.istart), 1, c.items, d_s, d_lo, d_hi, d_cv,
+                          d_cb, v.W, v.K, d_cnt, h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, s),
              "sweep launch");
     std::vector<int> slab(c.slab_elems), slabb(c.slab_elems), lo(v.R), hi(v.R);
     TVS_CUDA(cudaMemcpyAsync(slab.data(), d_cv, c.slab_elems * 4, cudaMemcpyDeviceToHost, s), "copy cv");
@@ -837,13 +933,18 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     DirDev dirs[kNoAllocMaxDirs];
     int istart[2 * kNoAllocMaxDirs + 1];
     int chunk_k0[kNoAllocMaxDirs + 1];
+    ChunkJob cjs[kNoAllocMaxDirs];
     int nchunks = 0;
-    const int nsplit = unskew_splits(rows, cols, std::min(n_sectors, FP32_GROUP * 64), num_sms);
+    const int tiles = unskew_tiles(rows, cols);
+    const Tuning tn;
+    const int nsplit_max = unskew_splits(tiles, n_sectors, num_sms, tn.unskew_ctas_per_sm);
     const size_t o_dirs = 0;
-    const size_t o_istart = o_dirs + align256((size_t)n_sectors * sizeof(DirDev));
+    const size_t o_job = o_dirs + align256((size_t)n_sectors * sizeof(DirDev));
+    const size_t o_cj = o_job + align256(sizeof(JobDev));
+    const size_t o_istart = o_cj + align256((size_t)n_sectors * sizeof(ChunkJob));
     const size_t o_vs64 = o_istart + align256((size_t)(2 * n_sectors + 1) * 4);
     const size_t o_part = o_vs64 + align256(cells * 8);
-    const size_t o_counter = o_part + (nsplit > 1 ? align256((size_t)nsplit * cells * 8) : 0);
+    const size_t o_counter = o_part + (nsplit_max > 1 ? align256((size_t)nsplit_max * cells * 8) : 0);
     const size_t o_chunk = o_counter + 256;
     if (o_chunk >= kNoAllocScratchBytes)
         return fail(TVS_ERR_OOM, "the DEM does not fit the 64 MiB no-allocation scratch");
@@ -860,13 +961,15 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 const size_t wp = (size_t)((d.W + 3) & ~3);
                 const size_t s2 = slab + (size_t)d.R * wp, r2 = nrows + d.R;
                 const size_t need = 2 * align256(r2 * 4) + 3 * align256(s2 * 4);
-                if (need > avail || 2LL * (long long)r2 * sweep_chunks(d.W) > kMaxChunkItems) break;
+                if (need > avail || 2LL * (long long)r2 * sweep_chunks(d.W, pov_for(tn, d.W)) > kMaxChunkItems) break;
                 DirDev& v = dirs[kk];
                 std::memset(&v, 0, sizeof(v));
                 v.t_fx = d.t_fx; v.slab = (long long)slab; v.frame = d.frame; v.H = d.H; v.W = d.W;
                 v.Wp = (int)wp; v.D = d.D; v.R = d.R;
                 v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
-                v.row_off = (int)nrows; v.chunks = sweep_chunks(d.W); v.gidx = kk; v.g = (float)d.g;
+                v.pov = pov_for(tn, d.W);
+                v.row_off = (int)nrows; v.chunks = sweep_chunks(d.W, v.pov); v.gidx = kk; v.job = 0;
+                v.g = (float)d.g; v.h0 = (float)obs_height_m;
                 slab = s2;
                 nrows = r2;
                 ++kk;
@@ -887,12 +990,30 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 ++at;
             }
             ++at;
+            const int nd = chunk_k0[c + 1] - chunk_k0[c];
+            ChunkJob& e = cjs[c];
+            std::memset(&e, 0, sizeof(e));
+            e.job = 0; e.dbeg = 0; e.dcnt = nd; e.tile_beg = 0; e.tiles_x = unskew_tiles_x(cols);
+            e.first = c == 0; e.last = c + 1 == nchunks;
+            const int want = unskew_splits(tiles, nd, num_sms, tn.unskew_ctas_per_sm);
+            e.per_split = unskew_per_split(nd, want);
+            e.nsplit = unskew_effective_splits(nd, want);
+            e.cell_beg = 0;
+            e.part_off = 0;
         }
     }
+    JobDev job;
+    job.dem = d_dem;
+    job.out = d_out;
+    job.vs64 = nchunks > 1 ? reinterpret_cast<double*>(base + o_vs64) : nullptr;
+    job.scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
+    job.rows = rows;
+    job.cols = cols;
     DirDev* d_dirs = reinterpret_cast<DirDev*>(base + o_dirs);
+    JobDev* d_job = reinterpret_cast<JobDev*>(base + o_job);
+    ChunkJob* d_cj = reinterpret_cast<ChunkJob*>(base + o_cj);
     int* d_istart = reinterpret_cast<int*>(base + o_istart);
-    double* d_vs64 = reinterpret_cast<double*>(base + o_vs64);
-    double* d_part = nsplit > 1 ? reinterpret_cast<double*>(base + o_part) : nullptr;
+    double* d_part = reinterpret_cast<double*>(base + o_part);
     unsigned* d_counter = reinterpret_cast<unsigned*>(base + o_counter);
     int* d_rowlo = reinterpret_cast<int*>(base + o_chunk);
     int* d_rowhi = reinterpret_cast<int*>(base + o_chunk + align256(max_rows * 4));
@@ -904,9 +1025,11 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     // Stack tables are staged by the runtime before these calls return.
     TVS_CUDA(cudaMemcpyAsync(d_dirs, dirs, (size_t)n_sectors * sizeof(DirDev), cudaMemcpyHostToDevice, s),
              "copy direction table");
+    TVS_CUDA(cudaMemcpyAsync(d_job, &job, sizeof(JobDev), cudaMemcpyHostToDevice, s), "copy job table");
+    TVS_CUDA(cudaMemcpyAsync(d_cj, cjs, (size_t)nchunks * sizeof(ChunkJob), cudaMemcpyHostToDevice, s),
+             "copy chunk table");
     TVS_CUDA(cudaMemcpyAsync(d_istart, istart, (size_t)(n_sectors + nchunks) * 4, cudaMemcpyHostToDevice, s),
              "copy item table");
-    const double scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
     int at = 0;
     for (int c = 0; c < nchunks; ++c) {
         const int k0 = chunk_k0[c], nd = chunk_k0[c + 1] - k0;
@@ -918,20 +1041,228 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
             wmax = std::max(wmax, dirs[q].W);
         }
         const DirDev* cd = d_dirs + k0;
-        const int first = c == 0, last = c + 1 == nchunks;
         TVS_CUDA(launch_rowmap(cd, nd, max_R, d_rowlo, d_rowhi, s), "rowmap launch");
-        TVS_CUDA(launch_skew(d_dem, rows, cols, cd, nd, max_tiles, d_rowlo, d_rowhi, d_sdem, s), "skew launch");
+        TVS_CUDA(launch_skew(d_job, cd, nd, max_tiles, d_sdem, s), "skew launch");
         // the shared array keeps the previous call's contents: the work counter must start at zero
         TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
         TVS_CUDA(launch_sweep(cd, d_istart + at, nd, istart[at + nd], d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                              (float)obs_height_m, wmax, dmax, d_counter, num_sms, smem_optin, s),
+                              wmax, dmax, d_counter, num_sms, smem_optin, tn.sweep_max_warps, s),
                  "sweep launch");
-        TVS_CUDA(launch_unskew(d_cvf, d_cvb, rows, cols, cd, nd, nsplit, d_part, d_vs64, d_out, first, last,
-                               scale, s),
+        TVS_CUDA(launch_unskew(d_cvf, d_cvb, d_job, cd, d_cj + c, 1, tiles, cjs[c].nsplit, d_part, s),
                  "unskew launch");
-        TVS_CUDA(launch_unskew_finalize(rows, cols, nd, nsplit, d_part, d_vs64, d_out, first, last, scale, s),
-                 "unskew finalize launch");
+        if (cjs[c].nsplit > 1)
+            TVS_CUDA(launch_unskew_finalize(d_job, d_cj + c, 1, (long long)cells, d_part, s),
+                     "unskew finalize launch");
         at += nd + 1;
     }
     return TVS_OK;
 }
+
+// ================================================================ batches ==
+namespace {
+
+int check_jobs(const tvs_job* jobs, int njobs, std::vector<JobSpec>* out)
+{
+    if (!jobs || njobs < 1) return fail(TVS_ERR_ARG, "jobs is NULL or njobs < 1");
+    for (int j = 0; j < njobs; ++j) {
+        const tvs_job& J = jobs[j];
+        const std::string pre = "job " + std::to_string(j) + ": ";
+        if (!J.d_dem || !J.d_out) return fail(TVS_ERR_ARG, pre + "d_dem or d_out is NULL");
+        const int rc = check_job(J.rows, J.cols, J.step_m, J.obs_height_m, J.n_sectors, J.max_range_m);
+        if (rc) return fail(rc, pre + g_err);
+        const size_t bytes = (size_t)J.rows * J.cols * 4;
+        const char* a = reinterpret_cast<const char*>(J.d_dem);
+        const char* b = reinterpret_cast<const char*>(J.d_out);
+        if (a < b + bytes && b < a + bytes) return fail(TVS_ERR_ARG, pre + "d_dem and d_out overlap");
+        out->push_back(JobSpec{J.d_dem, J.d_out, J.rows, J.cols, J.n_sectors, J.step_m, J.obs_height_m,
+                               J.max_range_m});
+    }
+    return TVS_OK;
+}
+
+}  // namespace
+
+struct tvs_batch {
+    tvs_ctx* h = nullptr;
+    BatchPlan plan;
+    Layout L{};
+    char* ws = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int kernels = 0;
+};
+
+extern "C" {
+
+int tvs_total_viewshed_batch(tvs_handle h, const tvs_job* jobs, int njobs, void* cuda_stream)
+{
+    if (!h) return fail(TVS_ERR_ARG, "handle is NULL");
+    std::vector<JobSpec> specs;
+    int rc = check_jobs(jobs, njobs, &specs);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    return run_batch(h, specs, reinterpret_cast<cudaStream_t>(cuda_stream), false, nullptr, nullptr);
+}
+
+void tvs_batch_destroy(tvs_batch_handle b)
+{
+    if (!b) return;
+    DeviceGuard g(b->h->device);
+    cudaDeviceSynchronize();
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->ws) cudaFree(b->ws);
+    delete b;
+}
+
+int tvs_batch_create(tvs_handle h, const tvs_job* jobs, int njobs, size_t hbm_budget_bytes,
+                     tvs_batch_handle* out)
+{
+    if (!h || !out) return fail(TVS_ERR_ARG, "handle or out is NULL");
+    *out = nullptr;
+    std::vector<JobSpec> specs;
+    int rc = check_jobs(jobs, njobs, &specs);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    const size_t budget = hbm_budget_bytes ? hbm_budget_bytes : h->budget;
+    const size_t fixed = fixed_bytes(specs, false, h->num_sms);
+    if (fixed >= budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
+    tvs_batch* b = new tvs_batch();
+    b->h = h;
+    rc = plan_batch(specs, budget - fixed, h->num_sms, h->tuning, &b->plan);
+    if (rc) { delete b; return rc; }
+    b->L = make_layout(b->plan, false);
+    cudaError_t e = cudaMalloc(&b->ws, b->L.total);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        b->ws = nullptr;
+        tvs_batch_destroy(b);
+        return fail(TVS_ERR_OOM, std::string("cudaMalloc of batch scratch failed: ") + cudaGetErrorString(e));
+    }
+    std::vector<char> img;
+    build_header(b->plan, b->L, b->ws, false, &img);
+    e = cudaMemcpy(b->ws + b->L.hdr, img.data(), img.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { tvs_batch_destroy(b); return cuda_fail(e, "copy batch tables"); }
+    cudaStream_t cap = nullptr;
+    e = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+    if (e != cudaSuccess) { tvs_batch_destroy(b); return cuda_fail(e, "cudaStreamCreate"); }
+    e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) { cudaStreamDestroy(cap); tvs_batch_destroy(b); return cuda_fail(e, "begin capture"); }
+    rc = enqueue_chunks(nullptr, b->plan, b->L, b->ws, h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, cap);
+    cudaGraph_t graph = nullptr;
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    b->graph = graph;
+    if (rc) { tvs_batch_destroy(b); return rc; }
+    if (e != cudaSuccess) { tvs_batch_destroy(b); return cuda_fail(e, "end capture"); }
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    if (e != cudaSuccess) { b->exec = nullptr; tvs_batch_destroy(b); return cuda_fail(e, "instantiate graph"); }
+    for (const Chunk& c : b->plan.chunks) b->kernels += 4 + (c.max_split > 1 ? 1 : 0);
+    *out = b;
+    return TVS_OK;
+}
+
+int tvs_batch_launch(tvs_batch_handle b, void* cuda_stream)
+{
+    if (!b) return fail(TVS_ERR_ARG, "batch is NULL");
+    DeviceGuard g(b->h->device);
+    TVS_CUDA(cudaGraphLaunch(b->exec, reinterpret_cast<cudaStream_t>(cuda_stream)), "graph launch");
+    return TVS_OK;
+}
+
+int tvs_batch_get_info(tvs_batch_handle b, tvs_batch_info* info)
+{
+    if (!b || !info) return fail(TVS_ERR_ARG, "NULL argument");
+    std::memset(info, 0, sizeof(*info));
+    info->jobs = (int32_t)b->plan.jobs.size();
+    info->chunks = (int32_t)b->plan.chunks.size();
+    info->kernels_per_launch = b->kernels;
+    info->evals = b->plan.evals;
+    info->scratch_bytes = (double)b->L.total;
+    return TVS_OK;
+}
+
+}  // extern "C"
+
+// ============================================================== tuning ==
+extern "C" {
+
+int tvs_get_tuning(tvs_handle h, tvs_tuning* t)
+{
+    if (!h || !t) return fail(TVS_ERR_ARG, "NULL argument");
+    std::memset(t, 0, sizeof(*t));
+    t->small_pov_below_w = h->tuning.small_pov_below_w;
+    t->sweep_max_warps = h->tuning.sweep_max_warps;
+    t->unskew_ctas_per_sm = h->tuning.unskew_ctas_per_sm;
+    return TVS_OK;
+}
+
+int tvs_set_tuning(tvs_handle h, const tvs_tuning* t)
+{
+    if (!h || !t) return fail(TVS_ERR_ARG, "NULL argument");
+    if (t->small_pov_below_w < 0 || t->sweep_max_warps < 0 || t->sweep_max_warps > SWEEP_MAX_WARPS ||
+        t->unskew_ctas_per_sm < 1)
+        return fail(TVS_ERR_ARG, "tuning out of range");
+    h->tuning.small_pov_below_w = t->small_pov_below_w;
+    h->tuning.sweep_max_warps = t->sweep_max_warps;
+    h->tuning.unskew_ctas_per_sm = t->unskew_ctas_per_sm;
+    return TVS_OK;
+}
+
+int tvs_autotune(tvs_handle h, const tvs_job* jobs, int njobs, tvs_tuning* best, double* best_ms)
+{
+    if (!h) return fail(TVS_ERR_ARG, "handle is NULL");
+    std::vector<JobSpec> specs;
+    int rc = check_jobs(jobs, njobs, &specs);
+    if (rc) return rc;
+    DeviceGuard g(h->device);
+    cudaStream_t s = h->stream;
+    cudaEvent_t a = nullptr, b = nullptr;
+    TVS_CUDA(cudaEventCreate(&a), "event");
+    TVS_CUDA(cudaEventCreate(&b), "event");
+    const bool prof = h->profiling;
+    h->profiling = false;
+    auto time_of = [&](const Tuning& tn, float* ms) -> int {
+        h->tuning = tn;
+        int r = run_batch(h, specs, s, false, nullptr, nullptr);   // warm-up (and scratch growth)
+        if (r) return r;
+        cudaEventRecord(a, s);
+        r = run_batch(h, specs, s, false, nullptr, nullptr);
+        if (r) return r;
+        cudaEventRecord(b, s);
+        cudaError_t e = cudaEventSynchronize(b);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+        e = cudaEventElapsedTime(ms, a, b);
+        if (e != cudaSuccess) return cuda_fail(e, "autotune timing");
+        return TVS_OK;
+    };
+    Tuning cur = h->tuning;
+    float cur_ms = 0.f;
+    rc = time_of(cur, &cur_ms);
+    const int povs[] = {0, 384, 768, 1536, 1 << 30};
+    const int warps[] = {0, 12, 8};
+    const int unskews[] = {1, 2, 4};
+    for (int stage = 0; stage < 3 && !rc; ++stage) {
+        const int* opts = stage == 0 ? povs : stage == 1 ? warps : unskews;
+        const int nopt = stage == 0 ? 5 : 3;
+        for (int o = 0; o < nopt && !rc; ++o) {
+            Tuning tn = cur;
+            if (stage == 0) tn.small_pov_below_w = opts[o];
+            if (stage == 1) tn.sweep_max_warps = opts[o];
+            if (stage == 2) tn.unskew_ctas_per_sm = opts[o];
+            float ms = 0.f;
+            rc = time_of(tn, &ms);
+            if (!rc && ms < cur_ms) { cur = tn; cur_ms = ms; }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    h->profiling = prof;
+    h->tuning = cur;
+    if (rc) return rc;
+    if (best) tvs_get_tuning(h, best);
+    if (best_ms) *best_ms = cur_ms;
+    return TVS_OK;
+}
+
+}  // extern "C"

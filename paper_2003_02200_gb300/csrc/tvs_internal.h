@@ -6,27 +6,22 @@
 
 namespace tvs {
 
-// Warp work item of the sweep: 32 lanes x POVS_PER_LANE consecutive samples.
-// Each lane walks two groups of POVS_PER_LANE consecutive samples (a group and
-// its mirror), so a warp item covers 64 groups of one skewed row.  The tile
-// constants can be set at compile time (-DTVS_POVS_PER_LANE=8, ...).
-#ifndef TVS_POVS_PER_LANE
-#define TVS_POVS_PER_LANE 8
-#endif
-#ifndef TVS_SWEEP_UNROLL
-#define TVS_SWEEP_UNROLL 24
-#endif
+// Sweep tiling.  Each lane walks two groups of consecutive samples (a group
+// and its mirror), 32 lanes per warp item.  A direction uses groups of
+// SMALL_POV samples (blocks of SMALL_UNROLL steps) or of LARGE_POV samples
+// (blocks of LARGE_UNROLL steps); the choice is per direction (DirDev::pov).
+constexpr int SMALL_POV = 4;
+constexpr int SMALL_UNROLL = 16;
+constexpr int LARGE_POV = 8;
+constexpr int LARGE_UNROLL = 24;
 #ifndef TVS_SWEEP_MAX_WARPS
 #define TVS_SWEEP_MAX_WARPS 16
 #endif
-constexpr int POVS_PER_LANE = TVS_POVS_PER_LANE;
-constexpr int SWEEP_UNROLL = TVS_SWEEP_UNROLL;
-constexpr int WARP_POVS = 64 * POVS_PER_LANE;
 constexpr int SWEEP_MAX_WARPS = TVS_SWEEP_MAX_WARPS;
 // Left pad of a staged row (floats); a multiple of 4.
 constexpr int ROW_PADL = 16;
 // Right pad: the last window of a block reads up to P + U floats past a target.
-constexpr int ROW_PADR = POVS_PER_LANE + 2 * SWEEP_UNROLL + 8;
+constexpr int ROW_PADR = LARGE_POV + 2 * LARGE_UNROLL + 8;
 // Directions whose FP32 partial sums are added once into the FP64 total.
 constexpr int FP32_GROUP = 8;
 
@@ -37,8 +32,8 @@ constexpr int SKEW_TJ = 32;
 constexpr int UNSKEW_TI = 32;
 constexpr int UNSKEW_TJ = 32;
 
-// One direction as the kernels see it (section 4.1 step 1, Alg. 6 extended to
-// the four eighths of the half-plane by a D4 view of the DEM).
+// One direction of one job as the kernels see it (section 4.1 step 1, Alg. 6
+// extended to the four eighths of the half-plane by a D4 view of the DEM).
 struct DirDev {
     unsigned long long t_fx;   // llround(tan(alpha) * 2^32), 0 .. 2^32
     long long slab;            // element offset of this direction's skewed slab
@@ -49,37 +44,64 @@ struct DirDev {
     int R;                     // skewed rows, H + D; row p has base row p - D
     int K;                     // walk limit in steps, clipped to [0, W]
     int row_off;               // offset of this direction in the row tables
-    int chunks;                // warp items per skewed row and walk direction, ceil(W / WARP_POVS)
-    int gidx;                  // global direction index k
+    int chunks;                // warp items per skewed row and walk direction
+    int gidx;                  // direction index k within its job
+    int job;                   // index of the job in the job table
     float g;                   // 1 + t^2
-    int pad_;
+    float h0;                  // observer height of the job
+    int pov;                   // sweep group size, SMALL_POV or LARGE_POV
 };
 
-struct KernelTimer;  // host-side event bookkeeping (tvs_api.cu)
+// One DEM of a call (a batch holds several).
+struct JobDev {
+    const float* dem;          // rows x cols elevations (device)
+    float* out;                // rows x cols visible areas (device)
+    double* vs64;              // FP64 running totals when the job spans several chunks, else NULL
+    double scale;              // (pi / (2n)) * step^2
+    int rows, cols;
+};
+
+// One job's share of a chunk of directions, for the unskew and its finalize.
+struct ChunkJob {
+    long long cell_beg;        // first cell of the job in the chunk's flattened cell space
+    long long part_off;        // FP64 partials of a split unskew: offset in the partials buffer
+    int job;                   // index in the job table
+    int dbeg, dcnt;            // the job's directions in the chunk (chunk-local)
+    int tile_beg;              // first unskew tile of the job in the chunk's flattened tiles
+    int tiles_x;               // cell tiles per DEM row
+    int first, last;           // the chunk is the job's first / last one
+    int nsplit;                // direction ranges of the unskew (1 = no partials)
+    int per_split;             // directions per range (a multiple of FP32_GROUP)
+    int pad_;
+};
 
 // Launchers (tvs_kernels.cu).  All are asynchronous on `stream`.
 cudaError_t launch_rowmap(const DirDev* d_dirs, int ndir, int max_R, int* rowlo, int* rowhi,
                           cudaStream_t stream);
 cudaError_t launch_colmap(const DirDev* d_dir, int* dest, unsigned* frac, cudaStream_t stream);
-cudaError_t launch_skew(const float* dem, int rows, int cols, const DirDev* d_dirs, int ndir,
-                        int max_tiles, const int* rowlo, const int* rowhi, float* sdem,
+cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, int max_tiles, float* sdem,
                         cudaStream_t stream);
+// Warp items of one skewed row and walk direction for a row of W samples.
+int sweep_chunks(int W, int pov);
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
-                         float h0, int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin,
+                         int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin, int max_warps,
                          cudaStream_t stream);
-// Number of direction ranges the unskew splits a chunk into for a DEM of this
-// size (1 for DEMs with enough cell tiles to fill the GPU).
-int unskew_splits(int rows, int cols, int ndir, int num_sms);
+// Unskew of a chunk: `total_tiles` flattened cell tiles over the chunk's jobs
+// (ncj entries of d_cj, sorted by tile_beg), `max_split` the largest nsplit.
+cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, const JobDev* d_jobs, const DirDev* d_dirs,
+                          const ChunkJob* d_cj, int ncj, int total_tiles, int max_split, double* part,
+                          cudaStream_t stream);
+// Adds the FP64 partials of the chunk's split jobs (a no-op entry for the others).
+cudaError_t launch_unskew_finalize(const JobDev* d_jobs, const ChunkJob* d_cj, int ncj, long long total_cells,
+                                   const double* part, cudaStream_t stream);
+
+// Number of direction ranges for one job of a chunk whose jobs have
+// `chunk_tiles` cell tiles in all (1 when the chunk fills the GPU).
+int unskew_splits(long long chunk_tiles, int ndir, int num_sms, int ctas_per_sm);
 int unskew_per_split(int ndir, int nsplit);
 int unskew_effective_splits(int ndir, int nsplit);
-// Adds the per-range FP64 partials of a split unskew (no-op when nsplit <= 1).
-cudaError_t launch_unskew_finalize(int rows, int cols, int ndir, int nsplit, const double* part, double* vs64,
-                                   float* out, int first_chunk, int last_chunk, double scale,
-                                   cudaStream_t stream);
-cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, int rows, int cols, const DirDev* d_dirs,
-                          int ndir, int nsplit, double* part, double* vs64, float* out, int first_chunk,
-                          int last_chunk, double scale, cudaStream_t stream);
-
+int unskew_tiles_x(int cols);
+int unskew_tiles(int rows, int cols);
 
 }  // namespace tvs

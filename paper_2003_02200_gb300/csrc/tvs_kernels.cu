@@ -77,12 +77,14 @@ __global__ void colmap_kernel(const DirDev* __restrict__ dir, int* __restrict__ 
 constexpr int SKEW_ROWS = SKEW_TP + SKEW_TJ + 3;
 constexpr int SKEW_PITCH = SKEW_TJ + 1;
 
-__global__ void __launch_bounds__(256) skew_kernel(const float* __restrict__ dem, int cols,
+__global__ void __launch_bounds__(256) skew_kernel(const JobDev* __restrict__ jobs,
                                                    const DirDev* __restrict__ dirs,
                                                    float* __restrict__ sdem)
 {
     __shared__ float S[SKEW_ROWS * SKEW_PITCH];
     const DirDev d = dirs[blockIdx.y];
+    const float* __restrict__ dem = jobs[d.job].dem;
+    const int cols = jobs[d.job].cols;
     const int tiles_j = (d.W + SKEW_TJ - 1) / SKEW_TJ;
     const int tiles_p = (d.R + SKEW_TP - 1) / SKEW_TP;
     if ((int)blockIdx.x >= tiles_j * tiles_p) return;
@@ -169,7 +171,6 @@ struct SweepParams {
     int inv_len;     // entries of the per-distance table (float4 each)
     int istart_len;  // ints of the item-start table (multiple of 4)
     int half;        // floats of one staged row (multiple of 4)
-    float h0;
 };
 
 __device__ __forceinline__ float fset_gt(float a, float b)
@@ -300,12 +301,12 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
 // A sweep work item: (direction, skewed row, chunk of lane slots, walk direction).
 struct ItemRow {
     long long rowbase;   // slab offset of the row's first usable sample
-    int L, c, K;
+    int L, c, K, pov;
+    float h0;
     bool rev;
 };
 
 // Decodes item into its row; false when the chunk has no used lane slot.
-template <int P>
 __device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* istart, int item, ItemRow* it)
 {
     int lo = 0, hi = sp.ndir - 1;
@@ -323,8 +324,10 @@ __device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* is
     const int jlo = sp.rowlo[d.row_off + p], jhi = sp.rowhi[d.row_off + p];
     it->L = jhi - jlo + 1;
     it->K = d.K;
+    it->h0 = d.h0;
+    it->pov = d.pov;
     it->rowbase = d.slab + (long long)p * d.Wp + jlo;
-    const int G = (it->L + P - 1) / P;
+    const int G = (it->L + d.pov - 1) / d.pov;
     return it->L > 0 && it->c * 32 < (G + 1) / 2;
 }
 
@@ -340,7 +343,6 @@ __device__ __forceinline__ void prefetch_row_l2(const float* p, int n)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(a), "r"(size) : "memory");
 }
 
-template <int P, int U>
 __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepParams sp)
 {
     extern __shared__ __align__(16) float smem[];
@@ -368,7 +370,7 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
         const int item = next;
         if (item >= sp.total_items) break;
         ItemRow it;
-        if (!decode_item<P>(sp, istart, item, &it)) {
+        if (!decode_item(sp, istart, item, &it)) {
             if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
             next = __shfl_sync(0xffffffffu, next, 0);
             continue;
@@ -395,13 +397,16 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
         if (lane == 0) {
             next = (int)atomicAdd(sp.counter, 1u);
             ItemRow nx;
-            if (next < sp.total_items && decode_item<P>(sp, istart, next, &nx))
+            if (next < sp.total_items && decode_item(sp, istart, next, &nx))
                 prefetch_row_l2(sp.sdem + nx.rowbase, nx.L);
         }
         next = __shfl_sync(0xffffffffu, next, 0);
         __syncwarp();   // the staged row is visible to every lane
-        sweep_lane<P, U>(F, tab, (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase, L, it.c * 32 + lane, it.K,
-                         sp.h0, it.rev);
+        int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
+        if (it.pov == SMALL_POV)
+            sweep_lane<SMALL_POV, SMALL_UNROLL>(F, tab, cvrow, L, it.c * 32 + lane, it.K, it.h0, it.rev);
+        else
+            sweep_lane<LARGE_POV, LARGE_UNROLL>(F, tab, cvrow, L, it.c * 32 + lane, it.K, it.h0, it.rev);
     }
 }
 
@@ -426,22 +431,40 @@ struct UnskewParams {
     const int* cvf;
     const int* cvb;
     const DirDev* dirs;
-    double* vs64;
+    const JobDev* jobs;
+    const ChunkJob* cj;
     double* part;
-    float* out;
-    double scale;
-    int rows, cols, ndir, per_split, nsplit, first, last;
+    long long total_cells;
+    int ncj;
 };
+
+// Entry of the chunk's job table that holds flattened index t (entries are
+// sorted by tile_beg or by cell_beg; `cells` selects which).
+__device__ __forceinline__ int find_chunk_job(const ChunkJob* __restrict__ cj, int ncj, long long t, bool cells)
+{
+    int lo = 0, hi = ncj - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        const long long beg = cells ? cj[mid].cell_beg : (long long)cj[mid].tile_beg;
+        if (beg <= t) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
 
 __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
 {
     __shared__ float T[UNSKEW_ROWS * UNSKEW_PITCH];
-    const int rows = up.rows, cols = up.cols;
-    const int iD0 = blockIdx.y * UNSKEW_TI, jD0 = blockIdx.x * UNSKEW_TJ;
+    const ChunkJob c = up.cj[find_chunk_job(up.cj, up.ncj, blockIdx.x, false)];
+    if ((int)blockIdx.z >= c.nsplit) return;
+    const JobDev J = up.jobs[c.job];
+    const int rows = J.rows, cols = J.cols;
+    const int tile = blockIdx.x - c.tile_beg;
+    const int ty = tile / c.tiles_x, tx = tile - ty * c.tiles_x;
+    const int iD0 = ty * UNSKEW_TI, jD0 = tx * UNSKEW_TJ;
     const int iD1 = min(iD0 + UNSKEW_TI, rows) - 1, jD1 = min(jD0 + UNSKEW_TJ, cols) - 1;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    const int kbeg = blockIdx.z * up.per_split;
-    const int kend = min(kbeg + up.per_split, up.ndir);
+    const int lx = threadIdx.x & 31, ly = threadIdx.x >> 5;
+    const int kbeg = c.dbeg + blockIdx.z * c.per_split;
+    const int kend = min(kbeg + c.per_split, c.dbeg + c.dcnt);
     float acc32[UNSKEW_CELLS];
     double acc64[UNSKEW_CELLS];
 #pragma unroll
@@ -467,16 +490,16 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
         const int np = pmax - pmin + 1, nj = vj1 - vj0 + 1;
         const long long off = d.slab + (long long)pmin * d.Wp + vj0;
         for (int idx = threadIdx.x; idx < np * 32; idx += UNSKEW_THREADS) {
-            const int r = idx >> 5, c = idx & 31;
-            if (c < nj) {
-                const long long a = off + (long long)r * d.Wp + c;
-                T[r * UNSKEW_PITCH + c] = (float)(up.cvf[a] + up.cvb[a]);
+            const int r = idx >> 5, cc = idx & 31;
+            if (cc < nj) {
+                const long long a = off + (long long)r * d.Wp + cc;
+                T[r * UNSKEW_PITCH + cc] = (float)(up.cvf[a] + up.cvb[a]);
             }
         }
         __syncthreads();
 #pragma unroll
         for (int m = 0; m < UNSKEW_CELLS; ++m) {
-            const int iD = iD0 + ty + 8 * m, jD = jD0 + tx;
+            const int iD = iD0 + ly + 8 * m, jD = jD0 + lx;
             if (iD > iD1 || jD > jD1) continue;
             int i, j;
             switch (d.frame) {
@@ -509,32 +532,37 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
         }
         __syncthreads();
     }
+    const long long cells = (long long)rows * cols;
 #pragma unroll
     for (int m = 0; m < UNSKEW_CELLS; ++m) {
-        const int iD = iD0 + ty + 8 * m, jD = jD0 + tx;
+        const int iD = iD0 + ly + 8 * m, jD = jD0 + lx;
         if (iD > iD1 || jD > jD1) continue;
         const long long idx = (long long)iD * cols + jD;
         double tot = acc64[m] + (double)acc32[m];
-        if (up.nsplit > 1) {
-            up.part[(long long)blockIdx.z * rows * cols + idx] = tot;
+        if (c.nsplit > 1) {
+            up.part[c.part_off + (long long)blockIdx.z * cells + idx] = tot;
             continue;
         }
-        if (!up.first) tot += up.vs64[idx];
-        if (up.last) up.out[idx] = (float)(tot * up.scale);
-        else up.vs64[idx] = tot;
+        if (!c.first) tot += J.vs64[idx];
+        if (c.last) J.out[idx] = (float)(tot * J.scale);
+        else J.vs64[idx] = tot;
     }
 }
 
 __global__ void unskew_finalize(UnskewParams up)
 {
-    const long long cells = (long long)up.rows * up.cols;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < cells;
-         idx += (long long)gridDim.x * blockDim.x) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < up.total_cells;
+         t += (long long)gridDim.x * blockDim.x) {
+        const ChunkJob c = up.cj[find_chunk_job(up.cj, up.ncj, t, true)];
+        if (c.nsplit <= 1) continue;
+        const JobDev J = up.jobs[c.job];
+        const long long cells = (long long)J.rows * J.cols;
+        const long long idx = t - c.cell_beg;
         double tot = 0.0;
-        for (int s = 0; s < up.nsplit; ++s) tot += up.part[s * cells + idx];
-        if (!up.first) tot += up.vs64[idx];
-        if (up.last) up.out[idx] = (float)(tot * up.scale);
-        else up.vs64[idx] = tot;
+        for (int z = 0; z < c.nsplit; ++z) tot += up.part[c.part_off + z * cells + idx];
+        if (!c.first) tot += J.vs64[idx];
+        if (c.last) J.out[idx] = (float)(tot * J.scale);
+        else J.vs64[idx] = tot;
     }
 }
 
@@ -556,28 +584,26 @@ cudaError_t launch_colmap(const DirDev* d_dir, int* dest, unsigned* frac, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_skew(const float* dem, int rows, int cols, const DirDev* d_dirs, int ndir,
-                        int max_tiles, const int* rowlo, const int* rowhi, float* sdem,
+cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, int max_tiles, float* sdem,
                         cudaStream_t stream)
 {
-    (void)rows; (void)rowlo; (void)rowhi;
     if (ndir <= 0 || max_tiles <= 0) return cudaSuccess;
     dim3 grid(max_tiles, ndir);
-    skew_kernel<<<grid, 256, 0, stream>>>(dem, cols, d_dirs, sdem);
+    skew_kernel<<<grid, 256, 0, stream>>>(d_jobs, d_dirs, sdem);
     return cudaGetLastError();
 }
 
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
-                         float h0, int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin,
+                         int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin, int max_warps,
                          cudaStream_t stream)
 {
     if (ndir <= 0 || total_items <= 0) return cudaSuccess;
-    constexpr int P = POVS_PER_LANE, U = SWEEP_UNROLL;
+    constexpr int U = LARGE_UNROLL;
     SweepParams sp;
     sp.dirs = d_dirs; sp.item_start = d_item_start; sp.sdem = sdem; sp.rowlo = rowlo;
     sp.rowhi = rowhi; sp.cv_fwd = cv_fwd; sp.cv_bwd = cv_bwd; sp.counter = counter; sp.ndir = ndir;
-    sp.total_items = total_items; sp.h0 = h0;
+    sp.total_items = total_items;
     // the distance table is read up to d = dmax + U (a walk of at most
     // min(K, W) - 1 steps, rounded up to U); dmax <= wmax
     sp.inv_len = (std::min(dmax, wmax) + 2 * U + 8 + 1) & ~1;
@@ -588,17 +614,24 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
     // As many resident warps as shared memory and registers allow, in one CTA per SM
     // (each warp stages its own row; the 1/d table is shared by the CTA).
-    int warps = (int)std::min<size_t>((smem_optin - fixed) / per_warp, (size_t)SWEEP_MAX_WARPS);
+    const int cap = max_warps > 0 ? std::min(max_warps, SWEEP_MAX_WARPS) : SWEEP_MAX_WARPS;
+    int warps = (int)std::min<size_t>((smem_optin - fixed) / per_warp, (size_t)cap);
     const size_t smem = fixed + (size_t)warps * per_warp;
-    cudaError_t err = cudaFuncSetAttribute(sweep_kernel<P, U>,
+    cudaError_t err = cudaFuncSetAttribute(sweep_kernel,
                                            cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel<P, U>, warps * 32, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, warps * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    sweep_kernel<P, U><<<per_sm * num_sms, warps * 32, smem, stream>>>(sp);
+    sweep_kernel<<<per_sm * num_sms, warps * 32, smem, stream>>>(sp);
     return cudaGetLastError();
+}
+
+int sweep_chunks(int W, int pov)
+{
+    const int groups = (W + pov - 1) / pov;
+    return ((groups + 1) / 2 + 31) / 32;
 }
 
 int unskew_per_split(int ndir, int nsplit)
@@ -614,41 +647,38 @@ int unskew_effective_splits(int ndir, int nsplit)
     return (ndir + per - 1) / per;
 }
 
-int unskew_splits(int rows, int cols, int ndir, int num_sms)
+int unskew_tiles_x(int cols) { return (cols + UNSKEW_TJ - 1) / UNSKEW_TJ; }
+
+int unskew_tiles(int rows, int cols) { return unskew_tiles_x(cols) * ((rows + UNSKEW_TI - 1) / UNSKEW_TI); }
+
+int unskew_splits(long long chunk_tiles, int ndir, int num_sms, int ctas_per_sm)
 {
-    const long long tiles = (long long)((cols + UNSKEW_TJ - 1) / UNSKEW_TJ) * ((rows + UNSKEW_TI - 1) / UNSKEW_TI);
-    const long long want = (2LL * num_sms + tiles - 1) / tiles;
+    const long long want = ((long long)std::max(ctas_per_sm, 1) * num_sms + chunk_tiles - 1) / std::max(chunk_tiles, 1LL);
     const int groups = (ndir + FP32_GROUP - 1) / FP32_GROUP;
     return (int)std::max<long long>(1, std::min<long long>(want, groups));
 }
 
-cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, int rows, int cols, const DirDev* d_dirs,
-                          int ndir, int nsplit, double* part, double* vs64, float* out, int first_chunk,
-                          int last_chunk, double scale, cudaStream_t stream)
+cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, const JobDev* d_jobs, const DirDev* d_dirs,
+                          const ChunkJob* d_cj, int ncj, int total_tiles, int max_split, double* part,
+                          cudaStream_t stream)
 {
-    UnskewParams up;
-    up.cvf = cv_fwd; up.cvb = cv_bwd; up.dirs = d_dirs; up.vs64 = vs64; up.part = part; up.out = out;
-    up.scale = scale; up.rows = rows; up.cols = cols; up.ndir = ndir;
-    up.first = first_chunk; up.last = last_chunk;
-    // split the directions into ranges of whole FP32 groups
-    up.per_split = unskew_per_split(ndir, nsplit);
-    up.nsplit = unskew_effective_splits(ndir, nsplit);
-    dim3 grid((cols + UNSKEW_TJ - 1) / UNSKEW_TJ, (rows + UNSKEW_TI - 1) / UNSKEW_TI, up.nsplit);
+    if (ncj <= 0 || total_tiles <= 0) return cudaSuccess;
+    UnskewParams up{};
+    up.cvf = cv_fwd; up.cvb = cv_bwd; up.dirs = d_dirs; up.jobs = d_jobs; up.cj = d_cj; up.part = part;
+    up.ncj = ncj;
+    dim3 grid(total_tiles, 1, std::max(max_split, 1));
     unskew_kernel<<<grid, UNSKEW_THREADS, 0, stream>>>(up);
     return cudaGetLastError();
 }
 
-cudaError_t launch_unskew_finalize(int rows, int cols, int ndir, int nsplit, const double* part, double* vs64,
-                                   float* out, int first_chunk, int last_chunk, double scale,
-                                   cudaStream_t stream)
+cudaError_t launch_unskew_finalize(const JobDev* d_jobs, const ChunkJob* d_cj, int ncj, long long total_cells,
+                                   const double* part, cudaStream_t stream)
 {
+    if (ncj <= 0 || total_cells <= 0) return cudaSuccess;
     UnskewParams up{};
-    up.part = const_cast<double*>(part); up.vs64 = vs64; up.out = out; up.scale = scale;
-    up.rows = rows; up.cols = cols; up.first = first_chunk; up.last = last_chunk;
-    up.nsplit = unskew_effective_splits(ndir, nsplit);
-    if (up.nsplit <= 1) return cudaSuccess;
-    const long long cells = (long long)rows * cols;
-    const int blocks = (int)std::min<long long>((cells + 255) / 256, 4096);
+    up.jobs = d_jobs; up.cj = d_cj; up.ncj = ncj; up.part = const_cast<double*>(part);
+    up.total_cells = total_cells;
+    const int blocks = (int)std::min<long long>((total_cells + 255) / 256, 4096);
     unskew_finalize<<<blocks, 256, 0, stream>>>(up);
     return cudaGetLastError();
 }
