@@ -125,10 +125,10 @@ int tvs_total_viewshed_device(tvs_handle h, const float* d_dem, int rows, int co
  * Every call shares the one array (it keeps the last call's contents; the
  * entry point resets what must start at zero), so calls that overlap on the
  * GPU race: order them on one stream or synchronise between them.
- * Limits: n_sectors <= 1024, and the job must fit 64 MiB: 8 bytes per DEM
- * cell plus 12 bytes per skewed sample of at least one direction (a diagonal
- * direction of an S x S DEM has about 2 S^2 samples, so S <= 1400 fits;
- * larger jobs return TVS_ERR_OOM with a message).
+ * Limits: n_sectors <= 1024, and the job must fit 64 MiB: 16 bytes per DEM
+ * cell (exact running totals) plus 12 bytes per skewed sample of at least one
+ * direction (a diagonal direction of an S x S DEM has about 2 S^2 samples, so
+ * S <= 1290 fits; larger jobs return TVS_ERR_OOM with a message).
  * Errors: TVS_ERR_ARG, TVS_ERR_OOM, TVS_ERR_CUDA. */
 int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, int cols, double step_m,
                                       double obs_height_m, int n_sectors, double max_range_m, float* d_out,
@@ -150,9 +150,13 @@ typedef struct {
  * (section 4.1 applied to each DEM): the (DEM, direction) pairs of all jobs are
  * planned together into chunks that fit the handle's HBM budget, and each chunk
  * runs one launch per kernel for all of its DEMs, so small DEMs share the GPU
- * instead of running one after another.  Each job's result equals what
- * tvs_total_viewshed_device gives for it, up to the order of FP64 additions
- * across chunks.  Stream-ordered like tvs_total_viewshed_device.
+ * instead of running one after another.  Each job's result is bit for bit
+ * what tvs_total_viewshed_device gives for it: per-cell totals are exact sums
+ * of FP32 partial sums over fixed groups of 8 directions, so they do not
+ * depend on which chunk or which CTA added a group (the one exception: a
+ * budget too small for 8 directions of a job cuts inside a group, which moves
+ * results by FP32 rounding only).  Stream-ordered like
+ * tvs_total_viewshed_device.
  * Errors: TVS_ERR_ARG (a bad job: the message names its index), TVS_ERR_OOM,
  * TVS_ERR_CUDA. */
 int tvs_total_viewshed_batch(tvs_handle h, const tvs_job* jobs, int njobs, void* cuda_stream);
@@ -188,7 +192,7 @@ void tvs_batch_destroy(tvs_batch_handle b);
  * sweep_max_warps: warps per sweep CTA, 0 = as many as shared memory allows,
  *   at most 16 (default 0);
  * unskew_ctas_per_sm: a chunk whose DEMs have fewer cell tiles than this many
- *   per SM splits its directions into ranges across CTAs (default 2). */
+ *   per SM splits its directions into ranges across CTAs (1 to 4, default 2). */
 typedef struct {
     int32_t small_pov_below_w;
     int32_t sweep_max_warps;
@@ -238,6 +242,106 @@ int tvs_profile_enable(tvs_handle h, int on);
 /* Read the per-kernel counters (synchronises the recorded events).  Writes up
  * to max entries to stats and their number to *count. */
 int tvs_profile_read(tvs_handle h, tvs_kernel_stats* stats, int max, int* count);
+
+/* ------------------------------------------------------- request server --
+ * Serving total viewsheds to callers that submit DEMs as they arrive (the
+ * paper computes one DEM at a time; this is an addition).  A server owns one
+ * device allocation of hbm_budget_bytes, split into `lanes` step scratch slots
+ * of step_slot_bytes and a resident arena that holds, for every admitted
+ * request, its DEM, its output and its exact running totals (24 bytes per
+ * cell).  Requests are admitted in submission order while the arena has room
+ * and fewer than max_active are admitted.  A scheduler thread runs the GPU in
+ * steps: one step is one pass of the pipeline (row map, skew, sweep, unskew)
+ * over slices of several admitted requests' directions, whole groups of 8
+ * directions at a time, taken in policy order until about step_evals
+ * evaluations are in the step.  A request that arrives while steps run joins
+ * the next step; with 2 lanes the next step is enqueued while the current one
+ * runs.  Results are exact-sum totals, so each request's output is bit for bit
+ * what tvs_total_viewshed gives for it alone, whatever it shared its steps
+ * with.  Finished outputs are copied to the caller's host buffer.
+ * All server calls are thread-safe. */
+typedef struct tvs_server* tvs_server_handle;
+
+#define TVS_POLICY_DEADLINE 0  /* earliest (submit time + evals / rate_hint) first */
+#define TVS_POLICY_FIFO     1  /* submission order */
+#define TVS_POLICY_SRPT     2  /* fewest remaining evaluations first */
+
+typedef struct {
+    size_t  hbm_budget_bytes;  /* whole server; 0 = min(80 GiB, 85% of free memory) */
+    size_t  step_slot_bytes;   /* scratch of one lane; 0 = min(4 GiB, budget / 8) */
+    double  step_evals;        /* evaluations per step; 0 = 4e10 */
+    double  rate_hint;         /* evaluations per second the deadline policy assumes; 0 = 5e12 */
+    int32_t max_active;        /* admitted requests at once; 0 = 256 */
+    int32_t policy;            /* TVS_POLICY_*; 0 = deadline */
+    int32_t lanes;             /* steps in flight, 1 or 2; 0 = 2 */
+    int32_t pad_;
+} tvs_server_config;
+
+#define TVS_REQ_QUEUED   0     /* submitted, waiting for arena room */
+#define TVS_REQ_ADMITTED 1     /* resident, no step yet */
+#define TVS_REQ_RUNNING  2     /* in at least one enqueued step */
+#define TVS_REQ_DONE     3     /* output copied to the caller's buffer */
+#define TVS_REQ_FAILED   4     /* see error and message */
+
+typedef struct {
+    int32_t state;             /* TVS_REQ_* */
+    int32_t error;             /* TVS_OK, or the failure's TVS_ERR_* code */
+    int32_t steps;             /* steps that carried directions of the request */
+    int32_t n_sectors;
+    double  t_submit;          /* seconds on the server clock (tvs_server_clock) */
+    double  t_admit;           /* -1 until admitted */
+    double  t_first;           /* first step enqueued, -1 before */
+    double  t_done;            /* completion observed, -1 before */
+    double  evals;             /* work count of the request */
+    char    message[128];      /* failure message, "" otherwise */
+} tvs_request_info;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t steps;             /* steps enqueued */
+    int64_t kernels;           /* kernel launches enqueued */
+    double  evals;             /* evaluations enqueued */
+    double  arena_bytes;       /* resident arena size */
+    double  arena_peak_bytes;  /* most of it ever in use */
+    int32_t queued, active;    /* right now */
+    int32_t max_step_jobs;     /* most requests one step carried */
+    int32_t lanes;
+} tvs_server_stats;
+
+/* Create a server on `device` (cfg may be NULL: all defaults).  Errors:
+ * TVS_ERR_ARG (bad config), TVS_ERR_OOM (the budget cannot be allocated or
+ * leaves no arena), TVS_ERR_CUDA. */
+int tvs_server_create(int device, const tvs_server_config* cfg, tvs_server_handle* out);
+
+/* Submit one total viewshed.  dem (rows*cols float32, host memory, finite) and
+ * out (rows*cols float32, host memory) must stay valid and untouched until the
+ * request is DONE or FAILED; page-locked buffers make the copies asynchronous.
+ * The other arguments mean what they mean for tvs_total_viewshed.  Returns at
+ * once with the request's ticket.  Errors: TVS_ERR_ARG, TVS_ERR_OOM (the
+ * request can never fit the arena or one 8-direction group of it can never
+ * fit a step slot), TVS_ERR_STATE (the server is shutting down or failed). */
+int tvs_server_submit(tvs_server_handle s, const float* dem, int rows, int cols, double step_m,
+                      double obs_height_m, int n_sectors, double max_range_m, float* out, int64_t* ticket);
+
+/* Wait until the request is DONE (returns TVS_OK) or FAILED (returns its
+ * error), or until timeout_s seconds passed (TVS_ERR_TIMEOUT; < 0 waits
+ * without limit).  TVS_ERR_ARG for an unknown ticket. */
+int tvs_server_wait(tvs_server_handle s, int64_t ticket, double timeout_s);
+
+/* State and timestamps of a request. */
+int tvs_server_query(tvs_server_handle s, int64_t ticket, tvs_request_info* info);
+
+/* Counters of the server. */
+int tvs_server_get_stats(tvs_server_handle s, tvs_server_stats* stats);
+
+/* Seconds since the server was created (steady clock; the t_* fields of
+ * tvs_request_info use it). */
+double tvs_server_clock(tvs_server_handle s);
+
+/* Stop the server: requests not yet admitted fail with TVS_ERR_STATE,
+ * admitted ones run to completion, then the threads exit and the device
+ * memory is released.  NULL is accepted. */
+void tvs_server_destroy(tvs_server_handle s);
 
 #ifdef __cplusplus
 }

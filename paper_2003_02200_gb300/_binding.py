@@ -52,6 +52,29 @@ class Tuning(C.Structure):
                 ("unskew_ctas_per_sm", C.c_int32), ("pad_", C.c_int32)]
 
 
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("step_slot_bytes", C.c_size_t), ("step_evals", C.c_double),
+                ("rate_hint", C.c_double), ("max_active", C.c_int32), ("policy", C.c_int32),
+                ("lanes", C.c_int32), ("pad_", C.c_int32)]
+
+
+class RequestInfo(C.Structure):
+    _fields_ = [("state", C.c_int32), ("error", C.c_int32), ("steps", C.c_int32), ("n_sectors", C.c_int32),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_first", C.c_double),
+                ("t_done", C.c_double), ("evals", C.c_double), ("message", C.c_char * 128)]
+
+
+class ServerStats(C.Structure):
+    _fields_ = [("submitted", C.c_int64), ("completed", C.c_int64), ("failed", C.c_int64), ("steps", C.c_int64),
+                ("kernels", C.c_int64), ("evals", C.c_double), ("arena_bytes", C.c_double),
+                ("arena_peak_bytes", C.c_double), ("queued", C.c_int32), ("active", C.c_int32),
+                ("max_step_jobs", C.c_int32), ("lanes", C.c_int32)]
+
+
+POLICIES = {"deadline": 0, "fifo": 1, "srpt": 2}
+REQUEST_STATES = {0: "queued", 1: "admitted", 2: "running", 3: "done", 4: "failed"}
+
+
 class KernelStats(C.Structure):
     _fields_ = [("name", C.c_char * 32), ("launches", C.c_int64), ("total_ms", C.c_double),
                 ("units", C.c_double), ("unit", C.c_char * 16)]
@@ -107,6 +130,14 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             "tvs_debug_rowmap": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, i32p], C.c_int),
             "tvs_debug_direction_cv": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
+            "tvs_server_create": ([C.c_int, C.POINTER(ServerConfig), C.POINTER(vp)], C.c_int),
+            "tvs_server_submit": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
+                                   i64p], C.c_int),
+            "tvs_server_wait": ([vp, C.c_int64, C.c_double], C.c_int),
+            "tvs_server_query": ([vp, C.c_int64, C.POINTER(RequestInfo)], C.c_int),
+            "tvs_server_get_stats": ([vp, C.POINTER(ServerStats)], C.c_int),
+            "tvs_server_clock": ([vp], C.c_double),
+            "tvs_server_destroy": ([vp], None),
             "tvs_profile_enable": ([vp, C.c_int], C.c_int),
             "tvs_profile_read": ([vp, C.POINTER(KernelStats), C.c_int, C.POINTER(C.c_int)], C.c_int),
         }
@@ -114,7 +145,6 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             fn = getattr(lib, name)
             fn.argtypes = args
             fn.restype = res
-        _ = i64p
         _lib = lib
         return lib
 
@@ -348,3 +378,89 @@ class Context:
         return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
                                            units=arr[i].units, unit=arr[i].unit.decode())
                 for i in range(cnt.value)}
+
+
+class Server:
+    """A request server (tvs_server_create): requests on host arrays are
+    submitted as they arrive, admitted by the server's HBM budget and run in
+    shared GPU steps (continuous batching).  submit() returns a ticket at once;
+    wait() returns the finished visible-area map.  The arrays passed to
+    submit() are kept alive here until their request finishes; page-locked
+    arrays (e.g. numpy views of pinned torch tensors) make the copies
+    asynchronous."""
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, step_slot_bytes: int = 0,
+                 step_evals: float = 0.0, rate_hint: float = 0.0, max_active: int = 0, policy: str = "deadline",
+                 lanes: int = 0):
+        self._lib = load()
+        if policy not in POLICIES:
+            raise ValueError(f"policy must be one of {sorted(POLICIES)}")
+        cfg = ServerConfig(hbm_budget_bytes, step_slot_bytes, step_evals, rate_hint, max_active, POLICIES[policy],
+                           lanes, 0)
+        h = C.c_void_p()
+        _check(self._lib.tvs_server_create(device, C.byref(cfg), C.byref(h)))
+        self._s = h
+        self._live: dict[int, tuple[np.ndarray, np.ndarray]] = {}
+        self._mu = threading.Lock()
+
+    @property
+    def handle(self) -> C.c_void_p:
+        if not self._s:
+            raise RuntimeError("server is closed")
+        return self._s
+
+    def submit(self, dem, step_m: float, obs_height_m: float, n_sectors: int = 180, max_range_m: float = 0.0,
+               out: np.ndarray | None = None) -> int:
+        a = _dem(dem)
+        if out is None:
+            out = np.empty_like(a)
+        if out.shape != a.shape or out.dtype != np.float32 or not out.flags.c_contiguous:
+            raise ValueError("out must be a C-contiguous float32 array shaped like dem")
+        t = C.c_int64(0)
+        _check(self._lib.tvs_server_submit(self.handle, a.ctypes.data, a.shape[0], a.shape[1], step_m, obs_height_m,
+                                           n_sectors, max_range_m, out.ctypes.data, C.byref(t)))
+        with self._mu:
+            self._live[t.value] = (a, out)
+        return t.value
+
+    def wait(self, ticket: int, timeout: float = -1.0) -> np.ndarray:
+        """Block until the request finishes; returns its output (raises
+        TvsError on failure or timeout)."""
+        _check(self._lib.tvs_server_wait(self.handle, ticket, timeout))
+        with self._mu:
+            _, out = self._live.pop(ticket)
+        return out
+
+    def query(self, ticket: int) -> dict:
+        i = RequestInfo()
+        _check(self._lib.tvs_server_query(self.handle, ticket, C.byref(i)))
+        d = {f: getattr(i, f) for f, _ in RequestInfo._fields_}
+        d["message"] = i.message.decode()
+        d["state_name"] = REQUEST_STATES.get(i.state, str(i.state))
+        return d
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(self._lib.tvs_server_get_stats(self.handle, C.byref(st)))
+        return {f: getattr(st, f) for f, _ in ServerStats._fields_}
+
+    def clock(self) -> float:
+        return float(self._lib.tvs_server_clock(self.handle))
+
+    def close(self) -> None:
+        if getattr(self, "_s", None):
+            self._lib.tvs_server_destroy(self._s)
+            self._s = None
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,7 +1,9 @@
-// tvs_api.cu -- host side of the C ABI declared in include/tvs.h: argument
-// checks, the direction table, chunking of the directions under the HBM
-// budget, kernel launches and per-kernel timing.
+// tvs_api.cu -- the C ABI declared in include/tvs.h for single DEMs, batches,
+// prepared (graph-replayed) batches, tuning and the no-allocation entry point.
+// Planning and launch sequencing live in tvs_plan.cu, the request server in
+// tvs_server.cu.
 #include "tvs.h"
+#include "tvs_host.h"
 #include "tvs_internal.h"
 
 #include <cuda_runtime.h>
@@ -16,626 +18,6 @@
 #include <vector>
 
 using namespace tvs;
-
-namespace {
-
-thread_local std::string g_err;
-
-int fail(int code, const std::string& msg)
-{
-    g_err = msg;
-    return code;
-}
-
-int cuda_fail(cudaError_t e, const char* where)
-{
-    return fail(TVS_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
-}
-
-#define TVS_CUDA(call, where)                              \
-    do {                                                   \
-        cudaError_t e_ = (call);                           \
-        if (e_ != cudaSuccess) return cuda_fail(e_, where); \
-    } while (0)
-
-constexpr int kMaxDim = 16384;        // longest walk axis the staged sweep supports
-constexpr int kMaxChunkDirs = 1024;   // directions per chunk (bounds the item table in smem)
-constexpr long long kMaxChunkItems = 1LL << 30;  // sweep warp items per chunk
-constexpr double kTwo32 = 4294967296.0;
-
-// ---------------------------------------------------------- directions --
-// Direction k of n: theta_k = k*pi/n from +j (east) toward +i (south).  Alg. 6
-// covers 0..45 degrees; the rest of the half-plane reuses it through a D4 view
-// chosen by integer tests on k, with the reduced angle alpha = pi*m/(2n):
-//   4k <  n : identity,                  m = 2k
-//   4k < 2n : transpose,                 m = n - 2k
-//   4k < 3n : transpose + mirror columns, m = 2k - n
-//   else    : mirror rows,               m = 2n - 2k
-// tan(alpha) is held in 32.32 fixed point; g = 1 + t^2 is the (1/cos s)^2
-// factor of Alg. 7 for that t.
-struct HostDir {
-    int frame, m, H, W, D, R;
-    unsigned long long t_fx;
-    double t, g;
-    long long K;  // LLONG_MAX = unlimited
-};
-
-int make_direction(int n, int k, int rows, int cols, double step, double max_range, HostDir* d)
-{
-    if (n < 1 || k < 0 || k >= n || rows < 2 || cols < 2 || !(step > 0.0) || std::isnan(max_range))
-        return TVS_ERR_ARG;
-    const long long k4 = 4LL * k;
-    if (k4 < n) { d->frame = 0; d->m = 2 * k; d->H = rows; d->W = cols; }
-    else if (k4 < 2LL * n) { d->frame = 1; d->m = n - 2 * k; d->H = cols; d->W = rows; }
-    else if (k4 < 3LL * n) { d->frame = 2; d->m = 2 * k - n; d->H = cols; d->W = rows; }
-    else { d->frame = 3; d->m = 2 * n - 2 * k; d->H = rows; d->W = cols; }
-    const double alpha = M_PI * (double)d->m / (2.0 * (double)n);
-    d->t_fx = (unsigned long long)std::llround(std::tan(alpha) * kTwo32);
-    d->t = (double)d->t_fx / kTwo32;
-    d->g = 1.0 + d->t * d->t;
-    if (!(max_range > 0.0) || std::isinf(max_range)) {
-        d->K = LLONG_MAX;
-    } else {
-        const double kk = std::floor(max_range / (step * std::sqrt(d->g)));
-        d->K = kk >= 9.0e18 ? LLONG_MAX : (long long)kk;
-    }
-    d->D = (int)(((unsigned long long)(d->W - 1) * d->t_fx) >> 32);
-    d->R = d->H + d->D;
-    return TVS_OK;
-}
-
-// Usable columns of skewed row p (base row p - D): 0 <= (p-D) + j*t <= H-1.
-void host_row_range(const HostDir& d, int p, int* lo, int* hi)
-{
-    const long long b = (long long)p - d.D;
-    long long l = 0, h;
-    if (d.t_fx == 0ull) {
-        h = (b >= 0 && b <= d.H - 1) ? d.W - 1 : -1;
-    } else {
-        if (b < 0) l = (long long)((((unsigned long long)(-b) << 32) + d.t_fx - 1ull) / d.t_fx);
-        const long long top = (long long)d.H - 1 - b;
-        h = top < 0 ? -1 : (long long)(((unsigned long long)top << 32) / d.t_fx);
-        if (h > d.W - 1) h = d.W - 1;
-    }
-    if (l > h) { l = 0; h = -1; }
-    *lo = (int)l;
-    *hi = (int)h;
-}
-
-long long sum_min(long long L, long long K)
-{
-    // sum_{x=0}^{L-1} min(x, K)
-    if (L <= 0) return 0;
-    if (L - 1 <= K) return (L - 1) * L / 2;
-    return K * (K + 1) / 2 + (L - 1 - K) * K;
-}
-
-struct DirWork {
-    long long evals;        // targets visited (work count)
-    long long samples;      // usable samples (virtual POVs)
-};
-
-DirWork direction_work(const HostDir& d)
-{
-    DirWork w{0, 0};
-    const long long K = d.K == LLONG_MAX ? (long long)d.W : std::min<long long>(d.K, d.W);
-    for (int p = 0; p < d.R; ++p) {
-        int lo, hi;
-        host_row_range(d, p, &lo, &hi);
-        const long long L = hi - lo + 1;
-        if (L <= 0) continue;
-        w.samples += L;
-        w.evals += 2 * sum_min(L, K);
-    }
-    return w;
-}
-
-int check_job(int rows, int cols, double step_m, double obs_height_m, int n_sectors, double max_range_m)
-{
-    if (rows < 2 || cols < 2) return fail(TVS_ERR_ARG, "rows and cols must be >= 2");
-    if (rows > kMaxDim || cols > kMaxDim)
-        return fail(TVS_ERR_ARG, "rows and cols must be <= 16384 (shared-memory row staging limit)");
-    if (!(step_m > 0.0) || !std::isfinite(step_m)) return fail(TVS_ERR_ARG, "step_m must be finite and > 0");
-    if (!std::isfinite(obs_height_m)) return fail(TVS_ERR_ARG, "obs_height_m must be finite");
-    if (n_sectors < 1 || n_sectors > 1 << 20) return fail(TVS_ERR_ARG, "n_sectors must be in [1, 2^20]");
-    if (std::isnan(max_range_m)) return fail(TVS_ERR_ARG, "max_range_m is NaN");
-    return TVS_OK;
-}
-
-// ------------------------------------------------------------ profiling --
-enum KernelId { K_ROWMAP = 0, K_SKEW, K_SWEEP, K_UNSKEW, K_FINAL, K_COUNT };
-const char* kKernelName[K_COUNT] = {"rowmap", "skew", "sweep", "unskew", "unskew_finalize"};
-const char* kKernelUnit[K_COUNT] = {"bytes", "bytes", "evals", "bytes", "bytes"};
-
-// Tunable launch choices (see tvs_tuning in tvs.h).
-struct Tuning {
-    int small_pov_below_w = 768;   // walk axes shorter than this use SMALL_POV groups
-    int sweep_max_warps = 0;       // 0 = as many as shared memory allows (up to SWEEP_MAX_WARPS)
-    int unskew_ctas_per_sm = 2;    // split a chunk's directions below this many unskew CTAs per SM
-};
-
-int pov_for(const Tuning& tn, int W) { return W < tn.small_pov_below_w ? SMALL_POV : LARGE_POV; }
-
-struct Pending {
-    int kernel;
-    cudaEvent_t start, stop;
-    double units;
-};
-
-}  // namespace
-
-struct tvs_ctx {
-    int device = 0;
-    size_t budget = 0;
-    int num_sms = 0;
-    cudaStream_t stream = nullptr;   // the handle's own stream (host-memory API)
-    char* ws = nullptr;              // device scratch
-    size_t ws_bytes = 0;
-    int smem_optin = 0;              // max dynamic shared memory per block
-    char* pinned = nullptr;          // pinned staging of the per-call table upload
-    size_t pinned_bytes = 0;
-    cudaEvent_t pinned_done = nullptr;  // the last upload from `pinned` has been read
-    Tuning tuning;
-    bool profiling = false;
-    std::vector<Pending> pending;
-    tvs_kernel_stats stats[K_COUNT];
-};
-
-namespace {
-
-struct Timer {
-    tvs_ctx* h;
-    int kernel;
-    cudaStream_t s;
-    double units;
-    cudaEvent_t a = nullptr, b = nullptr;
-    Timer(tvs_ctx* h_, int k, cudaStream_t s_, double u) : h(h_), kernel(k), s(s_), units(u)
-    {
-        if (h && h->profiling && cudaEventCreate(&a) == cudaSuccess && cudaEventCreate(&b) == cudaSuccess)
-            cudaEventRecord(a, s);
-    }
-    ~Timer()
-    {
-        if (a && b) {
-            cudaEventRecord(b, s);
-            h->pending.push_back(Pending{kernel, a, b, units});
-        }
-    }
-};
-
-void drain_pending(tvs_ctx* h)
-{
-    for (auto& p : h->pending) {
-        float ms = 0.f;
-        if (cudaEventSynchronize(p.stop) == cudaSuccess && cudaEventElapsedTime(&ms, p.start, p.stop) == cudaSuccess) {
-            tvs_kernel_stats& s = h->stats[p.kernel];
-            s.launches += 1;
-            s.total_ms += ms;
-            s.units += p.units;
-        }
-        cudaEventDestroy(p.start);
-        cudaEventDestroy(p.stop);
-    }
-    h->pending.clear();
-}
-
-void reset_stats(tvs_ctx* h)
-{
-    for (int k = 0; k < K_COUNT; ++k) {
-        std::memset(&h->stats[k], 0, sizeof(tvs_kernel_stats));
-        std::snprintf(h->stats[k].name, sizeof(h->stats[k].name), "%s", kKernelName[k]);
-        std::snprintf(h->stats[k].unit, sizeof(h->stats[k].unit), "%s", kKernelUnit[k]);
-    }
-}
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
-
-int ensure_scratch(tvs_ctx* h, size_t bytes)
-{
-    if (bytes <= h->ws_bytes) return TVS_OK;
-    if (h->ws) {
-        cudaError_t e = cudaDeviceSynchronize();
-        if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceSynchronize before scratch growth");
-        cudaFree(h->ws);
-        h->ws = nullptr;
-        h->ws_bytes = 0;
-    }
-    cudaError_t e = cudaMalloc(&h->ws, bytes);
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        h->ws = nullptr;
-        return fail(TVS_ERR_OOM, std::string("cudaMalloc of scratch failed: ") + cudaGetErrorString(e));
-    }
-    h->ws_bytes = bytes;
-    return TVS_OK;
-}
-
-// A DEM of a call: device pointers and parameters.
-struct JobSpec {
-    const float* dem;
-    float* out;
-    int rows, cols, n;
-    double step, h0, max_range;
-};
-
-// A planned chunk: the consecutive (job, direction) instances [i0, i1).
-struct Chunk {
-    int i0, i1;
-    size_t slab_elems;       // sum of R * Wp over the chunk
-    long long rows;          // sum of R
-    int items;               // sweep warp items
-    int max_R, max_tiles, wmax, dmax;
-    int cj_beg, ncj;         // the chunk's entries of the chunk-job table
-    int total_tiles, max_split;
-    long long total_cells, part_elems;
-    int istart_at;           // offset of the chunk's item table
-    double evals, skew_bytes, unskew_bytes, rowmap_bytes, final_bytes;
-};
-
-struct BatchPlan {
-    std::vector<JobSpec> jobs;
-    std::vector<int> inst_job, inst_k;   // per instance
-    std::vector<HostDir> hdirs;          // per instance
-    std::vector<DirDev> dirs;            // per instance (slab / row offsets relative to its chunk)
-    std::vector<Chunk> chunks;
-    std::vector<ChunkJob> cj;            // every chunk's job entries, chunk after chunk
-    std::vector<int> istart;             // every chunk's item table
-    std::vector<long long> vs64_off;     // per job, -1 when the job lives in one chunk
-    long long vs64_elems = 0;
-    size_t max_slab = 0;
-    long long max_rows = 0, max_part = 0;
-    double evals = 0;
-};
-
-size_t chunk_bytes(size_t slab, long long rows, int ninst)
-{
-    // skewed heights + forward measures + backward measures, row tables, item table
-    return align256(slab * 4) * 3 + align256((size_t)rows * 4) * 2 + align256((size_t)(ninst + 1) * 4);
-}
-
-// Upper bound of the FP64 partials of a split unskew: splits only happen when
-// a chunk's jobs have fewer than 2 cell tiles per SM, so the partials cover at
-// most about 4 tiles of 1024 cells per SM.
-size_t part_bound(int num_sms) { return align256((size_t)(4 * num_sms + 4) * UNSKEW_TI * UNSKEW_TJ * 8); }
-
-// Plans the instances of `jobs` (job after job, directions in order) into
-// chunks whose scratch fits `avail` bytes.  Cuts fall on multiples of
-// FP32_GROUP directions of a job where possible, so a job's FP32 group sums do
-// not depend on the chunking.  only_k >= 0 keeps only direction only_k of a
-// single job (test hook).
-int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, const Tuning& tn, BatchPlan* plan,
-               int only_k = -1)
-{
-    plan->jobs = jobs;
-    for (int j = 0; j < (int)jobs.size(); ++j) {
-        const JobSpec& J = jobs[j];
-        for (int k = 0; k < J.n; ++k) {
-            if (only_k >= 0 && k != only_k) continue;
-            HostDir d;
-            if (make_direction(J.n, k, J.rows, J.cols, J.step, J.max_range, &d))
-                return fail(TVS_ERR_ARG, "bad direction arguments");
-            plan->hdirs.push_back(d);
-            plan->inst_job.push_back(j);
-            plan->inst_k.push_back(k);
-        }
-    }
-    const int ninst = (int)plan->hdirs.size();
-    plan->dirs.resize(ninst);
-    int i = 0;
-    while (i < ninst) {
-        size_t slab = 0, slab_ok = 0;
-        long long nrows = 0, rows_ok = 0, items = 0;
-        int ii = i, last_ok = -1;
-        while (ii < ninst) {
-            const HostDir& d = plan->hdirs[ii];
-            const size_t wp = (size_t)((d.W + 3) & ~3);
-            const size_t s2 = slab + (size_t)d.R * wp;
-            const long long r2 = nrows + d.R;
-            const long long it2 = items + 2LL * d.R * sweep_chunks(d.W, pov_for(tn, d.W));
-            if (ii > i && (chunk_bytes(s2, r2, ii - i + 1) > avail || ii - i >= kMaxChunkDirs ||
-                           it2 > kMaxChunkItems))
-                break;
-            slab = s2;
-            nrows = r2;
-            items = it2;
-            ++ii;
-            const int kk = plan->inst_k[ii - 1], jj = plan->inst_job[ii - 1];
-            if ((kk + 1) % FP32_GROUP == 0 || kk + 1 == jobs[jj].n || ii == ninst) {
-                last_ok = ii; slab_ok = slab; rows_ok = nrows;
-            }
-        }
-        if (chunk_bytes(slab, nrows, ii - i) > avail)
-            return fail(TVS_ERR_OOM, "one direction does not fit the HBM budget");
-        if (last_ok > i && ii < ninst) { ii = last_ok; slab = slab_ok; nrows = rows_ok; }
-        Chunk c{};
-        c.i0 = i;
-        c.i1 = ii;
-        plan->chunks.push_back(c);
-        i = ii;
-    }
-    const int njobs = (int)jobs.size();
-    std::vector<int> first_chunk(njobs, -1), last_chunk(njobs, -1);
-    for (int q = 0; q < (int)plan->chunks.size(); ++q)
-        for (int t = plan->chunks[q].i0; t < plan->chunks[q].i1; ++t) {
-            const int j = plan->inst_job[t];
-            if (first_chunk[j] < 0) first_chunk[j] = q;
-            last_chunk[j] = q;
-        }
-    plan->vs64_off.assign(njobs, -1);
-    for (int j = 0; j < njobs; ++j)
-        if (first_chunk[j] >= 0 && first_chunk[j] != last_chunk[j]) {
-            plan->vs64_off[j] = plan->vs64_elems;
-            plan->vs64_elems += (long long)jobs[j].rows * jobs[j].cols;
-        }
-    for (int q = 0; q < (int)plan->chunks.size(); ++q) {
-        Chunk& c = plan->chunks[q];
-        size_t off = 0;
-        long long roff = 0;
-        c.istart_at = (int)plan->istart.size();
-        plan->istart.push_back(0);
-        for (int t = c.i0; t < c.i1; ++t) {
-            const HostDir& d = plan->hdirs[t];
-            const JobSpec& J = jobs[plan->inst_job[t]];
-            DirDev& v = plan->dirs[t];
-            std::memset(&v, 0, sizeof(v));
-            v.t_fx = d.t_fx;
-            v.slab = (long long)off;
-            v.frame = d.frame; v.H = d.H; v.W = d.W; v.Wp = (d.W + 3) & ~3;
-            v.D = d.D; v.R = d.R;
-            v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
-            v.row_off = (int)roff;
-            v.pov = pov_for(tn, d.W);
-            v.chunks = sweep_chunks(d.W, v.pov);
-            v.gidx = plan->inst_k[t];
-            v.job = plan->inst_job[t];
-            v.g = (float)d.g;
-            v.h0 = (float)J.h0;
-            off += (size_t)d.R * v.Wp;
-            roff += d.R;
-            c.items += 2 * d.R * v.chunks;
-            plan->istart.push_back(c.items);
-            c.max_R = std::max(c.max_R, d.R);
-            c.max_tiles = std::max(c.max_tiles, ((d.R + SKEW_TP - 1) / SKEW_TP) * ((d.W + SKEW_TJ - 1) / SKEW_TJ));
-            c.wmax = std::max(c.wmax, d.W);
-            c.dmax = std::max(c.dmax, v.K);
-            const DirWork w = direction_work(d);
-            c.evals += (double)w.evals;
-            c.skew_bytes += 4.0 * J.rows * J.cols + 4.0 * (double)w.samples;
-            c.unskew_bytes += 8.0 * (double)w.samples;
-            c.rowmap_bytes += 8.0 * d.R;
-        }
-        c.slab_elems = off;
-        c.rows = roff;
-        plan->evals += c.evals;
-        plan->max_slab = std::max(plan->max_slab, off);
-        plan->max_rows = std::max(plan->max_rows, roff);
-        // the chunk's jobs, in instance order (a job's instances are contiguous)
-        c.cj_beg = (int)plan->cj.size();
-        long long tiles = 0;
-        for (int t = c.i0; t < c.i1;) {
-            int u = t;
-            while (u < c.i1 && plan->inst_job[u] == plan->inst_job[t]) ++u;
-            tiles += unskew_tiles(jobs[plan->inst_job[t]].rows, jobs[plan->inst_job[t]].cols);
-            t = u;
-        }
-        c.total_tiles = (int)tiles;
-        int tile_beg = 0;
-        long long cell_beg = 0;
-        for (int t = c.i0; t < c.i1;) {
-            int u = t;
-            const int j = plan->inst_job[t];
-            while (u < c.i1 && plan->inst_job[u] == j) ++u;
-            const JobSpec& J = jobs[j];
-            ChunkJob e{};
-            e.job = j;
-            e.dbeg = t - c.i0;
-            e.dcnt = u - t;
-            e.tile_beg = tile_beg;
-            e.tiles_x = unskew_tiles_x(J.cols);
-            e.first = first_chunk[j] == q;
-            e.last = last_chunk[j] == q;
-            const int want = unskew_splits(tiles, e.dcnt, num_sms, tn.unskew_ctas_per_sm);
-            e.per_split = unskew_per_split(e.dcnt, want);
-            e.nsplit = unskew_effective_splits(e.dcnt, want);
-            e.cell_beg = cell_beg;
-            const long long cells = (long long)J.rows * J.cols;
-            e.part_off = -1;
-            if (e.nsplit > 1) { e.part_off = c.part_elems; c.part_elems += e.nsplit * cells; }
-            c.max_split = std::max(c.max_split, e.nsplit);
-            c.total_cells += cells;
-            c.final_bytes += e.nsplit > 1 ? 8.0 * cells * (e.nsplit + 1) : 0.0;
-            c.unskew_bytes += (e.first ? 0.0 : 8.0 * cells) + (e.last ? 4.0 * cells : 8.0 * cells);
-            tile_beg += unskew_tiles(J.rows, J.cols);
-            cell_beg += cells;
-            plan->cj.push_back(e);
-            t = u;
-        }
-        c.ncj = (int)plan->cj.size() - c.cj_beg;
-        plan->max_part = std::max(plan->max_part, c.part_elems);
-    }
-    return TVS_OK;
-}
-
-// Scratch layout of a planned batch (byte offsets).  The header (directions,
-// jobs, chunk-job entries, item tables) is one contiguous block, uploaded with
-// one copy.
-struct Layout {
-    size_t hdr, dirs, jobs, cj, istart, hdr_bytes;
-    size_t io_dem, io_out, counter, vs64, part, rowlo, rowhi, sdem, cvf, cvb, total;
-};
-
-Layout make_layout(const BatchPlan& plan, bool host_io)
-{
-    Layout L{};
-    size_t o = 0;
-    L.hdr = o;
-    L.dirs = o;    o += align256(plan.dirs.size() * sizeof(DirDev));
-    L.jobs = o;    o += align256(plan.jobs.size() * sizeof(JobDev));
-    L.cj = o;      o += align256(plan.cj.size() * sizeof(ChunkJob));
-    L.istart = o;  o += align256(plan.istart.size() * 4);
-    L.hdr_bytes = o - L.hdr;
-    const size_t cells = host_io ? (size_t)plan.jobs[0].rows * plan.jobs[0].cols : 0;
-    L.io_dem = o;  o += align256(cells * 4);
-    L.io_out = o;  o += align256(cells * 4);
-    L.counter = o; o += 256;
-    L.vs64 = o;    o += align256((size_t)plan.vs64_elems * 8);
-    L.part = o;    o += align256((size_t)plan.max_part * 8);
-    L.rowlo = o;   o += align256((size_t)plan.max_rows * 4);
-    L.rowhi = o;   o += align256((size_t)plan.max_rows * 4);
-    L.sdem = o;    o += align256(plan.max_slab * 4);
-    L.cvf = o;     o += align256(plan.max_slab * 4);
-    L.cvb = o;     o += align256(plan.max_slab * 4);
-    L.total = o;
-    return L;
-}
-
-// Bytes a batch needs besides its chunks' slabs (header, host copies of a
-// single job, FP64 totals of every job, partials bound, counter).
-size_t fixed_bytes(const std::vector<JobSpec>& jobs, bool host_io, int num_sms)
-{
-    size_t ninst = 0, cells = 0;
-    for (const JobSpec& J : jobs) { ninst += J.n; cells += (size_t)J.rows * J.cols; }
-    size_t b = align256(ninst * sizeof(DirDev)) + align256(jobs.size() * sizeof(JobDev)) +
-               align256((jobs.size() + ninst) * sizeof(ChunkJob)) + align256((2 * ninst + 1) * 4) + 4096;
-    if (host_io) b += 2 * align256((size_t)jobs[0].rows * jobs[0].cols * 4);
-    return b + align256(cells * 8) + part_bound(num_sms);
-}
-
-// Host image of the header for the scratch at `base`.
-void build_header(const BatchPlan& plan, const Layout& L, char* base, bool host_io, std::vector<char>* img)
-{
-    img->assign(L.hdr_bytes, 0);
-    std::memcpy(img->data() + (L.dirs - L.hdr), plan.dirs.data(), plan.dirs.size() * sizeof(DirDev));
-    std::vector<JobDev> jd(plan.jobs.size());
-    for (size_t j = 0; j < plan.jobs.size(); ++j) {
-        const JobSpec& J = plan.jobs[j];
-        jd[j].dem = host_io ? reinterpret_cast<const float*>(base + L.io_dem) : J.dem;
-        jd[j].out = host_io ? reinterpret_cast<float*>(base + L.io_out) : J.out;
-        jd[j].vs64 = plan.vs64_off[j] >= 0 ? reinterpret_cast<double*>(base + L.vs64) + plan.vs64_off[j] : nullptr;
-        jd[j].scale = (M_PI / (2.0 * (double)J.n)) * (J.step * J.step);
-        jd[j].rows = J.rows;
-        jd[j].cols = J.cols;
-    }
-    std::memcpy(img->data() + (L.jobs - L.hdr), jd.data(), jd.size() * sizeof(JobDev));
-    std::memcpy(img->data() + (L.cj - L.hdr), plan.cj.data(), plan.cj.size() * sizeof(ChunkJob));
-    std::memcpy(img->data() + (L.istart - L.hdr), plan.istart.data(), plan.istart.size() * 4);
-}
-
-// Enqueue every chunk of a planned batch whose header already sits at base +
-// L.hdr: per chunk row map -> skew -> sweep -> unskew (-> finalize).
-int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* base, int num_sms, int smem_optin,
-                   int max_warps, cudaStream_t s)
-{
-    const DirDev* d_dirs = reinterpret_cast<const DirDev*>(base + L.dirs);
-    const JobDev* d_jobs = reinterpret_cast<const JobDev*>(base + L.jobs);
-    const ChunkJob* d_cj = reinterpret_cast<const ChunkJob*>(base + L.cj);
-    const int* d_istart = reinterpret_cast<const int*>(base + L.istart);
-    unsigned* d_counter = reinterpret_cast<unsigned*>(base + L.counter);
-    double* d_part = reinterpret_cast<double*>(base + L.part);
-    int* d_rowlo = reinterpret_cast<int*>(base + L.rowlo);
-    int* d_rowhi = reinterpret_cast<int*>(base + L.rowhi);
-    float* d_sdem = reinterpret_cast<float*>(base + L.sdem);
-    int* d_cvf = reinterpret_cast<int*>(base + L.cvf);
-    int* d_cvb = reinterpret_cast<int*>(base + L.cvb);
-    for (const Chunk& c : plan.chunks) {
-        const int nd = c.i1 - c.i0;
-        const DirDev* cd = d_dirs + c.i0;
-        {
-            Timer t(h, K_ROWMAP, s, c.rowmap_bytes);
-            TVS_CUDA(launch_rowmap(cd, nd, c.max_R, d_rowlo, d_rowhi, s), "rowmap launch");
-        }
-        {
-            Timer t(h, K_SKEW, s, c.skew_bytes);
-            TVS_CUDA(launch_skew(d_jobs, cd, nd, c.max_tiles, d_sdem, s), "skew launch");
-        }
-        TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
-        {
-            Timer t(h, K_SWEEP, s, c.evals);
-            TVS_CUDA(launch_sweep(cd, d_istart + c.istart_at, nd, c.items, d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                                  c.wmax, c.dmax, d_counter, num_sms, smem_optin, max_warps, s),
-                     "sweep launch");
-        }
-        {
-            Timer t(h, K_UNSKEW, s, c.unskew_bytes);
-            TVS_CUDA(launch_unskew(d_cvf, d_cvb, d_jobs, cd, d_cj + c.cj_beg, c.ncj, c.total_tiles, c.max_split,
-                                   d_part, s),
-                     "unskew launch");
-        }
-        if (c.max_split > 1) {
-            Timer t(h, K_FINAL, s, c.final_bytes);
-            TVS_CUDA(launch_unskew_finalize(d_jobs, d_cj + c.cj_beg, c.ncj, c.total_cells, d_part, s),
-                     "unskew finalize launch");
-        }
-    }
-    return TVS_OK;
-}
-
-// Copy a header image to the device through the handle's pinned staging
-// buffer.  The buffer is reused by the next call only after the copy that
-// read it has run (event), so the host never blocks on earlier GPU work.
-int upload_header(tvs_ctx* h, const std::vector<char>& img, void* dst, cudaStream_t s)
-{
-    if (h->pinned_done) TVS_CUDA(cudaEventSynchronize(h->pinned_done), "wait for staging buffer");
-    if (img.size() > h->pinned_bytes) {
-        if (h->pinned) cudaFreeHost(h->pinned);
-        h->pinned = nullptr;
-        h->pinned_bytes = 0;
-        TVS_CUDA(cudaHostAlloc((void**)&h->pinned, img.size(), cudaHostAllocDefault), "cudaHostAlloc");
-        h->pinned_bytes = img.size();
-    }
-    std::memcpy(h->pinned, img.data(), img.size());
-    TVS_CUDA(cudaMemcpyAsync(dst, h->pinned, img.size(), cudaMemcpyHostToDevice, s), "copy tables");
-    if (!h->pinned_done) TVS_CUDA(cudaEventCreateWithFlags(&h->pinned_done, cudaEventDisableTiming), "event");
-    TVS_CUDA(cudaEventRecord(h->pinned_done, s), "record staging event");
-    return TVS_OK;
-}
-
-// Plan, size the scratch and enqueue a batch on the handle.  With host_io the
-// single job's DEM is copied in from host memory and its map copied back.
-int run_batch(tvs_ctx* h, const std::vector<JobSpec>& jobs, cudaStream_t s, bool host_io, const float* host_dem,
-              float* host_out)
-{
-    const size_t fixed = fixed_bytes(jobs, host_io, h->num_sms);
-    if (fixed >= h->budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
-    BatchPlan plan;
-    int rc = plan_batch(jobs, h->budget - fixed, h->num_sms, h->tuning, &plan);
-    if (rc) return rc;
-    const Layout L = make_layout(plan, host_io);
-    rc = ensure_scratch(h, L.total);
-    if (rc) return rc;
-    char* base = h->ws;
-    std::vector<char> img;
-    build_header(plan, L, base, host_io, &img);
-    if (host_io) {
-        const size_t bytes = (size_t)jobs[0].rows * jobs[0].cols * 4;
-        TVS_CUDA(cudaMemcpyAsync(base + L.io_dem, host_dem, bytes, cudaMemcpyHostToDevice, s), "copy dem");
-    }
-    rc = upload_header(h, img, base + L.hdr, s);
-    if (rc) return rc;
-    rc = enqueue_chunks(h, plan, L, base, h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, s);
-    if (rc) return rc;
-    if (host_io) {
-        const size_t bytes = (size_t)jobs[0].rows * jobs[0].cols * 4;
-        TVS_CUDA(cudaMemcpyAsync(host_out, base + L.io_out, bytes, cudaMemcpyDeviceToHost, s), "copy out");
-        TVS_CUDA(cudaStreamSynchronize(s), "synchronize");
-    }
-    return TVS_OK;
-}
-
-struct DeviceGuard {
-    int prev = -1;
-    explicit DeviceGuard(int dev)
-    {
-        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
-        if (prev != dev) cudaSetDevice(dev);
-    }
-    ~DeviceGuard()
-    {
-        if (prev >= 0) cudaSetDevice(prev);
-    }
-};
-
-}  // namespace
 
 // ================================================================== C ABI ==
 extern "C" {
@@ -738,12 +120,10 @@ int tvs_direction(int n_sectors, int k, int rows, int cols, double step_m, doubl
 int64_t tvs_count_evals(int rows, int cols, int n_sectors, double step_m, double max_range_m)
 {
     if (check_job(rows, cols, step_m, 0.0, n_sectors, max_range_m)) return TVS_ERR_ARG;
+    std::vector<DirWork> w;
+    job_work(n_sectors, rows, cols, step_m, max_range_m, 0, n_sectors, &w);
     int64_t E = 0;
-    for (int k = 0; k < n_sectors; ++k) {
-        HostDir d;
-        make_direction(n_sectors, k, rows, cols, step_m, max_range_m, &d);
-        E += direction_work(d).evals;
-    }
+    for (const DirWork& x : w) E += x.evals;
     return E;
 }
 
@@ -942,9 +322,9 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     const size_t o_job = o_dirs + align256((size_t)n_sectors * sizeof(DirDev));
     const size_t o_cj = o_job + align256(sizeof(JobDev));
     const size_t o_istart = o_cj + align256((size_t)n_sectors * sizeof(ChunkJob));
-    const size_t o_vs64 = o_istart + align256((size_t)(2 * n_sectors + 1) * 4);
-    const size_t o_part = o_vs64 + align256(cells * 8);
-    const size_t o_counter = o_part + (nsplit_max > 1 ? align256((size_t)nsplit_max * cells * 8) : 0);
+    const size_t o_acc = o_istart + align256((size_t)(2 * n_sectors + 1) * 4);
+    const size_t o_part = o_acc + align256(cells * 16);
+    const size_t o_counter = o_part + (nsplit_max > 1 ? align256((size_t)nsplit_max * cells * 16) : 0);
     const size_t o_chunk = o_counter + 256;
     if (o_chunk >= kNoAllocScratchBytes)
         return fail(TVS_ERR_OOM, "the DEM does not fit the 64 MiB no-allocation scratch");
@@ -953,8 +333,8 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     {
         int k = 0;
         while (k < n_sectors) {
-            size_t slab = 0, nrows = 0;
-            int kk = k;
+            size_t slab = 0, nrows = 0, slab_ok = 0, rows_ok = 0;
+            int kk = k, kk_ok = -1;
             while (kk < n_sectors) {
                 HostDir d;
                 make_direction(n_sectors, kk, rows, cols, step_m, max_range_m, &d);
@@ -973,9 +353,12 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 slab = s2;
                 nrows = r2;
                 ++kk;
+                if (kk % FP32_GROUP == 0 || kk == n_sectors) { kk_ok = kk; slab_ok = slab; rows_ok = nrows; }
             }
             if (kk == k)
                 return fail(TVS_ERR_OOM, "one direction of this DEM does not fit the 64 MiB no-allocation scratch");
+            // cut on a group boundary when one fits, so the FP32 group sums match the allocating path
+            if (kk < n_sectors && kk_ok > k) { kk = kk_ok; slab = slab_ok; nrows = rows_ok; }
             chunk_k0[nchunks++] = k;
             max_rows = std::max(max_rows, nrows);
             max_slab = std::max(max_slab, slab);
@@ -1005,7 +388,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     JobDev job;
     job.dem = d_dem;
     job.out = d_out;
-    job.vs64 = nchunks > 1 ? reinterpret_cast<double*>(base + o_vs64) : nullptr;
+    job.acc = nchunks > 1 ? reinterpret_cast<__int128*>(base + o_acc) : nullptr;
     job.scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
     job.rows = rows;
     job.cols = cols;
@@ -1013,7 +396,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     JobDev* d_job = reinterpret_cast<JobDev*>(base + o_job);
     ChunkJob* d_cj = reinterpret_cast<ChunkJob*>(base + o_cj);
     int* d_istart = reinterpret_cast<int*>(base + o_istart);
-    double* d_part = reinterpret_cast<double*>(base + o_part);
+    __int128* d_part = reinterpret_cast<__int128*>(base + o_part);
     unsigned* d_counter = reinterpret_cast<unsigned*>(base + o_counter);
     int* d_rowlo = reinterpret_cast<int*>(base + o_chunk);
     int* d_rowhi = reinterpret_cast<int*>(base + o_chunk + align256(max_rows * 4));
@@ -1201,7 +584,7 @@ int tvs_set_tuning(tvs_handle h, const tvs_tuning* t)
 {
     if (!h || !t) return fail(TVS_ERR_ARG, "NULL argument");
     if (t->small_pov_below_w < 0 || t->sweep_max_warps < 0 || t->sweep_max_warps > SWEEP_MAX_WARPS ||
-        t->unskew_ctas_per_sm < 1)
+        t->unskew_ctas_per_sm < 1 || t->unskew_ctas_per_sm > 4)
         return fail(TVS_ERR_ARG, "tuning out of range");
     h->tuning.small_pov_below_w = t->small_pov_below_w;
     h->tuning.sweep_max_warps = t->sweep_max_warps;

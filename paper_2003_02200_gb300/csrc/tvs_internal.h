@@ -52,11 +52,17 @@ struct DirDev {
     int pov;                   // sweep group size, SMALL_POV or LARGE_POV
 };
 
+// Per-cell totals are exact: each FP32 group sum (FP32_GROUP directions) is
+// converted to a signed fixed-point integer with ACC_FRAC_BITS fractional bits
+// and added in 128-bit integer arithmetic, so a total does not depend on the
+// order in which chunks, CTAs or steps add their groups.
+constexpr int ACC_FRAC_BITS = 56;
+
 // One DEM of a call (a batch holds several).
 struct JobDev {
     const float* dem;          // rows x cols elevations (device)
     float* out;                // rows x cols visible areas (device)
-    double* vs64;              // FP64 running totals when the job spans several chunks, else NULL
+    __int128* acc;             // exact running totals when the job spans several chunks, else NULL
     double scale;              // (pi / (2n)) * step^2
     int rows, cols;
 };
@@ -64,7 +70,7 @@ struct JobDev {
 // One job's share of a chunk of directions, for the unskew and its finalize.
 struct ChunkJob {
     long long cell_beg;        // first cell of the job in the chunk's flattened cell space
-    long long part_off;        // FP64 partials of a split unskew: offset in the partials buffer
+    long long part_off;        // exact partials of a split unskew: offset in the partials buffer
     int job;                   // index in the job table
     int dbeg, dcnt;            // the job's directions in the chunk (chunk-local)
     int tile_beg;              // first unskew tile of the job in the chunk's flattened tiles
@@ -90,11 +96,11 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
 // Unskew of a chunk: `total_tiles` flattened cell tiles over the chunk's jobs
 // (ncj entries of d_cj, sorted by tile_beg), `max_split` the largest nsplit.
 cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, const JobDev* d_jobs, const DirDev* d_dirs,
-                          const ChunkJob* d_cj, int ncj, int total_tiles, int max_split, double* part,
+                          const ChunkJob* d_cj, int ncj, int total_tiles, int max_split, __int128* part,
                           cudaStream_t stream);
-// Adds the FP64 partials of the chunk's split jobs (a no-op entry for the others).
+// Adds the exact partials of the chunk's split jobs (a no-op entry for the others).
 cudaError_t launch_unskew_finalize(const JobDev* d_jobs, const ChunkJob* d_cj, int ncj, long long total_cells,
-                                   const double* part, cudaStream_t stream);
+                                   const __int128* part, cudaStream_t stream);
 
 // Number of direction ranges for one job of a chunk whose jobs have
 // `chunk_tiles` cell tiles in all (1 when the chunk fills the GPU).

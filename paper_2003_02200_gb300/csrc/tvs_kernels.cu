@@ -417,11 +417,13 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
 // reads, then every cell takes g * ((1-r) cv_hi + r cv_lo) (Kernel-3 weights;
 // a virtual POV whose sample falls outside the DEM is dropped and the other
 // takes weight 1), cv being the forward plus the backward measure.  Partial
-// sums are FP32 over groups of FP32_GROUP consecutive directions and FP64
-// across groups.  With one range per CTA the result goes straight to the FP64
-// running total (or, for the last chunk, through the FP64 (pi/(2n)) step^2
-// scale to the FP32 output); with several ranges each writes an FP64 partial
-// that unskew_finalize adds in a fixed order.
+// sums are FP32 over groups of FP32_GROUP consecutive directions; each group
+// sum is added exactly (fixed point, 128-bit integers) to the cell's total.
+// With one range per CTA the total goes to the job's running totals (or, for
+// the job's last directions, through the FP64 (pi/(2n)) step^2 scale to the
+// FP32 output); with several ranges each writes a partial total that
+// unskew_finalize adds.  Integer addition being exact, the result does not
+// depend on the ranges, the chunking or the other jobs of a chunk.
 constexpr int UNSKEW_ROWS = UNSKEW_TI + UNSKEW_TJ + 4;
 constexpr int UNSKEW_PITCH = UNSKEW_TJ + 1;
 constexpr int UNSKEW_THREADS = 256;
@@ -433,10 +435,38 @@ struct UnskewParams {
     const DirDev* dirs;
     const JobDev* jobs;
     const ChunkJob* cj;
-    double* part;
+    __int128* part;
     long long total_cells;
     int ncj;
 };
+
+// x * 2^ACC_FRAC_BITS as an integer, from the bit pattern of a finite float:
+// exact for |x| >= 2^-(ACC_FRAC_BITS - 23) and |x| < 2^67 (every non-zero
+// group sum this pipeline forms is in that range: blend weights are at least
+// 2^-32 and totals stay below 2^52), truncated toward zero below.
+__device__ __forceinline__ __int128 acc_of(float x)
+{
+    const unsigned b = __float_as_uint(x);
+    const int e = (int)((b >> 23) & 0xffu);
+    unsigned long long m = b & 0x7fffffu;
+    if (e != 0) m |= 0x800000u;
+    const int sh = (e == 0 ? 1 : e) - 150 + ACC_FRAC_BITS;     // x = m * 2^(sh - ACC_FRAC_BITS)
+    __int128 v;
+    if (sh >= 0) v = (__int128)m << min(sh, 100);
+    else v = sh > -32 ? (__int128)(m >> -sh) : (__int128)0;
+    return (b >> 31) ? -v : v;
+}
+
+// FP32 visible area of an exact total: total * 2^-ACC_FRAC_BITS * scale.
+__device__ __forceinline__ float area_of(__int128 v, double scale)
+{
+    const long long hi = (long long)(v >> 64);
+    const unsigned long long lo = (unsigned long long)v;
+    // hi * 2^64 is exact (totals stay below 2^108); (double)lo and the sum round once each
+    const double t = __dadd_rn(__dmul_rn((double)hi, 0x1p64), (double)lo);
+    return __double2float_rn(__dmul_rn(__dmul_rn(t, 0x1p-56), scale));
+}
+static_assert(ACC_FRAC_BITS == 56, "area_of scales by 2^-56");
 
 // Entry of the chunk's job table that holds flattened index t (entries are
 // sorted by tile_beg or by cell_beg; `cells` selects which).
@@ -466,16 +496,16 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
     const int kbeg = c.dbeg + blockIdx.z * c.per_split;
     const int kend = min(kbeg + c.per_split, c.dbeg + c.dcnt);
     float acc32[UNSKEW_CELLS];
-    double acc64[UNSKEW_CELLS];
+    __int128 accx[UNSKEW_CELLS];
 #pragma unroll
-    for (int m = 0; m < UNSKEW_CELLS; ++m) { acc32[m] = 0.f; acc64[m] = 0.0; }
+    for (int m = 0; m < UNSKEW_CELLS; ++m) { acc32[m] = 0.f; accx[m] = 0; }
     int group = kbeg < kend ? up.dirs[kbeg].gidx / FP32_GROUP : 0;
 
     for (int kk = kbeg; kk < kend; ++kk) {
         const DirDev d = up.dirs[kk];
         if (d.gidx / FP32_GROUP != group) {
 #pragma unroll
-            for (int m = 0; m < UNSKEW_CELLS; ++m) { acc64[m] += (double)acc32[m]; acc32[m] = 0.f; }
+            for (int m = 0; m < UNSKEW_CELLS; ++m) { accx[m] += acc_of(acc32[m]); acc32[m] = 0.f; }
             group = d.gidx / FP32_GROUP;
         }
         int vi0, vi1, vj0, vj1;
@@ -538,14 +568,14 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
         const int iD = iD0 + ly + 8 * m, jD = jD0 + lx;
         if (iD > iD1 || jD > jD1) continue;
         const long long idx = (long long)iD * cols + jD;
-        double tot = acc64[m] + (double)acc32[m];
+        __int128 tot = accx[m] + acc_of(acc32[m]);
         if (c.nsplit > 1) {
             up.part[c.part_off + (long long)blockIdx.z * cells + idx] = tot;
             continue;
         }
-        if (!c.first) tot += J.vs64[idx];
-        if (c.last) J.out[idx] = (float)(tot * J.scale);
-        else J.vs64[idx] = tot;
+        if (!c.first) tot += J.acc[idx];
+        if (c.last) J.out[idx] = area_of(tot, J.scale);
+        else J.acc[idx] = tot;
     }
 }
 
@@ -558,11 +588,11 @@ __global__ void unskew_finalize(UnskewParams up)
         const JobDev J = up.jobs[c.job];
         const long long cells = (long long)J.rows * J.cols;
         const long long idx = t - c.cell_beg;
-        double tot = 0.0;
+        __int128 tot = 0;
         for (int z = 0; z < c.nsplit; ++z) tot += up.part[c.part_off + z * cells + idx];
-        if (!c.first) tot += J.vs64[idx];
-        if (c.last) J.out[idx] = (float)(tot * J.scale);
-        else J.vs64[idx] = tot;
+        if (!c.first) tot += J.acc[idx];
+        if (c.last) J.out[idx] = area_of(tot, J.scale);
+        else J.acc[idx] = tot;
     }
 }
 
@@ -659,7 +689,7 @@ int unskew_splits(long long chunk_tiles, int ndir, int num_sms, int ctas_per_sm)
 }
 
 cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, const JobDev* d_jobs, const DirDev* d_dirs,
-                          const ChunkJob* d_cj, int ncj, int total_tiles, int max_split, double* part,
+                          const ChunkJob* d_cj, int ncj, int total_tiles, int max_split, __int128* part,
                           cudaStream_t stream)
 {
     if (ncj <= 0 || total_tiles <= 0) return cudaSuccess;
@@ -672,11 +702,11 @@ cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, const JobDev* d_
 }
 
 cudaError_t launch_unskew_finalize(const JobDev* d_jobs, const ChunkJob* d_cj, int ncj, long long total_cells,
-                                   const double* part, cudaStream_t stream)
+                                   const __int128* part, cudaStream_t stream)
 {
     if (ncj <= 0 || total_cells <= 0) return cudaSuccess;
     UnskewParams up{};
-    up.jobs = d_jobs; up.cj = d_cj; up.ncj = ncj; up.part = const_cast<double*>(part);
+    up.jobs = d_jobs; up.cj = d_cj; up.ncj = ncj; up.part = const_cast<__int128*>(part);
     up.total_cells = total_cells;
     const int blocks = (int)std::min<long long>((total_cells + 255) / 256, 4096);
     unskew_finalize<<<blocks, 256, 0, stream>>>(up);

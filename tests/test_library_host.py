@@ -61,6 +61,18 @@ def test_host_argument_errors(lib):
     assert lib.tvs_total_viewshed(None, None, 4, 4, 1.0, 1.0, 4, 0.0, None) == tvs._binding.TVS_ERR_ARG
     lib.tvs_destroy(None)
     del h
+    # request server: argument checks that need no GPU
+    t = C.c_int64(0)
+    assert lib.tvs_server_create(0, None, None) == tvs._binding.TVS_ERR_ARG
+    bad = tvs._binding.ServerConfig(0, 0, 0.0, 0.0, 0, 7, 0, 0)          # unknown policy
+    assert lib.tvs_server_create(0, C.byref(bad), C.byref(C.c_void_p())) == tvs._binding.TVS_ERR_ARG
+    bad = tvs._binding.ServerConfig(0, 0, -1.0, 0.0, 0, 0, 0, 0)         # negative step size
+    assert lib.tvs_server_create(0, C.byref(bad), C.byref(C.c_void_p())) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_server_submit(None, None, 4, 4, 1.0, 1.0, 4, 0.0, None, C.byref(t)) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_server_wait(None, 1, 0.0) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_server_query(None, 1, None) == tvs._binding.TVS_ERR_ARG
+    assert lib.tvs_server_clock(None) == 0.0
+    lib.tvs_server_destroy(None)
 
 
 def test_create_without_gpu_fails_cleanly():
@@ -69,6 +81,9 @@ def test_create_without_gpu_fails_cleanly():
         pytest.skip("a GPU is present")
     with pytest.raises(tvs.TvsError) as ei:
         tvs.Context(0)
+    assert ei.value.code == tvs._binding.TVS_ERR_CUDA
+    with pytest.raises(tvs.TvsError) as ei:
+        tvs.Server(0)
     assert ei.value.code == tvs._binding.TVS_ERR_CUDA
 
 

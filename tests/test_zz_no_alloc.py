@@ -20,8 +20,12 @@ from paper_2003_02200_gb300 import terrain
 
 pytestmark = pytest.mark.gpu
 
-# same bound as the chunked-budget parity test: only FP64 association moves
-RTOL = 2e-7
+# Chunks of the no-allocation path are cut on 8-direction group boundaries
+# when 8 directions fit its array, and the per-cell totals are exact sums of
+# FP32 group sums: the result is then bit for bit the allocating path's.  A
+# job whose 8 directions do not fit is cut inside groups, which moves results
+# by FP32 rounding of the group sums only.
+RTOL_INSIDE_GROUPS = 1e-6
 
 
 def _reference(dem_t, step, h0, n, rng):
@@ -44,8 +48,8 @@ def _noalloc(lib, dem_t, step, h0, n, rng):
     return out.cpu().numpy()
 
 
-@pytest.mark.parametrize("rows,cols,n,rng", [(300, 260, 96, 0.0), (640, 480, 45, 1500.0)])
-def test_noalloc_matches_allocating_entry_point_twice(rows, cols, n, rng):
+@pytest.mark.parametrize("rows,cols,n,rng,exact", [(300, 260, 96, 0.0, True), (640, 480, 45, 1500.0, False)])
+def test_noalloc_matches_allocating_entry_point_twice(rows, cols, n, rng, exact):
     import torch
     lib = tvs.load()
     dem = terrain.fractal_dem(rows, cols, 0.8, 800.0, seed=rows + cols)
@@ -53,7 +57,10 @@ def test_noalloc_matches_allocating_entry_point_twice(rows, cols, n, rng):
     want = _reference(d, 10.0, 1.5, n, rng)
     for _ in range(2):
         got = _noalloc(lib, d, 10.0, 1.5, n, rng)
-        np.testing.assert_allclose(got, want, rtol=RTOL, atol=0)
+        if exact:
+            np.testing.assert_array_equal(got, want)
+        else:
+            np.testing.assert_allclose(got, want, rtol=RTOL_INSIDE_GROUPS, atol=0)
 
 
 def test_noalloc_refuses_a_job_larger_than_its_array():
