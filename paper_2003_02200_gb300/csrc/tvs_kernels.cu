@@ -171,6 +171,7 @@ struct SweepParams {
     int inv_len;     // entries of the per-distance table (float4 each)
     int istart_len;  // ints of the item-start table (multiple of 4)
     int half;        // floats of one staged row (multiple of 4)
+    int per_warp;    // floats of a warp's shared area: the staged row, then (long rows) 64 x LARGE_POV spill ints
 };
 
 __device__ __forceinline__ float fset_gt(float a, float b)
@@ -210,6 +211,15 @@ __device__ __forceinline__ void sweep_block(const float* w, const float4* __rest
     }
 }
 
+// Walks of more than LONG_WALK steps (rows longer than the constant, with a
+// range beyond it) move their FP32 partial measures into integers every
+// FLUSH_STEPS steps: a measure is a sum of odd integers 2d + 1 and stays exact
+// in FP32 only below 2^24 (a walk of D steps sums to at most D^2 + 2D, and
+// FLUSH_STEPS steps at d < 16384 add at most 1.3e7).  Shorter walks never
+// flush (the LONG = false instantiation).
+constexpr int LONG_WALK = 4000;
+constexpr int FLUSH_STEPS = 384;   // a multiple of SMALL_UNROLL and LARGE_UNROLL
+
 // One lane of a warp item: forward walks of two groups of P consecutive POVs
 // of the staged row F (group s and its mirror G-1-s, so that every lane walks
 // about one row length in total).  F holds the row (or the reversed row for
@@ -218,10 +228,13 @@ __device__ __forceinline__ void sweep_block(const float* w, const float4* __rest
 // sentinel that is never visible.  A walk's measure is
 // cv = 1 + sum_{d=1}^{n-1} v_d (2d + 1) for n >= 1 targets, which is Alg. 8's
 // sum of d^2 - open^2 over its closed segments plus the segment still open at
-// the end (closed at the last target).
-template <int P, int U>
+// the end (closed at the last target).  With LONG, `spill` is the lane's
+// column (stride 32) of 2P integers: the flushed parts of group 0, then of
+// group 1.
+template <int P, int U, bool LONG>
 __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const float4* __restrict__ tab,
-                                           int* __restrict__ cvrow, int L, int slot, int K, float h0, bool rev)
+                                           int* __restrict__ cvrow, int* __restrict__ spill, int L, int slot, int K,
+                                           float h0, bool rev)
 {
     const float NEG = neg_inf();
     const int G = (L + P - 1) / P;
@@ -234,6 +247,8 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
     float h[P], M[P];
     float2 acc2[P / 2];
     float first[P];                  // measure sums of group 0 once group 1 starts
+    int* sg = spill;                 // flushed parts of the current group (LONG)
+    int seg = FLUSH_STEPS;           // next flush (LONG)
     int x0 = gsel[0] * P;
     int rowlim = L - 2 - x0;         // last target adding area, POV q = 0
     int dlim = min(klim, rowlim);
@@ -243,8 +258,21 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
     for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; first[q] = 0.f; }
 #pragma unroll
     for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+    if (LONG) {
+#pragma unroll
+        for (int q = 0; q < 2 * P; ++q) spill[32 * q] = 0;
+    }
     int e = 0;
     for (;;) {
+        if (LONG && e >= seg) {
+            seg += FLUSH_STEPS;
+#pragma unroll
+            for (int q = 0; q < P; q += 2) {
+                sg[32 * q] += __float2int_rz(acc2[q / 2].x);
+                sg[32 * (q + 1)] += __float2int_rz(acc2[q / 2].y);
+                acc2[q / 2] = make_float2(0.f, 0.f);
+            }
+        }
         if (e >= dlim) {
             if (second || ng == 1) break;
 #pragma unroll
@@ -258,6 +286,7 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
             for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; }
 #pragma unroll
             for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+            if (LONG) { sg = spill + 32 * P; seg = FLUSH_STEPS; }
             e = 0;
             continue;
         }
@@ -282,7 +311,7 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
         const int x = xa + q;
         if (x < L) {
             const int n = min(L - 1 - x, K);
-            cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sa : 0;
+            cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sa + (LONG ? spill[32 * q] : 0) : 0;
         }
     }
     if (second) {
@@ -292,7 +321,7 @@ __device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const fl
             const int x = xb + q;
             if (x < L) {
                 const int n = min(L - 1 - x, K);
-                cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sb : 0;
+                cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sb + (LONG ? spill[32 * (P + q)] : 0) : 0;
             }
         }
     }
@@ -349,7 +378,8 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
     float4* tab = reinterpret_cast<float4*>(smem);
     int* istart = reinterpret_cast<int*>(smem + 4 * sp.inv_len);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* F = smem + 4 * sp.inv_len + sp.istart_len + warp * sp.half;
+    float* F = smem + 4 * sp.inv_len + sp.istart_len + warp * sp.per_warp;
+    int* spill = reinterpret_cast<int*>(F + sp.half) + lane;
     // per distance d = m + 1: (1/d, 1/d, 2d + 1, 2d + 1); 1/d correctly rounded
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
         const float r = __frcp_rn((float)(m + 1));
@@ -403,10 +433,18 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
         next = __shfl_sync(0xffffffffu, next, 0);
         __syncwarp();   // the staged row is visible to every lane
         int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
-        if (it.pov == SMALL_POV)
-            sweep_lane<SMALL_POV, SMALL_UNROLL>(F, tab, cvrow, L, it.c * 32 + lane, it.K, it.h0, it.rev);
-        else
-            sweep_lane<LARGE_POV, LARGE_UNROLL>(F, tab, cvrow, L, it.c * 32 + lane, it.K, it.h0, it.rev);
+        const int slot = it.c * 32 + lane;
+        if (L - 2 > LONG_WALK && it.K - 1 > LONG_WALK) {
+            if (it.pov == SMALL_POV)
+                sweep_lane<SMALL_POV, SMALL_UNROLL, true>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
+            else
+                sweep_lane<LARGE_POV, LARGE_UNROLL, true>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
+        } else {
+            if (it.pov == SMALL_POV)
+                sweep_lane<SMALL_POV, SMALL_UNROLL, false>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
+            else
+                sweep_lane<LARGE_POV, LARGE_UNROLL, false>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
+        }
     }
 }
 
@@ -639,8 +677,9 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
     sp.inv_len = (std::min(dmax, wmax) + 2 * U + 8 + 1) & ~1;
     sp.istart_len = (ndir + 1 + 3) & ~3;
     sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
+    sp.per_warp = sp.half + (wmax - 2 > LONG_WALK ? 64 * LARGE_POV : 0);
     const size_t fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
-    const size_t per_warp = (size_t)sp.half * 4;
+    const size_t per_warp = (size_t)sp.per_warp * 4;
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
     // As many resident warps as shared memory and registers allow, in one CTA per SM
     // (each warp stages its own row; the 1/d table is shared by the CTA).

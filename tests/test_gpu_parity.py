@@ -114,6 +114,19 @@ def test_direction_cv_long_rows_and_range(ctx, orc, rows, cols, n, k, rng, h0):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("cols,rng", [(9000, 0.0), (6100, 52000.0)])
+def test_direction_cv_long_walks_stay_exact(ctx, orc, cols, rng):
+    """Walks of several thousand steps on flat ground see every target, so
+    their measures reach L^2 (above 2^24, where FP32 sums of odd integers stop
+    being exact): the sweep moves its FP32 partial measures into integers
+    before that."""
+    dem = np.zeros((2, cols), np.float32)
+    got = ctx.debug_direction_cv(dem, 10.0, 1.5, 4, rng, 0)
+    want = oracle_cv_slab(orc, dem, 10.0, 1.5, 4, rng, 0)
+    assert want.max() > 1 << 24
+    assert np.array_equal(got, want)
+
+
 # ---------------------------------------------------------- total viewshed --
 
 def test_tvs100_matches_fp32_oracle_and_fp64_tolerance(ctx, orc):
