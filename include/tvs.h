@@ -186,9 +186,12 @@ int tvs_batch_get_info(tvs_batch_handle b, tvs_batch_info* info);
 void tvs_batch_destroy(tvs_batch_handle b);
 
 /* Launch choices of a handle (no effect on results, only on speed).
- * small_pov_below_w: skewed rows of directions whose walk axis is shorter
- *   than this are swept with 4 POVs per lane group, longer ones with 8
- *   (default 768);
+ * small_pov_below_w: every skewed row of a direction whose walk axis is
+ *   shorter than this is swept with 4 POVs per lane group (default 0: none);
+ * p4_cost_pct: the other rows pick 4 or 8 POVs per lane group row by row,
+ *   whichever needs fewer warp items x walk steps x POVs x step cost, where a
+ *   4-POV step costs p4_cost_pct percent of an 8-POV step per POV (default
+ *   107; 1 << 20 keeps every such row on 8; 0 in tvs_set_tuning = default);
  * sweep_max_warps: warps per sweep CTA, 0 = as many as shared memory allows,
  *   at most 16 (default 0);
  * unskew_ctas_per_sm: a chunk whose DEMs have fewer cell tiles than this many
@@ -197,7 +200,7 @@ typedef struct {
     int32_t small_pov_below_w;
     int32_t sweep_max_warps;
     int32_t unskew_ctas_per_sm;
-    int32_t pad_;
+    int32_t p4_cost_pct;
 } tvs_tuning;
 
 int tvs_get_tuning(tvs_handle h, tvs_tuning* t);

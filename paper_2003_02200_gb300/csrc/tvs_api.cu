@@ -140,6 +140,7 @@ int tvs_debug_rowmap(tvs_handle h, int rows, int cols, int n_sectors, int k, int
     DirDev v{};
     v.t_fx = d.t_fx; v.frame = d.frame; v.H = d.H; v.W = d.W; v.Wp = (d.W + 3) & ~3;
     v.D = d.D; v.R = d.R; v.K = d.W; v.row_off = 0; v.chunks = 1; v.gidx = k; v.g = (float)d.g;
+    v.pov = LARGE_POV; v.p4_pct = 100;
     const size_t need = align256(sizeof(DirDev)) + 4 * align256((size_t)std::max(d.R, d.W) * 4);
     rc = ensure_scratch(h, need);
     if (rc) return rc;
@@ -341,14 +342,16 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 const size_t wp = (size_t)((d.W + 3) & ~3);
                 const size_t s2 = slab + (size_t)d.R * wp, r2 = nrows + d.R;
                 const size_t need = 2 * align256(r2 * 4) + 3 * align256(s2 * 4);
-                if (need > avail || 2LL * (long long)r2 * sweep_chunks(d.W, pov_for(tn, d.W)) > kMaxChunkItems) break;
+                const int Kc = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
+                if (need > avail || 2LL * (long long)r2 * dir_chunks(tn, d.W, Kc) > kMaxChunkItems) break;
                 DirDev& v = dirs[kk];
                 std::memset(&v, 0, sizeof(v));
                 v.t_fx = d.t_fx; v.slab = (long long)slab; v.frame = d.frame; v.H = d.H; v.W = d.W;
                 v.Wp = (int)wp; v.D = d.D; v.R = d.R;
                 v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
-                v.pov = pov_for(tn, d.W);
-                v.row_off = (int)nrows; v.chunks = sweep_chunks(d.W, v.pov); v.gidx = kk; v.job = 0;
+                v.pov = pov_mode(tn, d.W);
+                v.p4_pct = tn.p4_cost_pct;
+                v.row_off = (int)nrows; v.chunks = dir_chunks(tn, d.W, v.K); v.gidx = kk; v.job = 0;
                 v.g = (float)d.g; v.h0 = (float)obs_height_m;
                 slab = s2;
                 nrows = r2;
@@ -577,6 +580,7 @@ int tvs_get_tuning(tvs_handle h, tvs_tuning* t)
     t->small_pov_below_w = h->tuning.small_pov_below_w;
     t->sweep_max_warps = h->tuning.sweep_max_warps;
     t->unskew_ctas_per_sm = h->tuning.unskew_ctas_per_sm;
+    t->p4_cost_pct = h->tuning.p4_cost_pct;
     return TVS_OK;
 }
 
@@ -584,11 +588,12 @@ int tvs_set_tuning(tvs_handle h, const tvs_tuning* t)
 {
     if (!h || !t) return fail(TVS_ERR_ARG, "NULL argument");
     if (t->small_pov_below_w < 0 || t->sweep_max_warps < 0 || t->sweep_max_warps > SWEEP_MAX_WARPS ||
-        t->unskew_ctas_per_sm < 1 || t->unskew_ctas_per_sm > 4)
+        t->unskew_ctas_per_sm < 1 || t->unskew_ctas_per_sm > 4 || t->p4_cost_pct < 0 || t->p4_cost_pct > (1 << 20))
         return fail(TVS_ERR_ARG, "tuning out of range");
     h->tuning.small_pov_below_w = t->small_pov_below_w;
     h->tuning.sweep_max_warps = t->sweep_max_warps;
     h->tuning.unskew_ctas_per_sm = t->unskew_ctas_per_sm;
+    h->tuning.p4_cost_pct = t->p4_cost_pct ? t->p4_cost_pct : Tuning().p4_cost_pct;
     return TVS_OK;
 }
 
@@ -622,17 +627,19 @@ int tvs_autotune(tvs_handle h, const tvs_job* jobs, int njobs, tvs_tuning* best,
     Tuning cur = h->tuning;
     float cur_ms = 0.f;
     rc = time_of(cur, &cur_ms);
-    const int povs[] = {0, 384, 768, 1536, 1 << 30};
+    const int costs[] = {100, 107, 115, 130, 1 << 20};
+    const int povs[] = {0, 256, 512};
     const int warps[] = {0, 12, 8};
     const int unskews[] = {1, 2, 4};
-    for (int stage = 0; stage < 3 && !rc; ++stage) {
-        const int* opts = stage == 0 ? povs : stage == 1 ? warps : unskews;
+    for (int stage = 0; stage < 4 && !rc; ++stage) {
+        const int* opts = stage == 0 ? costs : stage == 1 ? povs : stage == 2 ? warps : unskews;
         const int nopt = stage == 0 ? 5 : 3;
         for (int o = 0; o < nopt && !rc; ++o) {
             Tuning tn = cur;
-            if (stage == 0) tn.small_pov_below_w = opts[o];
-            if (stage == 1) tn.sweep_max_warps = opts[o];
-            if (stage == 2) tn.unskew_ctas_per_sm = opts[o];
+            if (stage == 0) tn.p4_cost_pct = opts[o];
+            if (stage == 1) tn.small_pov_below_w = opts[o];
+            if (stage == 2) tn.sweep_max_warps = opts[o];
+            if (stage == 3) tn.unskew_ctas_per_sm = opts[o];
             float ms = 0.f;
             rc = time_of(tn, &ms);
             if (!rc && ms < cur_ms) { cur = tn; cur_ms = ms; }

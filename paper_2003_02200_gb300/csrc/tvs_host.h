@@ -71,12 +71,16 @@ enum KernelId { K_ROWMAP = 0, K_SKEW, K_SWEEP, K_UNSKEW, K_FINAL, K_COUNT };
 
 // Tunable launch choices (see tvs_tuning in tvs.h).
 struct Tuning {
-    int small_pov_below_w = 768;   // walk axes shorter than this use SMALL_POV groups
+    int small_pov_below_w = 0;     // directions whose walk axis is shorter than this use SMALL_POV groups
     int sweep_max_warps = 0;       // 0 = as many as shared memory allows (up to SWEEP_MAX_WARPS)
     int unskew_ctas_per_sm = 2;    // split a chunk's directions below this many unskew CTAs per SM
+    int p4_cost_pct = 107;         // per-row group choice: SMALL_POV step cost relative to LARGE_POV, percent
 };
 
-inline int pov_for(const Tuning& tn, int W) { return W < tn.small_pov_below_w ? SMALL_POV : LARGE_POV; }
+// Group-size mode of a direction (DirDev::pov): forced SMALL_POV below the
+// threshold, else chosen per row.
+inline int pov_mode(const Tuning& tn, int W) { return W < tn.small_pov_below_w ? SMALL_POV : 0; }
+inline int dir_chunks(const Tuning& tn, int W, int K) { return sweep_chunks(W, K, pov_mode(tn, W), tn.p4_cost_pct); }
 
 struct Pending {
     int kernel;

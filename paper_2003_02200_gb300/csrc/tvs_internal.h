@@ -7,9 +7,9 @@
 namespace tvs {
 
 // Sweep tiling.  Each lane walks two groups of consecutive samples (a group
-// and its mirror), 32 lanes per warp item.  A direction uses groups of
+// and its mirror), 32 lanes per warp item.  A row is swept with groups of
 // SMALL_POV samples (blocks of SMALL_UNROLL steps) or of LARGE_POV samples
-// (blocks of LARGE_UNROLL steps); the choice is per direction (DirDev::pov).
+// (blocks of LARGE_UNROLL steps), chosen per row by row_pov.
 constexpr int SMALL_POV = 4;
 constexpr int SMALL_UNROLL = 16;
 constexpr int LARGE_POV = 8;
@@ -44,13 +44,44 @@ struct DirDev {
     int R;                     // skewed rows, H + D; row p has base row p - D
     int K;                     // walk limit in steps, clipped to [0, W]
     int row_off;               // offset of this direction in the row tables
-    int chunks;                // warp items per skewed row and walk direction
+    int chunks;                // warp items per skewed row and walk direction (the most any row needs)
     int gidx;                  // direction index k within its job
     int job;                   // index of the job in the job table
     float g;                   // 1 + t^2
     float h0;                  // observer height of the job
-    int pov;                   // sweep group size, SMALL_POV or LARGE_POV
+    int pov;                   // group size of every row (SMALL_POV or LARGE_POV), 0 = chosen per row
+    int p4_pct;                // row_pov's relative cost of a SMALL_POV step, percent
 };
+
+// Lane slots of a row of L samples swept with groups of P POVs (two mirrored
+// groups per slot), and the warp items they take.
+__host__ __device__ inline int row_slots(int L, int P) { return ((L + P - 1) / P + 1) / 2; }
+__host__ __device__ inline int row_chunks(int L, int P) { return (row_slots(L, P) + 31) / 32; }
+
+// Steps lane 0 of a row walks (groups 0 and G-1, each rounded up to blocks of
+// U steps): about every lane's share, since mirrored groups balance.
+__host__ __device__ inline long long lane_steps(int L, int K, int P, int U)
+{
+    const int G = (L + P - 1) / P;
+    const int a = (K - 1 < L - 2) ? K - 1 : L - 2;
+    const int t = L - 2 - (G - 1) * P;
+    const int b = G > 1 ? ((K - 1 < t) ? K - 1 : t) : 0;
+    return (a > 0 ? (long long)((a + U - 1) / U) * U : 0) + (b > 0 ? (long long)((b + U - 1) / U) * U : 0);
+}
+
+// Group size of a row of L samples with walk limit K: `mode` forces one
+// (SMALL_POV or LARGE_POV); mode 0 takes the smaller of items x lane steps x
+// P x step cost, a SMALL_POV step costing p4_pct percent of a LARGE_POV step
+// per POV.  Only speed depends on it: the measures are exact integers.
+__host__ __device__ inline int row_pov(int L, int K, int mode, int p4_pct)
+{
+    if (mode) return mode;
+    const long long c8 = (long long)row_chunks(L, LARGE_POV) * lane_steps(L, K, LARGE_POV, LARGE_UNROLL) *
+                         LARGE_POV * 100;
+    const long long c4 = (long long)row_chunks(L, SMALL_POV) * lane_steps(L, K, SMALL_POV, SMALL_UNROLL) *
+                         SMALL_POV * p4_pct;
+    return c4 < c8 ? SMALL_POV : LARGE_POV;
+}
 
 // Per-cell totals are exact: each FP32 group sum (FP32_GROUP directions) is
 // converted to a signed fixed-point integer with ACC_FRAC_BITS fractional bits
@@ -87,8 +118,9 @@ cudaError_t launch_rowmap(const DirDev* d_dirs, int ndir, int max_R, int* rowlo,
 cudaError_t launch_colmap(const DirDev* d_dir, int* dest, unsigned* frac, cudaStream_t stream);
 cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, int max_tiles, float* sdem,
                         cudaStream_t stream);
-// Warp items of one skewed row and walk direction for a row of W samples.
-int sweep_chunks(int W, int pov);
+// Warp items per skewed row and walk direction of a direction whose rows
+// have at most W samples: the most any row length up to W needs.
+int sweep_chunks(int W, int K, int mode, int p4_pct);
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
                          int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin, int max_warps,

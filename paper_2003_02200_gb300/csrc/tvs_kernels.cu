@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <tuple>
 
 namespace tvs {
 
@@ -354,10 +356,9 @@ __device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* is
     it->L = jhi - jlo + 1;
     it->K = d.K;
     it->h0 = d.h0;
-    it->pov = d.pov;
+    it->pov = row_pov(it->L, d.K, d.pov, d.p4_pct);
     it->rowbase = d.slab + (long long)p * d.Wp + jlo;
-    const int G = (it->L + d.pov - 1) / d.pov;
-    return it->L > 0 && it->c * 32 < (G + 1) / 2;
+    return it->L > 0 && it->c * 32 < row_slots(it->L, it->pov);
 }
 
 // L2 prefetch of the n floats at p with one bulk request: start rounded down
@@ -697,10 +698,23 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
     return cudaGetLastError();
 }
 
-int sweep_chunks(int W, int pov)
+int sweep_chunks(int W, int K, int mode, int p4_pct)
 {
-    const int groups = (W + pov - 1) / pov;
-    return ((groups + 1) / 2 + 31) / 32;
+    if (mode) return row_chunks(W, mode);
+    // row_chunks grows with L for either group size, so the most is the
+    // count at W or at the longest row below W that takes SMALL_POV groups;
+    // scanning down stops once SMALL_POV rows can no longer need more.
+    // Memoised per thread: a plan asks for few distinct (W, K).
+    thread_local std::map<std::tuple<int, int, int>, int> memo;
+    const auto key = std::make_tuple(W, K, p4_pct);
+    const auto it = memo.find(key);
+    if (it != memo.end()) return it->second;
+    int most = row_chunks(W, row_pov(W, K, 0, p4_pct));
+    for (int L = W; L >= 2 && row_chunks(L, SMALL_POV) > most; --L)
+        if (row_pov(L, K, 0, p4_pct) == SMALL_POV) { most = row_chunks(L, SMALL_POV); break; }
+    if (memo.size() > 4096) memo.clear();
+    memo.emplace(key, most);
+    return most;
 }
 
 int unskew_per_split(int ndir, int nsplit)

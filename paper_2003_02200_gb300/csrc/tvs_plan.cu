@@ -309,7 +309,8 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
             const size_t wp = (size_t)((d.W + 3) & ~3);
             const size_t s2 = slab + (size_t)d.R * wp;
             const long long r2 = nrows + d.R;
-            const long long it2 = items + 2LL * d.R * sweep_chunks(d.W, pov_for(tn, d.W));
+            const int Kc = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
+            const long long it2 = items + 2LL * d.R * dir_chunks(tn, d.W, Kc);
             if (ii > i && (chunk_bytes(s2, r2, ii - i + 1) > avail || ii - i >= kMaxChunkDirs ||
                            it2 > kMaxChunkItems))
                 break;
@@ -365,8 +366,9 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
             v.D = d.D; v.R = d.R;
             v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
             v.row_off = (int)roff;
-            v.pov = pov_for(tn, d.W);
-            v.chunks = sweep_chunks(d.W, v.pov);
+            v.pov = pov_mode(tn, d.W);
+            v.p4_pct = tn.p4_cost_pct;
+            v.chunks = dir_chunks(tn, d.W, v.K);
             v.gidx = plan->inst_k[t];
             v.job = plan->inst_job[t];
             v.g = (float)d.g;

@@ -588,7 +588,8 @@ int tvs_server_submit(tvs_server_handle S, const float* dem, int rows, int cols,
         r->cum_evals[k + 1] = r->cum_evals[k] + (double)r->work[k].evals;
         r->cum_slab[k + 1] = r->cum_slab[k] + (long long)d.R * wp;
         r->cum_rows[k + 1] = r->cum_rows[k] + d.R;
-        r->cum_items[k + 1] = r->cum_items[k] + 2LL * d.R * sweep_chunks(d.W, pov_for(S->tuning, d.W));
+        const int Kc = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
+        r->cum_items[k + 1] = r->cum_items[k] + 2LL * d.R * dir_chunks(S->tuning, d.W, Kc);
         if ((k + 1) % FP32_GROUP == 0 || k + 1 == n_sectors) {
             const int g0 = (k / FP32_GROUP) * FP32_GROUP;
             worst_group = std::max(worst_group,

@@ -125,15 +125,17 @@ def test_autotune_keeps_results_and_sets_the_handle(ctx):
         np.testing.assert_array_equal(j["out"].cpu().numpy(), w)
 
 
-@pytest.mark.parametrize("pov_below", [0, 1 << 30])
-def test_group_size_choice_does_not_change_results(ctx, pov_below):
-    """Every direction swept with 8-POV groups (threshold 0) or 4-POV groups
-    (threshold huge): the per-sample measures are exact integers either way."""
+@pytest.mark.parametrize("pov_below,p4_cost", [(0, 1 << 20), (1 << 30, 107), (0, 100), (0, 130)])
+def test_group_size_choice_does_not_change_results(ctx, pov_below, p4_cost):
+    """Every row on 8-POV groups (4-POV cost prohibitive), every row on 4-POV
+    groups (threshold huge), or a per-row mix: the per-sample measures are
+    exact integers either way."""
     import torch
     jobs = _jobs(SPECS[:3], seed=40)
     want = _singles(ctx, jobs)
     with tvs.Context(0) as c:
-        c.set_tuning(small_pov_below_w=pov_below)
+        c.set_tuning(small_pov_below_w=pov_below, p4_cost_pct=p4_cost)
+        assert c.get_tuning()["p4_cost_pct"] == p4_cost
         for j in jobs:
             c.total_viewshed_device(j["dem"], j["step_m"], j["obs_height_m"], j["n_sectors"], j["max_range_m"],
                                     out=j["out"])
