@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define TVS_ABI_VERSION 1
+#define TVS_ABI_VERSION 2
 
 #define TVS_OK            0
 #define TVS_ERR_ARG     (-1)  /* bad pointer, size, step, height, count or non-finite value */
@@ -195,12 +195,19 @@ void tvs_batch_destroy(tvs_batch_handle b);
  * sweep_max_warps: warps per sweep CTA, 0 = as many as shared memory allows,
  *   at most 16 (default 0);
  * unskew_ctas_per_sm: a chunk whose DEMs have fewer cell tiles than this many
- *   per SM splits its directions into ranges across CTAs (1 to 4, default 2). */
+ *   per SM splits its directions into ranges across CTAs (1 to 4, default 2);
+ * prune: exact horizon pruning in the sweep (1, default) or none (0): a group
+ *   of POVs stops walking once no remaining target can rise above its running
+ *   maximum elevation angle (bounded through the row's suffix maximum with
+ *   monotone FP32 rounding), which leaves every result bit for bit the same;
+ *   the work count (evaluations) stays the unpruned one. */
 typedef struct {
     int32_t small_pov_below_w;
     int32_t sweep_max_warps;
     int32_t unskew_ctas_per_sm;
     int32_t p4_cost_pct;
+    int32_t prune;
+    int32_t pad_;
 } tvs_tuning;
 
 int tvs_get_tuning(tvs_handle h, tvs_tuning* t);

@@ -49,7 +49,8 @@ class BatchInfo(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("small_pov_below_w", C.c_int32), ("sweep_max_warps", C.c_int32),
-                ("unskew_ctas_per_sm", C.c_int32), ("p4_cost_pct", C.c_int32)]
+                ("unskew_ctas_per_sm", C.c_int32), ("p4_cost_pct", C.c_int32), ("prune", C.c_int32),
+                ("pad_", C.c_int32)]
 
 
 class ServerConfig(C.Structure):
@@ -330,7 +331,8 @@ class Context:
     def set_tuning(self, **kw) -> None:
         cur = self.get_tuning()
         cur.update(kw)
-        t = Tuning(cur["small_pov_below_w"], cur["sweep_max_warps"], cur["unskew_ctas_per_sm"], cur["p4_cost_pct"])
+        t = Tuning(cur["small_pov_below_w"], cur["sweep_max_warps"], cur["unskew_ctas_per_sm"], cur["p4_cost_pct"],
+                   int(cur["prune"]), 0)
         _check(self._lib.tvs_set_tuning(self.handle, C.byref(t)))
 
     def autotune(self, jobs) -> tuple[dict, float]:

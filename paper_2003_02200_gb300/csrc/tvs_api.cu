@@ -139,7 +139,7 @@ int tvs_debug_rowmap(tvs_handle h, int rows, int cols, int n_sectors, int k, int
     make_direction(n_sectors, k, rows, cols, 1.0, 0.0, &d);
     DirDev v{};
     v.t_fx = d.t_fx; v.frame = d.frame; v.H = d.H; v.W = d.W; v.Wp = (d.W + 3) & ~3;
-    v.D = d.D; v.R = d.R; v.K = d.W; v.row_off = 0; v.chunks = 1; v.gidx = k; v.g = (float)d.g;
+    v.D = d.D; v.R = d.R; v.K = d.W; v.row_off = 0; v.gidx = k; v.g = (float)d.g;
     v.pov = LARGE_POV; v.p4_pct = 100;
     const size_t need = align256(sizeof(DirDev)) + 4 * align256((size_t)std::max(d.R, d.W) * 4);
     rc = ensure_scratch(h, need);
@@ -203,7 +203,8 @@ int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, d
     TVS_CUDA(launch_skew(d_jobs, d_dir, 1, c.max_tiles, d_s, s), "skew launch");
     TVS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), s), "reset work counter");
     TVS_CUDA(launch_sweep(d_dir, reinterpret_cast<const int*>(ws + L.istart), 1, c.items, d_s, d_lo, d_hi, d_cv,
-                          d_cb, v.W, v.K, d_cnt, h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, s),
+                          d_cb, v.W, v.K, h->tuning.prune, d_cnt, h->num_sms, h->smem_optin,
+                          h->tuning.sweep_max_warps, s),
              "sweep launch");
     std::vector<int> slab(c.slab_elems), slabb(c.slab_elems), lo(v.R), hi(v.R);
     TVS_CUDA(cudaMemcpyAsync(slab.data(), d_cv, c.slab_elems * 4, cudaMemcpyDeviceToHost, s), "copy cv");
@@ -342,8 +343,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 const size_t wp = (size_t)((d.W + 3) & ~3);
                 const size_t s2 = slab + (size_t)d.R * wp, r2 = nrows + d.R;
                 const size_t need = 2 * align256(r2 * 4) + 3 * align256(s2 * 4);
-                const int Kc = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
-                if (need > avail || 2LL * (long long)r2 * dir_chunks(tn, d.W, Kc) > kMaxChunkItems) break;
+                if (need > avail || 2LL * (long long)r2 > kMaxChunkItems) break;
                 DirDev& v = dirs[kk];
                 std::memset(&v, 0, sizeof(v));
                 v.t_fx = d.t_fx; v.slab = (long long)slab; v.frame = d.frame; v.H = d.H; v.W = d.W;
@@ -351,7 +351,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
                 v.pov = pov_mode(tn, d.W);
                 v.p4_pct = tn.p4_cost_pct;
-                v.row_off = (int)nrows; v.chunks = dir_chunks(tn, d.W, v.K); v.gidx = kk; v.job = 0;
+                v.row_off = (int)nrows; v.gidx = kk; v.job = 0;
                 v.g = (float)d.g; v.h0 = (float)obs_height_m;
                 slab = s2;
                 nrows = r2;
@@ -372,7 +372,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
         for (int c = 0; c < nchunks; ++c) {
             istart[at] = 0;
             for (int q = chunk_k0[c]; q < chunk_k0[c + 1]; ++q) {
-                istart[at + 1] = istart[at] + 2 * dirs[q].R * dirs[q].chunks;
+                istart[at + 1] = istart[at] + 2 * dirs[q].R;
                 ++at;
             }
             ++at;
@@ -432,7 +432,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
         // the shared array keeps the previous call's contents: the work counter must start at zero
         TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
         TVS_CUDA(launch_sweep(cd, d_istart + at, nd, istart[at + nd], d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                              wmax, dmax, d_counter, num_sms, smem_optin, tn.sweep_max_warps, s),
+                              wmax, dmax, tn.prune, d_counter, num_sms, smem_optin, tn.sweep_max_warps, s),
                  "sweep launch");
         TVS_CUDA(launch_unskew(d_cvf, d_cvb, d_job, cd, d_cj + c, 1, tiles, cjs[c].nsplit, d_part, s),
                  "unskew launch");
@@ -534,7 +534,7 @@ int tvs_batch_create(tvs_handle h, const tvs_job* jobs, int njobs, size_t hbm_bu
     if (e != cudaSuccess) { tvs_batch_destroy(b); return cuda_fail(e, "cudaStreamCreate"); }
     e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) { cudaStreamDestroy(cap); tvs_batch_destroy(b); return cuda_fail(e, "begin capture"); }
-    rc = enqueue_chunks(nullptr, b->plan, b->L, b->ws, h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, cap);
+    rc = enqueue_chunks(nullptr, b->plan, b->L, b->ws, h->num_sms, h->smem_optin, h->tuning, cap);
     cudaGraph_t graph = nullptr;
     e = cudaStreamEndCapture(cap, &graph);
     cudaStreamDestroy(cap);
@@ -581,6 +581,7 @@ int tvs_get_tuning(tvs_handle h, tvs_tuning* t)
     t->sweep_max_warps = h->tuning.sweep_max_warps;
     t->unskew_ctas_per_sm = h->tuning.unskew_ctas_per_sm;
     t->p4_cost_pct = h->tuning.p4_cost_pct;
+    t->prune = h->tuning.prune;
     return TVS_OK;
 }
 
@@ -588,12 +589,14 @@ int tvs_set_tuning(tvs_handle h, const tvs_tuning* t)
 {
     if (!h || !t) return fail(TVS_ERR_ARG, "NULL argument");
     if (t->small_pov_below_w < 0 || t->sweep_max_warps < 0 || t->sweep_max_warps > SWEEP_MAX_WARPS ||
-        t->unskew_ctas_per_sm < 1 || t->unskew_ctas_per_sm > 4 || t->p4_cost_pct < 0 || t->p4_cost_pct > (1 << 20))
+        t->unskew_ctas_per_sm < 1 || t->unskew_ctas_per_sm > 4 || t->p4_cost_pct < 0 || t->p4_cost_pct > (1 << 20) ||
+        t->prune < 0 || t->prune > 1)
         return fail(TVS_ERR_ARG, "tuning out of range");
     h->tuning.small_pov_below_w = t->small_pov_below_w;
     h->tuning.sweep_max_warps = t->sweep_max_warps;
     h->tuning.unskew_ctas_per_sm = t->unskew_ctas_per_sm;
     h->tuning.p4_cost_pct = t->p4_cost_pct ? t->p4_cost_pct : Tuning().p4_cost_pct;
+    h->tuning.prune = t->prune;
     return TVS_OK;
 }
 
@@ -627,19 +630,21 @@ int tvs_autotune(tvs_handle h, const tvs_job* jobs, int njobs, tvs_tuning* best,
     Tuning cur = h->tuning;
     float cur_ms = 0.f;
     rc = time_of(cur, &cur_ms);
+    const int prunes[] = {1, 0};
     const int costs[] = {100, 107, 115, 130, 1 << 20};
     const int povs[] = {0, 256, 512};
     const int warps[] = {0, 12, 8};
     const int unskews[] = {1, 2, 4};
-    for (int stage = 0; stage < 4 && !rc; ++stage) {
-        const int* opts = stage == 0 ? costs : stage == 1 ? povs : stage == 2 ? warps : unskews;
-        const int nopt = stage == 0 ? 5 : 3;
+    for (int stage = 0; stage < 5 && !rc; ++stage) {
+        const int* opts = stage == 0 ? prunes : stage == 1 ? costs : stage == 2 ? povs : stage == 3 ? warps : unskews;
+        const int nopt = stage == 0 ? 2 : stage == 1 ? 5 : 3;
         for (int o = 0; o < nopt && !rc; ++o) {
             Tuning tn = cur;
-            if (stage == 0) tn.p4_cost_pct = opts[o];
-            if (stage == 1) tn.small_pov_below_w = opts[o];
-            if (stage == 2) tn.sweep_max_warps = opts[o];
-            if (stage == 3) tn.unskew_ctas_per_sm = opts[o];
+            if (stage == 0) tn.prune = opts[o];
+            if (stage == 1) tn.p4_cost_pct = opts[o];
+            if (stage == 2) tn.small_pov_below_w = opts[o];
+            if (stage == 3) tn.sweep_max_warps = opts[o];
+            if (stage == 4) tn.unskew_ctas_per_sm = opts[o];
             float ms = 0.f;
             rc = time_of(tn, &ms);
             if (!rc && ms < cur_ms) { cur = tn; cur_ms = ms; }

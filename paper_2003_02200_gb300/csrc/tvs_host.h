@@ -75,12 +75,12 @@ struct Tuning {
     int sweep_max_warps = 0;       // 0 = as many as shared memory allows (up to SWEEP_MAX_WARPS)
     int unskew_ctas_per_sm = 2;    // split a chunk's directions below this many unskew CTAs per SM
     int p4_cost_pct = 107;         // per-row group choice: SMALL_POV step cost relative to LARGE_POV, percent
+    int prune = 1;                 // exact horizon pruning in the sweep
 };
 
 // Group-size mode of a direction (DirDev::pov): forced SMALL_POV below the
 // threshold, else chosen per row.
 inline int pov_mode(const Tuning& tn, int W) { return W < tn.small_pov_below_w ? SMALL_POV : 0; }
-inline int dir_chunks(const Tuning& tn, int W, int K) { return sweep_chunks(W, K, pov_mode(tn, W), tn.p4_cost_pct); }
 
 struct Pending {
     int kernel;
@@ -206,7 +206,7 @@ int ensure_scratch(tvs_ctx* h, size_t bytes);
 // before the first unskew (the request server orders the unskews of steps on
 // different streams that add to the same totals).
 int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* base, int num_sms, int smem_optin,
-                   int max_warps, cudaStream_t s, int* kernels = nullptr, cudaEvent_t before_unskew = nullptr);
+                   const Tuning& tn, cudaStream_t s, int* kernels = nullptr, cudaEvent_t before_unskew = nullptr);
 
 // Copy a header image to the device through the handle's pinned staging buffer.
 int upload_header(tvs_ctx* h, const std::vector<char>& img, void* dst, cudaStream_t s);

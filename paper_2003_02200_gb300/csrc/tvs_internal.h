@@ -44,7 +44,6 @@ struct DirDev {
     int R;                     // skewed rows, H + D; row p has base row p - D
     int K;                     // walk limit in steps, clipped to [0, W]
     int row_off;               // offset of this direction in the row tables
-    int chunks;                // warp items per skewed row and walk direction (the most any row needs)
     int gidx;                  // direction index k within its job
     int job;                   // index of the job in the job table
     float g;                   // 1 + t^2
@@ -53,34 +52,42 @@ struct DirDev {
     int p4_pct;                // row_pov's relative cost of a SMALL_POV step, percent
 };
 
-// Lane slots of a row of L samples swept with groups of P POVs (two mirrored
-// groups per slot), and the warp items they take.
-__host__ __device__ inline int row_slots(int L, int P) { return ((L + P - 1) / P + 1) / 2; }
-__host__ __device__ inline int row_chunks(int L, int P) { return (row_slots(L, P) + 31) / 32; }
-
-// Steps lane 0 of a row walks (groups 0 and G-1, each rounded up to blocks of
-// U steps): about every lane's share, since mirrored groups balance.
-__host__ __device__ inline long long lane_steps(int L, int K, int P, int U)
+// Lane steps of the sweep of one row of L samples (walk limit K) with groups
+// of P POVs: `total` over all groups (unrounded walk lengths) and `longest`
+// (group 0).  A row's 32 lanes share its groups, so it takes about
+// max(total / 32, longest) steps of P POVs.
+__host__ __device__ inline void row_steps(int L, int K, int P, long long* total, long long* longest)
 {
-    const int G = (L + P - 1) / P;
-    const int a = (K - 1 < L - 2) ? K - 1 : L - 2;
-    const int t = L - 2 - (G - 1) * P;
-    const int b = G > 1 ? ((K - 1 < t) ? K - 1 : t) : 0;
-    return (a > 0 ? (long long)((a + U - 1) / U) * U : 0) + (b > 0 ? (long long)((b + U - 1) / U) * U : 0);
+    const long long c = K - 1, G = (L + P - 1) / P;
+    *longest = c < L - 2 ? (c > 0 ? c : 0) : (L - 2 > 0 ? L - 2 : 0);
+    if (c <= 0 || L < 3) { *total = 0; return; }
+    // groups with L - 2 - gP >= c walk c steps, the rest L - 2 - gP while positive
+    long long n1 = L - 2 - c >= 0 ? (L - 2 - c) / P + 1 : 0;
+    if (n1 > G) n1 = G;
+    long long glast = (L - 3) / P;
+    if (glast > G - 1) glast = G - 1;
+    long long t = n1 * c;
+    if (glast >= n1) {
+        const long long cnt = glast - n1 + 1;
+        t += cnt * (L - 2) - (long long)P * (n1 + glast) * cnt / 2;
+    }
+    *total = t;
 }
 
 // Group size of a row of L samples with walk limit K: `mode` forces one
-// (SMALL_POV or LARGE_POV); mode 0 takes the smaller of items x lane steps x
-// P x step cost, a SMALL_POV step costing p4_pct percent of a LARGE_POV step
-// per POV.  Only speed depends on it: the measures are exact integers.
+// (SMALL_POV or LARGE_POV); mode 0 takes the smaller of
+// max(total / 32, longest) x P x step cost, a SMALL_POV step costing p4_pct
+// percent of a LARGE_POV step per POV.  Only speed depends on it: the
+// measures are exact integers.
 __host__ __device__ inline int row_pov(int L, int K, int mode, int p4_pct)
 {
     if (mode) return mode;
-    const long long c8 = (long long)row_chunks(L, LARGE_POV) * lane_steps(L, K, LARGE_POV, LARGE_UNROLL) *
-                         LARGE_POV * 100;
-    const long long c4 = (long long)row_chunks(L, SMALL_POV) * lane_steps(L, K, SMALL_POV, SMALL_UNROLL) *
-                         SMALL_POV * p4_pct;
-    return c4 < c8 ? SMALL_POV : LARGE_POV;
+    long long t8, l8, t4, l4;
+    row_steps(L, K, LARGE_POV, &t8, &l8);
+    row_steps(L, K, SMALL_POV, &t4, &l4);
+    const long long s8 = (t8 + 31) / 32 > l8 ? (t8 + 31) / 32 : l8;
+    const long long s4 = (t4 + 31) / 32 > l4 ? (t4 + 31) / 32 : l4;
+    return s4 * SMALL_POV * p4_pct < s8 * LARGE_POV * 100 ? SMALL_POV : LARGE_POV;
 }
 
 // Per-cell totals are exact: each FP32 group sum (FP32_GROUP directions) is
@@ -118,13 +125,13 @@ cudaError_t launch_rowmap(const DirDev* d_dirs, int ndir, int max_R, int* rowlo,
 cudaError_t launch_colmap(const DirDev* d_dir, int* dest, unsigned* frac, cudaStream_t stream);
 cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, int max_tiles, float* sdem,
                         cudaStream_t stream);
-// Warp items per skewed row and walk direction of a direction whose rows
-// have at most W samples: the most any row length up to W needs.
-int sweep_chunks(int W, int K, int mode, int p4_pct);
+// Sweep of a chunk: one warp item per skewed row and walk direction (items
+// 2p and 2p + 1 of a direction are row p forward and backward); `prune` turns
+// exact horizon pruning on.
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
-                         int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin, int max_warps,
-                         cudaStream_t stream);
+                         int wmax, int dmax, int prune, unsigned* counter, int num_sms, int smem_optin,
+                         int max_warps, cudaStream_t stream);
 // Unskew of a chunk: `total_tiles` flattened cell tiles over the chunk's jobs
 // (ncj entries of d_cj, sorted by tile_beg), `max_split` the largest nsplit.
 cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, const JobDev* d_jobs, const DirDev* d_dirs,

@@ -14,8 +14,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <map>
-#include <tuple>
 
 namespace tvs {
 
@@ -173,7 +171,8 @@ struct SweepParams {
     int inv_len;     // entries of the per-distance table (float4 each)
     int istart_len;  // ints of the item-start table (multiple of 4)
     int half;        // floats of one staged row (multiple of 4)
-    int per_warp;    // floats of a warp's shared area: the staged row, then (long rows) 64 x LARGE_POV spill ints
+    int zs_len;      // floats of the row's suffix maxima (0 without pruning)
+    int per_warp;    // floats of a warp's shared area: staged row, suffix maxima, (long rows) 32 x LARGE_POV ints
 };
 
 __device__ __forceinline__ float fset_gt(float a, float b)
@@ -221,123 +220,167 @@ __device__ __forceinline__ void sweep_block(const float* w, const float4* __rest
 // flush (the LONG = false instantiation).
 constexpr int LONG_WALK = 4000;
 constexpr int FLUSH_STEPS = 384;   // a multiple of SMALL_UNROLL and LARGE_UNROLL
+// Suffix maxima of a staged row are kept at every ZS_STRIDE-th sample; pruning
+// checks every PRUNE_EVERY blocks.
+constexpr int ZS_STRIDE = 4;
+constexpr int PRUNE_EVERY = 2;
 
-// One lane of a warp item: forward walks of two groups of P consecutive POVs
-// of the staged row F (group s and its mirror G-1-s, so that every lane walks
-// about one row length in total).  F holds the row (or the reversed row for
-// backward walks) with -inf at its last sample and after it: the last target
-// of a walk never adds area (its segment closes there), so it may be a
-// sentinel that is never visible.  A walk's measure is
+// A warp item is one skewed row and one walk direction.  Its G groups of P
+// consecutive POVs are taken in order (longest walks first) from a warp-local
+// queue by whichever lane is free, so lanes stay busy whatever the walk
+// lengths (and wherever pruning ends a walk early).  F holds the row (or the
+// reversed row for backward walks) with -inf at its last sample and after it:
+// the last target of a walk never adds area (its segment closes there), so it
+// may be a sentinel that is never visible.  A walk's measure is
 // cv = 1 + sum_{d=1}^{n-1} v_d (2d + 1) for n >= 1 targets, which is Alg. 8's
 // sum of d^2 - open^2 over its closed segments plus the segment still open at
-// the end (closed at the last target).  With LONG, `spill` is the lane's
-// column (stride 32) of 2P integers: the flushed parts of group 0, then of
-// group 1.
-template <int P, int U, bool LONG>
-__device__ __forceinline__ void sweep_lane(const float* __restrict__ F, const float4* __restrict__ tab,
-                                           int* __restrict__ cvrow, int* __restrict__ spill, int L, int slot, int K,
-                                           float h0, bool rev)
+// the end (closed at the last target).
+//
+// PRUNE (exact horizon pruning): every PRUNE_EVERY blocks a lane stops its
+// group's walks once min_q M_q >= B, B = fl(A * (1/d)) if A >= 0 else 0, where
+// d is the next target distance and A = fl(Zmax - min_q h_q) with Zmax an upper
+// bound of every remaining target (the suffix maximum ZS).  Rounding to nearest
+// is monotone, so every remaining slope fl(fl(z - h_q) * fl(1/d')) is at most
+// fl(A * fl(1/d)) when A >= 0 (d' >= d) and at most 0 when A < 0: no remaining
+// target can be strictly above its POV's running maximum, and the walk's
+// measure is already complete.  The result is bit for bit the same.
+//
+// With LONG, `spill` is the lane's column (stride 32) of P integers.
+template <int P, int U, bool LONG, bool PRUNE>
+__device__ __forceinline__ void sweep_row(const float* __restrict__ F, const float* __restrict__ ZS,
+                                          const float4* __restrict__ tab, int* __restrict__ cvrow,
+                                          int* __restrict__ spill, int L, int K, float h0, bool rev, int lane)
 {
+    const unsigned FULL = 0xffffffffu;
+    const unsigned below = (1u << lane) - 1u;
     const float NEG = neg_inf();
     const int G = (L + P - 1) / P;
-    const int nslots = (G + 1) / 2;
-    if (slot >= nslots) return;
-    const int gsel[2] = {slot, G - 1 - slot};
-    const int ng = gsel[0] == gsel[1] ? 1 : 2;
     const int klim = K - 1;          // last target distance that still adds area
-
     float h[P], M[P];
     float2 acc2[P / 2];
-    float first[P];                  // measure sums of group 0 once group 1 starts
-    int* sg = spill;                 // flushed parts of the current group (LONG)
-    int seg = FLUSH_STEPS;           // next flush (LONG)
-    int x0 = gsel[0] * P;
-    int rowlim = L - 2 - x0;         // last target adding area, POV q = 0
-    int dlim = min(klim, rowlim);
-    bool klimited = klim < rowlim;
-    bool second = false;
+    float hmin = 0.f;
+    int g = lane, next = 32;         // the lane's group; the first group nobody has taken
+    int x0 = 0, e = 0, dlim = -1, seg = FLUSH_STEPS;
+    int pc = 1;                      // blocks until the next pruning check
+    bool klimited = false;
+
+    auto start = [&]() {
+        x0 = g * P;
+        const int rowlim = L - 2 - x0;   // last target adding area, POV q = 0
+        dlim = min(klim, rowlim);
+        klimited = klim < rowlim;
+        e = 0;
+        seg = FLUSH_STEPS;
+        pc = 1;
 #pragma unroll
-    for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; first[q] = 0.f; }
+        for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; }
 #pragma unroll
-    for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
-    if (LONG) {
+        for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+        if (PRUNE) {
+            hmin = h[0];
 #pragma unroll
-        for (int q = 0; q < 2 * P; ++q) spill[32 * q] = 0;
-    }
-    int e = 0;
-    for (;;) {
-        if (LONG && e >= seg) {
-            seg += FLUSH_STEPS;
-#pragma unroll
-            for (int q = 0; q < P; q += 2) {
-                sg[32 * q] += __float2int_rz(acc2[q / 2].x);
-                sg[32 * (q + 1)] += __float2int_rz(acc2[q / 2].y);
-                acc2[q / 2] = make_float2(0.f, 0.f);
-            }
+            for (int q = 1; q < P; ++q) hmin = fminf(hmin, h[q]);
         }
-        if (e >= dlim) {
-            if (second || ng == 1) break;
+        if (LONG) {
 #pragma unroll
-            for (int q = 0; q < P; q += 2) { first[q] = acc2[q / 2].x; first[q + 1] = acc2[q / 2].y; }
-            second = true;
-            x0 = gsel[1] * P;
-            rowlim = L - 2 - x0;
-            dlim = min(klim, rowlim);
-            klimited = klim < rowlim;
+            for (int q = 0; q < P; ++q) spill[32 * q] = 0;
+        }
+    };
+    if (g < G) start();
+    for (;;) {
+        const bool fin = g < G && e >= dlim;
+        const unsigned need = __ballot_sync(FULL, fin);
+        if (need) {
+            if (fin) {
 #pragma unroll
-            for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; }
-#pragma unroll
-            for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
-            if (LONG) { sg = spill + 32 * P; seg = FLUSH_STEPS; }
-            e = 0;
+                for (int q = 0; q < P; ++q) {
+                    const int x = x0 + q;
+                    if (x < L) {
+                        const int n = min(L - 1 - x, K);
+                        const float s = q % 2 ? acc2[q / 2].y : acc2[q / 2].x;
+                        cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)s + (LONG ? spill[32 * q] : 0) : 0;
+                    }
+                }
+            }
+            if (fin) {
+                g = next + __popc(need & below);
+                if (g < G) start(); else g = G;
+            }
+            next += __popc(need);
+            if (!__any_sync(FULL, g < G)) break;
             continue;
         }
-        const float* base = F + ROW_PADL + x0 + e;
-        float w[P + U];
+        if (g < G) {
+            if (LONG && e >= seg) {
+                seg += FLUSH_STEPS;
 #pragma unroll
-        for (int m = 0; m < P + U; m += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(base + m);
-            w[m] = v.x; w[m + 1] = v.y; w[m + 2] = v.z; w[m + 3] = v.w;
-        }
-        if (klimited && e + U > dlim)
-            sweep_block<P, U, true>(w, tab + e, h, M, acc2, dlim - e);
-        else
-            sweep_block<P, U, false>(w, tab + e, h, M, acc2, U);
-        e += U;
-    }
-    // group 0 ends in `first` when a second group ran, else in acc2
-    const int xa = gsel[0] * P, xb = gsel[1] * P;
-#pragma unroll
-    for (int q = 0; q < P; ++q) {
-        const float sa = second ? first[q] : (q % 2 ? acc2[q / 2].y : acc2[q / 2].x);
-        const int x = xa + q;
-        if (x < L) {
-            const int n = min(L - 1 - x, K);
-            cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sa + (LONG ? spill[32 * q] : 0) : 0;
-        }
-    }
-    if (second) {
-#pragma unroll
-        for (int q = 0; q < P; ++q) {
-            const float sb = q % 2 ? acc2[q / 2].y : acc2[q / 2].x;
-            const int x = xb + q;
-            if (x < L) {
-                const int n = min(L - 1 - x, K);
-                cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)sb + (LONG ? spill[32 * (P + q)] : 0) : 0;
+                for (int q = 0; q < P; q += 2) {
+                    spill[32 * q] += __float2int_rz(acc2[q / 2].x);
+                    spill[32 * (q + 1)] += __float2int_rz(acc2[q / 2].y);
+                    acc2[q / 2] = make_float2(0.f, 0.f);
+                }
             }
+            if (PRUNE && --pc < 0) {
+                pc = PRUNE_EVERY - 1;
+                const float A = __fsub_rn(ZS[(x0 + e + 1) / ZS_STRIDE], hmin);
+                const float B = A >= 0.f ? __fmul_rn(A, tab[e].x) : 0.f;
+                float m = M[0];
+#pragma unroll
+                for (int q = 1; q < P; ++q) m = fminf(m, M[q]);
+                if (m >= B) { e = dlim; continue; }
+            }
+            const float* base = F + ROW_PADL + x0 + e;
+            float w[P + U];
+#pragma unroll
+            for (int m = 0; m < P + U; m += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(base + m);
+                w[m] = v.x; w[m + 1] = v.y; w[m + 2] = v.z; w[m + 3] = v.w;
+            }
+            if (klimited && e + U > dlim)
+                sweep_block<P, U, true>(w, tab + e, h, M, acc2, dlim - e);
+            else
+                sweep_block<P, U, false>(w, tab + e, h, M, acc2, U);
+            e += U;
         }
     }
 }
 
-// A sweep work item: (direction, skewed row, chunk of lane slots, walk direction).
+// Suffix maxima of the staged row F (L samples, -inf from L - 1 on) at every
+// ZS_STRIDE-th sample: ZS[j] = max F[x] over x >= ZS_STRIDE * j, for
+// j <= (L - 1) / ZS_STRIDE.  Lane l scans its own segment, a warp scan joins
+// the segments.
+__device__ __forceinline__ void suffix_max(const float* __restrict__ F, float* __restrict__ ZS, int L, int lane)
+{
+    const float NEG = neg_inf();
+    const int seglen = ((L + 31) / 32 + ZS_STRIDE - 1) / ZS_STRIDE * ZS_STRIDE;
+    const int a = lane * seglen, b = min(a + seglen, L);
+    float m = NEG;
+    for (int x = b - 1; x >= a; --x) m = fmaxf(m, F[ROW_PADL + x]);
+    // inclusive suffix scan of the segment maxima over the lanes
+    float s = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_down_sync(0xffffffffu, s, o);
+        if (lane + o < 32) s = fmaxf(s, t);
+    }
+    float after = __shfl_down_sync(0xffffffffu, s, 1);   // maximum of the following segments
+    if (lane == 31) after = NEG;
+    float run = after;
+    for (int x = b - 1; x >= a; --x) {
+        run = fmaxf(run, F[ROW_PADL + x]);
+        if (x % ZS_STRIDE == 0) ZS[x / ZS_STRIDE] = run;
+    }
+}
+
+// A sweep work item: (direction, skewed row, walk direction).
 struct ItemRow {
     long long rowbase;   // slab offset of the row's first usable sample
-    int L, c, K, pov;
+    int L, K, pov;
     float h0;
     bool rev;
 };
 
-// Decodes item into its row; false when the chunk has no used lane slot.
+// Decodes item into its row; false when the row is empty.
 __device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* istart, int item, ItemRow* it)
 {
     int lo = 0, hi = sp.ndir - 1;
@@ -347,18 +390,15 @@ __device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* is
     }
     const DirDev& d = sp.dirs[lo];
     const int rem = item - istart[lo];
-    const int per_row = 2 * d.chunks;
-    const int p = rem / per_row;
-    const int r2 = rem - p * per_row;
-    it->rev = (r2 & 1) != 0;
-    it->c = r2 >> 1;
+    const int p = rem >> 1;
+    it->rev = (rem & 1) != 0;
     const int jlo = sp.rowlo[d.row_off + p], jhi = sp.rowhi[d.row_off + p];
     it->L = jhi - jlo + 1;
     it->K = d.K;
     it->h0 = d.h0;
     it->pov = row_pov(it->L, d.K, d.pov, d.p4_pct);
     it->rowbase = d.slab + (long long)p * d.Wp + jlo;
-    return it->L > 0 && it->c * 32 < row_slots(it->L, it->pov);
+    return it->L > 0;
 }
 
 // L2 prefetch of the n floats at p with one bulk request: start rounded down
@@ -373,6 +413,19 @@ __device__ __forceinline__ void prefetch_row_l2(const float* p, int n)
     asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" :: "l"(a), "r"(size) : "memory");
 }
 
+template <bool LONG, bool PRUNE>
+__device__ __forceinline__ void sweep_item(const ItemRow& it, const float* F, const float* ZS, const float4* tab,
+                                           int* cvrow, int* spill, int lane)
+{
+    if (it.pov == SMALL_POV)
+        sweep_row<SMALL_POV, SMALL_UNROLL, LONG, PRUNE>(F, ZS, tab, cvrow, spill, it.L, it.K, it.h0, it.rev, lane);
+    else
+        sweep_row<LARGE_POV, LARGE_UNROLL, LONG, PRUNE>(F, ZS, tab, cvrow, spill, it.L, it.K, it.h0, it.rev, lane);
+}
+
+// PRUNE: exact horizon pruning; LONG: the launch holds rows with walks of
+// more than LONG_WALK steps (every row then takes the flushing walk).
+template <bool PRUNE, bool LONG>
 __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepParams sp)
 {
     extern __shared__ __align__(16) float smem[];
@@ -380,7 +433,8 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
     int* istart = reinterpret_cast<int*>(smem + 4 * sp.inv_len);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* F = smem + 4 * sp.inv_len + sp.istart_len + warp * sp.per_warp;
-    int* spill = reinterpret_cast<int*>(F + sp.half) + lane;
+    float* ZS = F + sp.half;
+    int* spill = reinterpret_cast<int*>(ZS + sp.zs_len) + lane;
     // per distance d = m + 1: (1/d, 1/d, 2d + 1, 2d + 1); 1/d correctly rounded
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
         const float r = __frcp_rn((float)(m + 1));
@@ -433,19 +487,12 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
         }
         next = __shfl_sync(0xffffffffu, next, 0);
         __syncwarp();   // the staged row is visible to every lane
-        int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
-        const int slot = it.c * 32 + lane;
-        if (L - 2 > LONG_WALK && it.K - 1 > LONG_WALK) {
-            if (it.pov == SMALL_POV)
-                sweep_lane<SMALL_POV, SMALL_UNROLL, true>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
-            else
-                sweep_lane<LARGE_POV, LARGE_UNROLL, true>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
-        } else {
-            if (it.pov == SMALL_POV)
-                sweep_lane<SMALL_POV, SMALL_UNROLL, false>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
-            else
-                sweep_lane<LARGE_POV, LARGE_UNROLL, false>(F, tab, cvrow, spill, L, slot, it.K, it.h0, it.rev);
+        if (PRUNE) {
+            suffix_max(F, ZS, L, lane);
+            __syncwarp();
         }
+        int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
+        sweep_item<LONG, PRUNE>(it, F, ZS, tab, cvrow, spill, lane);
     }
 }
 
@@ -664,8 +711,8 @@ cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, in
 
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
-                         int wmax, int dmax, unsigned* counter, int num_sms, int smem_optin, int max_warps,
-                         cudaStream_t stream)
+                         int wmax, int dmax, int prune, unsigned* counter, int num_sms, int smem_optin,
+                         int max_warps, cudaStream_t stream)
 {
     if (ndir <= 0 || total_items <= 0) return cudaSuccess;
     constexpr int U = LARGE_UNROLL;
@@ -678,7 +725,11 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
     sp.inv_len = (std::min(dmax, wmax) + 2 * U + 8 + 1) & ~1;
     sp.istart_len = (ndir + 1 + 3) & ~3;
     sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
-    sp.per_warp = sp.half + (wmax - 2 > LONG_WALK ? 64 * LARGE_POV : 0);
+    const bool longw = wmax - 2 > LONG_WALK && dmax - 1 > LONG_WALK;
+    sp.zs_len = prune ? ((wmax + ZS_STRIDE - 1) / ZS_STRIDE + 4) & ~3 : 0;
+    sp.per_warp = sp.half + sp.zs_len + (longw ? 32 * LARGE_POV : 0);
+    void (*kern)(SweepParams) = prune ? (longw ? sweep_kernel<true, true> : sweep_kernel<true, false>)
+                                      : (longw ? sweep_kernel<false, true> : sweep_kernel<false, false>);
     const size_t fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
     const size_t per_warp = (size_t)sp.per_warp * 4;
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
@@ -687,34 +738,14 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
     const int cap = max_warps > 0 ? std::min(max_warps, SWEEP_MAX_WARPS) : SWEEP_MAX_WARPS;
     int warps = (int)std::min<size_t>((smem_optin - fixed) / per_warp, (size_t)cap);
     const size_t smem = fixed + (size_t)warps * per_warp;
-    cudaError_t err = cudaFuncSetAttribute(sweep_kernel,
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sweep_kernel, warps * 32, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    sweep_kernel<<<per_sm * num_sms, warps * 32, smem, stream>>>(sp);
+    kern<<<per_sm * num_sms, warps * 32, smem, stream>>>(sp);
     return cudaGetLastError();
-}
-
-int sweep_chunks(int W, int K, int mode, int p4_pct)
-{
-    if (mode) return row_chunks(W, mode);
-    // row_chunks grows with L for either group size, so the most is the
-    // count at W or at the longest row below W that takes SMALL_POV groups;
-    // scanning down stops once SMALL_POV rows can no longer need more.
-    // Memoised per thread: a plan asks for few distinct (W, K).
-    thread_local std::map<std::tuple<int, int, int>, int> memo;
-    const auto key = std::make_tuple(W, K, p4_pct);
-    const auto it = memo.find(key);
-    if (it != memo.end()) return it->second;
-    int most = row_chunks(W, row_pov(W, K, 0, p4_pct));
-    for (int L = W; L >= 2 && row_chunks(L, SMALL_POV) > most; --L)
-        if (row_pov(L, K, 0, p4_pct) == SMALL_POV) { most = row_chunks(L, SMALL_POV); break; }
-    if (memo.size() > 4096) memo.clear();
-    memo.emplace(key, most);
-    return most;
 }
 
 int unskew_per_split(int ndir, int nsplit)

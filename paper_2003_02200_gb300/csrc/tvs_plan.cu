@@ -309,8 +309,7 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
             const size_t wp = (size_t)((d.W + 3) & ~3);
             const size_t s2 = slab + (size_t)d.R * wp;
             const long long r2 = nrows + d.R;
-            const int Kc = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
-            const long long it2 = items + 2LL * d.R * dir_chunks(tn, d.W, Kc);
+            const long long it2 = items + 2LL * d.R;
             if (ii > i && (chunk_bytes(s2, r2, ii - i + 1) > avail || ii - i >= kMaxChunkDirs ||
                            it2 > kMaxChunkItems))
                 break;
@@ -368,14 +367,13 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
             v.row_off = (int)roff;
             v.pov = pov_mode(tn, d.W);
             v.p4_pct = tn.p4_cost_pct;
-            v.chunks = dir_chunks(tn, d.W, v.K);
             v.gidx = plan->inst_k[t];
             v.job = plan->inst_job[t];
             v.g = (float)d.g;
             v.h0 = (float)J.h0;
             off += (size_t)d.R * v.Wp;
             roff += d.R;
-            c.items += 2 * d.R * v.chunks;
+            c.items += 2 * d.R;
             plan->istart.push_back(c.items);
             c.max_R = std::max(c.max_R, d.R);
             c.max_tiles = std::max(c.max_tiles, ((d.R + SKEW_TP - 1) / SKEW_TP) * ((d.W + SKEW_TJ - 1) / SKEW_TJ));
@@ -498,7 +496,7 @@ void build_header(const BatchPlan& plan, const Layout& L, char* base, bool host_
 }
 
 int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* base, int num_sms, int smem_optin,
-                   int max_warps, cudaStream_t s, int* kernels, cudaEvent_t before_unskew)
+                   const Tuning& tn, cudaStream_t s, int* kernels, cudaEvent_t before_unskew)
 {
     const DirDev* d_dirs = reinterpret_cast<const DirDev*>(base + L.dirs);
     const JobDev* d_jobs = reinterpret_cast<const JobDev*>(base + L.jobs);
@@ -527,7 +525,7 @@ int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* bas
         {
             Timer t(h, K_SWEEP, s, c.evals);
             TVS_CUDA(launch_sweep(cd, d_istart + c.istart_at, nd, c.items, d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                                  c.wmax, c.dmax, d_counter, num_sms, smem_optin, max_warps, s),
+                                  c.wmax, c.dmax, tn.prune, d_counter, num_sms, smem_optin, tn.sweep_max_warps, s),
                      "sweep launch");
         }
         if (before_unskew) {
@@ -591,7 +589,7 @@ int run_batch(tvs_ctx* h, const std::vector<JobSpec>& jobs, cudaStream_t s, bool
     }
     rc = upload_header(h, img, base + L.hdr, s);
     if (rc) return rc;
-    rc = enqueue_chunks(h, plan, L, base, h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, s);
+    rc = enqueue_chunks(h, plan, L, base, h->num_sms, h->smem_optin, h->tuning, s);
     if (rc) return rc;
     if (host_io) {
         const size_t bytes = (size_t)jobs[0].rows * jobs[0].cols * 4;

@@ -307,8 +307,8 @@ int enqueue_step(tvs_server* S, Lane& lane, const std::vector<Slice>& slices)
              "copy step tables");
     for (const Slice& sl : slices) TVS_CUDA(cudaStreamWaitEvent(lane.stream, sl.r->loaded, 0), "wait for DEM");
     int kernels = 0;
-    rc = enqueue_chunks(nullptr, plan, L, lane.scratch, S->num_sms, S->smem_optin, S->tuning.sweep_max_warps,
-                        lane.stream, &kernels, S->last_step_done);
+    rc = enqueue_chunks(nullptr, plan, L, lane.scratch, S->num_sms, S->smem_optin, S->tuning, lane.stream, &kernels,
+                        S->last_step_done);
     if (rc) return rc;
     TVS_CUDA(cudaEventRecord(lane.done, lane.stream), "record step end");
     S->last_step_done = lane.done;
@@ -588,8 +588,7 @@ int tvs_server_submit(tvs_server_handle S, const float* dem, int rows, int cols,
         r->cum_evals[k + 1] = r->cum_evals[k] + (double)r->work[k].evals;
         r->cum_slab[k + 1] = r->cum_slab[k] + (long long)d.R * wp;
         r->cum_rows[k + 1] = r->cum_rows[k] + d.R;
-        const int Kc = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
-        r->cum_items[k + 1] = r->cum_items[k] + 2LL * d.R * dir_chunks(S->tuning, d.W, Kc);
+        r->cum_items[k + 1] = r->cum_items[k] + 2LL * d.R;
         if ((k + 1) % FP32_GROUP == 0 || k + 1 == n_sectors) {
             const int g0 = (k / FP32_GROUP) * FP32_GROUP;
             worst_group = std::max(worst_group,

@@ -127,6 +127,31 @@ def test_direction_cv_long_walks_stay_exact(ctx, orc, cols, rng):
     assert np.array_equal(got, want)
 
 
+@pytest.mark.parametrize("kind,h0,rng", [("fractal", 1.5, 0.0), ("fractal", 30.0, 900.0), ("spiky", 10.0, 0.0),
+                                         ("flat", 1.5, 0.0), ("ramp", 0.0, 0.0)])
+def test_pruning_changes_no_bit(ctx, kind, h0, rng):
+    """Exact horizon pruning stops walks whose remaining targets cannot rise
+    above the running maximum: every per-sample measure and every area is
+    the same with and without it."""
+    rows, cols = 230, 170
+    if kind == "flat":
+        dem = np.zeros((rows, cols), np.float32)
+    elif kind == "ramp":
+        dem = (np.arange(cols, dtype=np.float32)[None, :] * 3.0).repeat(rows, 0)
+    else:
+        dem = terrain.fractal_dem(rows, cols, 0.8, 900.0, seed=77, spike_frac=0.05 if kind == "spiky" else 0.0)
+    with tvs.Context(0) as c:
+        c.set_tuning(prune=0)
+        cv0 = [c.debug_direction_cv(dem, 10.0, h0, 36, rng, k) for k in (0, 5, 9, 13, 22, 31)]
+        a0 = c.total_viewshed(dem, 10.0, h0, 36, rng)
+        c.set_tuning(prune=1)
+        cv1 = [c.debug_direction_cv(dem, 10.0, h0, 36, rng, k) for k in (0, 5, 9, 13, 22, 31)]
+        a1 = c.total_viewshed(dem, 10.0, h0, 36, rng)
+    for x, y in zip(cv0, cv1):
+        assert np.array_equal(x, y)
+    assert np.array_equal(a0, a1)
+
+
 # ---------------------------------------------------------- total viewshed --
 
 def test_tvs100_matches_fp32_oracle_and_fp64_tolerance(ctx, orc):

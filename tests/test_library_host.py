@@ -19,7 +19,7 @@ def test_library_exports_every_declared_function(lib):
     assert len(names) >= 12
     for name in names:
         assert hasattr(lib, name), name
-    assert lib.tvs_abi_version() == 1
+    assert lib.tvs_abi_version() == 2
 
 
 @pytest.mark.parametrize("n,rows,cols", [(180, 100, 100), (7, 13, 29), (360, 50, 21), (1, 2, 2), (4, 9, 5)])
