@@ -67,6 +67,9 @@ def load() -> C.CDLL:
             lib.orc_line_range.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64, i64p, i64p]
             lib.orc_column_offsets.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p,
                                                C.c_void_p, C.c_int]
+            lib.orc_direct_viewshed.argtypes = [
+                C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int,
+                C.c_void_p, C.c_int64, C.c_void_p]
             lib.orc_count_evals.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]
             lib.orc_count_evals.restype = C.c_int64
             _lib = lib
@@ -111,6 +114,18 @@ def total_viewshed(dem, step: float, h0: float, n: int, max_range: float = 0.0, 
         info["threads"] = used.value
         info["evals_visited"] = nev.value
     return out.reshape(rows, cols) if cells is None else out
+
+
+def direct_viewshed(dem, step: float, h0: float, n: int, max_range: float = 0.0, prec: int = 64,
+                    cells=None) -> np.ndarray:
+    """Singular viewsheds by definition (Alg. 1-3: lines of sight through the
+    POV cell itself, no virtual POVs) of the cells listed by flat index."""
+    a = _dem(dem)
+    idx = np.ascontiguousarray(cells, dtype=np.int64).ravel()
+    out = np.empty(idx.size, dtype=np.float64)
+    _check(load().orc_direct_viewshed(a.ctypes.data, a.shape[0], a.shape[1], step, h0, n, max_range, prec,
+                                      idx.ctypes.data, idx.size, out.ctypes.data), "direct_viewshed")
+    return out
 
 
 def cell_direction(dem, step, h0, n, max_range, prec, i, j, k) -> list[dict]:

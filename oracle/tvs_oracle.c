@@ -474,4 +474,106 @@ int64_t orc_count_evals(int rows, int cols, int n, double step, double max_range
     return E;
 }
 
+/*
+ * The singular viewshed by its definition (Alg. 1-3), without the skewed
+ * layout's virtual POVs: the POV is the cell itself, lifted by h0, and each
+ * direction's line of sight passes through the cell centre.  Along the view's
+ * walk axis the line meets column j at row i + (j - j0) * t, sampled the way
+ * Alg. 6 samples (integer part and 32-bit fraction of the fixed-point offset,
+ * linear blend of the two rows it falls between, usable iff both rows lie in
+ * the DEM).  Each direction adds g * (cv_fwd + cv_bwd) with the walks of
+ * Alg. 2 / Alg. 8 read as in walk64; the area is scaled as in Alg. 1.  This is
+ * the reference the sDEM discretisation (virtual POVs on lines through whole
+ * rows) is compared with, the way section 5 compares sDEM with TVS.
+ */
+static inline void direct_pos(const orc_dir* d, int64_t i, int64_t j0, int64_t j, int64_t* a, uint32_t* fr)
+{
+    /* y = (j - j0) * t in 32.32 fixed point; |y| < 2^47.  floor(y / 2^32) and
+     * its remainder, for either sign of y. */
+    int64_t y = (j - j0) * (int64_t)d->t_fx;
+    int64_t q = y >= 0 ? y / (int64_t)4294967296LL : -((-y + 4294967295LL) / (int64_t)4294967296LL);
+    *a = i + q;
+    *fr = (uint32_t)(y - q * (int64_t)4294967296LL);
+}
+
+static inline int direct_ok(const orc_dir* d, int64_t i, int64_t j0, int64_t j)
+{
+    if (j < 0 || j >= d->W) return 0;
+    int64_t a; uint32_t fr;
+    direct_pos(d, i, j0, j, &a, &fr);
+    if (a < 0) return 0;
+    return fr == 0 ? (a <= d->H - 1) : (a + 1 <= d->H - 1);
+}
+
+static double direct_walk(const orc_ctx* c, const orc_dir* d, int64_t i, int64_t j0, int dir)
+{
+    int vis = 1;
+    int64_t open = 0, last = 0, cv = 0;
+    double h64 = (double)view_at(c->dem, c->cols, d, i, j0) + c->h0;
+    float h32 = view_at(c->dem, c->cols, d, i, j0) + (float)c->h0;
+    double maxth = -INFINITY;
+    float maxth32 = -INFINITY;
+    for (int64_t dd = 1; dd <= d->K; ++dd) {
+        int64_t j = j0 + dir * dd;
+        if (!direct_ok(d, i, j0, j)) break;
+        int64_t a; uint32_t fr;
+        direct_pos(d, i, j0, j, &a, &fr);
+        int above;
+        if (c->prec == 64) {
+            double z = (double)view_at(c->dem, c->cols, d, a, j);
+            if (fr != 0) {
+                double r = (double)fr / TWO32;
+                z = (1.0 - r) * z + r * (double)view_at(c->dem, c->cols, d, a + 1, j);
+            }
+            double th = (z - h64) / (double)dd;
+            above = th > maxth;
+            if (th > maxth) maxth = th;
+        } else {
+            float z = view_at(c->dem, c->cols, d, a, j);
+            if (fr != 0) {
+                float r = (float)fr * 0x1p-32f;
+                float pa = (1.0f - r) * z;
+                float pb = r * view_at(c->dem, c->cols, d, a + 1, j);
+                z = pa + pb;
+            }
+            float diff = z - h32;
+            float th = diff * c->rcp[dd];
+            above = th > maxth32;
+            if (th > maxth32) maxth32 = th;
+        }
+        if (above && !vis) open = dd;
+        if (!above && vis) cv += dd * dd - open * open;
+        vis = above;
+        last = dd;
+    }
+    if (vis) cv += last * last - open * open;
+    return (double)cv;
+}
+
+int orc_direct_viewshed(const float* dem, int rows, int cols, double step, double h0, int n,
+                        double max_range, int prec, const int64_t* idx, int64_t count, double* out)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, dem, rows, cols, step, h0, n, max_range, prec);
+    if (rc) return rc;
+    if (!idx || !out || count < 0) { ctx_free(&c); return ORC_ERR_ARG; }
+    for (int64_t q = 0; q < count; ++q)
+        if (idx[q] < 0 || idx[q] >= (int64_t)rows * cols) { ctx_free(&c); return ORC_ERR_ARG; }
+    double scale = pappus_scale(n, step);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int64_t q = 0; q < count; ++q) {
+        int64_t iD = idx[q] / cols, jD = idx[q] % cols;
+        double acc = 0.0;
+        for (int k = 0; k < n; ++k) {
+            const orc_dir* d = &c.dirs[k];
+            int64_t i, j;
+            to_view(d, iD, jD, &i, &j);
+            acc += d->g * (direct_walk(&c, d, i, j, +1) + direct_walk(&c, d, i, j, -1));
+        }
+        out[q] = scale * acc;
+    }
+    ctx_free(&c);
+    return ORC_OK;
+}
+
 int orc_abi_version(void) { return 1; }

@@ -200,3 +200,46 @@ def walk_lengths(rows: int, cols: int, n: int, step: float, max_range: float, iD
     t = tan_of(n, m)
     return [(v["w"], v["L_fwd"], v["L_bwd"], 1.0 + t * t)
             for v in cell_direction_cv(dem, step, 1.0, n, max_range, iD, jD, k)]
+
+
+def direct_profile(view: View, t: float, i: int, j0: int, direction: int, K: int) -> list[float]:
+    """Heights of the targets of the half-line through view cell (i, j0)
+    itself (no virtual POVs): Y(j) = i + (j - j0) * t."""
+    out = []
+    d = 1
+    while d <= K:
+        j = j0 + direction * d
+        if j < 0 or j >= view.W:
+            break
+        Y = i + (j - j0) * t
+        if 0 < abs(Y - round(Y)) < AMBIGUOUS:
+            raise AssertionError("sample too close to a grid line for a float reference")
+        if not _usable(view.H, Y):
+            break
+        out.append(_height(view.V, Y, j))
+        d += 1
+    return out
+
+
+def brute_direct_viewshed(dem: np.ndarray, step: float, h0: float, n: int, max_range: float = 0.0,
+                          cells=None) -> np.ndarray:
+    """Singular viewsheds by definition (Alg. 1-3): the POV is the cell itself
+    and every line of sight passes through it."""
+    rows, cols = dem.shape
+    if cells is None:
+        cells = range(rows * cols)
+    out = []
+    for c in cells:
+        iD, jD = divmod(int(c), cols)
+        acc = 0.0
+        for k in range(n):
+            frame, m = frame_of(n, k)
+            t = tan_of(n, m)
+            view = View(dem, frame)
+            i, j0 = view.cell_to_view(iD, jD)
+            K = walk_limit(step, max_range, t)
+            h = float(view.V[i, j0]) + h0
+            cv = sum(measure(visible_intervals(h, direct_profile(view, t, i, j0, s, K))) for s in (+1, -1))
+            acc += (1.0 + t * t) * cv
+        out.append(math.pi / (2 * n) * step * step * acc)
+    return np.array(out)

@@ -383,3 +383,88 @@ def test_oracle_rejects_bad_arguments(orc):
         orc.total_viewshed(bad, 10.0, 1.5, 4)
     with pytest.raises(ValueError):
         orc.total_viewshed(dem, 10.0, float("inf"), 4)
+
+
+# --- the singular viewshed by definition (Alg. 1-3), no virtual POVs ---------
+
+@pytest.mark.parametrize("rows,cols,n,max_range", [
+    (12, 12, 8, 0.0), (9, 14, 16, 0.0), (7, 6, 180, 0.0), (11, 9, 7, 0.0), (13, 10, 12, 47.0), (2, 9, 5, 0.0),
+])
+def test_direct_viewshed_brute_force(orc, rows, cols, n, max_range):
+    """Alg. 1-3 with the line of sight through the POV cell itself: the oracle
+    against explicit interval lists from floating-point geometry."""
+    dem = rand_dem(rows, cols, seed=rows * 31 + cols + n)
+    cells = list(range(rows * cols))
+    got = orc.direct_viewshed(dem, 10.0, 1.5, n, max_range, prec=64, cells=cells)
+    want = refgeom.brute_direct_viewshed(dem, 10.0, 1.5, n, max_range, cells=cells)
+    np.testing.assert_allclose(got, want, rtol=1e-9, atol=0)
+
+
+@pytest.mark.parametrize("n", [4, 9, 180])
+def test_direct_viewshed_flat_closed_form(orc, n):
+    """Flat ground and h0 > 0: every target is visible, so each half-line adds
+    L^2 (L its number of targets), counted here with exact rational geometry:
+    column j of the line through view cell (i, j0) is a target iff
+    0 <= i + (j - j0) t <= H - 1 (Alg. 1-3 with the Alg. 6 sampling)."""
+    from fractions import Fraction
+    rows, cols = 14, 11
+    dem = np.zeros((rows, cols), np.float32)
+    cells = [0, 5, 3 * cols + 7, rows * cols - 1, 6 * cols + 5]
+    got = orc.direct_viewshed(dem, 3.0, 2.0, n, 0.0, prec=64, cells=cells)
+    for q, c in enumerate(cells):
+        iD, jD = divmod(c, cols)
+        acc = Fraction(0)
+        for k in range(n):
+            d = orc.direction(n, k, rows, cols)
+            t = Fraction(d["t_fx"], 1 << 32)
+            view = refgeom.View(dem, d["frame"])
+            i, j0 = view.cell_to_view(iD, jD)
+            for s in (1, -1):
+                L = 0
+                while 0 <= j0 + s * (L + 1) < view.W and 0 <= i + s * (L + 1) * t <= view.H - 1:
+                    L += 1
+                acc += (1 + t * t) * L * L
+        want = scale_of(n, 3.0) * float(acc)
+        assert got[q] == pytest.approx(want, rel=1e-12)
+
+
+def test_direct_viewshed_zero_height_flat(orc):
+    """Flat ground, h0 = 0: every slope is 0, so only the first target is
+    strictly above the initial -inf maximum; a half-line with L >= 2 targets
+    adds 2^2 (its segment closes at the second target), one with L = 1 adds 1."""
+    rows, cols = 8, 8
+    dem = np.zeros((rows, cols), np.float32)
+    got = orc.direct_viewshed(dem, 1.0, 0.0, 1, 0.0, prec=64, cells=[3 * cols + 3, 0, cols - 1])
+    # n = 1: the walk axis is the row; cell (3, 3) has 4 targets east and 3 west
+    assert got[0] == pytest.approx(math.pi / 2 * (4 + 4), rel=1e-15)
+    # (0, 0): 7 targets east, none west; (0, 7): none east, 7 west
+    assert got[1] == pytest.approx(math.pi / 2 * 4, rel=1e-15)
+    assert got[2] == pytest.approx(math.pi / 2 * 4, rel=1e-15)
+
+
+@pytest.mark.parametrize("prec", [64, 32])
+def test_direct_equals_sdem_when_lines_hit_cell_centres(orc, prec):
+    """With n in {1, 2, 4} every direction has t in {0, 1}: the sampled lines of
+    the skewed layout pass through every cell centre, so each cell is its own
+    (single) virtual POV and sDEM and the definition coincide exactly."""
+    dem = rand_dem(15, 12, seed=9)
+    cells = list(range(15 * 12))
+    for n in (1, 2, 4):
+        a = orc.total_viewshed(dem, 10.0, 1.5, n, 0.0, prec=prec, cells=cells)
+        b = orc.direct_viewshed(dem, 10.0, 1.5, n, 0.0, prec=prec, cells=cells)
+        np.testing.assert_array_equal(a, b)
+
+
+def test_direct_differs_from_sdem_only_by_discretisation(orc):
+    """For general n the two differ (virtual POVs on whole-row lines against the
+    cell's own lines) but stay close on smooth terrain: the sDEM discretisation
+    error the paper reports against TVS (section 5) is of the order of 1 %."""
+    rows, cols = 40, 40
+    y, x = np.mgrid[0:rows, 0:cols]
+    dem = (200.0 * np.sin(x / 9.0) * np.cos(y / 11.0)).astype(np.float32)
+    cells = [c for c in range(rows * cols) if c % 7 == 0]
+    a = orc.total_viewshed(dem, 10.0, 1.5, 60, 0.0, prec=64, cells=cells)
+    b = orc.direct_viewshed(dem, 10.0, 1.5, 60, 0.0, prec=64, cells=cells)
+    rel = np.abs(a - b) / b
+    assert not np.array_equal(a, b)
+    assert np.median(rel) < 0.05
