@@ -253,6 +253,28 @@ int tvs_profile_enable(tvs_handle h, int on);
  * to max entries to stats and their number to *count. */
 int tvs_profile_read(tvs_handle h, tvs_kernel_stats* stats, int max, int* count);
 
+/* ---------------------------------------------- singular / multiple viewsheds --
+ * The visible area of each of npov points of view (section 2.1: the singular
+ * viewshed of Alg. 1-3; several POVs give the multiple viewshed of the
+ * paper's first experiment).  pov_ij: HOST array of npov (row, col) pairs of
+ * DEM cells.  d_dem: rows*cols float32 on the device; d_area: npov float32 on
+ * the device (m^2); stream-ordered like tvs_total_viewshed_device (the POV
+ * list is copied before the call returns).  Modes:
+ *   TVS_POINTS_SDEM:   the sDEM discretisation; area[q] is bit for bit the
+ *                      value tvs_total_viewshed gives for that cell;
+ *   TVS_POINTS_DIRECT: Alg. 1-3 by definition, lines of sight through the
+ *                      POV cell itself (no virtual POVs); the difference from
+ *                      TVS_POINTS_SDEM is the sDEM discretisation.
+ * Work per POV: n_sectors x 2 lines x (forward + backward) walks.
+ * Errors: TVS_ERR_ARG (NULL pointer, bad job, a POV outside the DEM, unknown
+ * mode), TVS_ERR_OOM, TVS_ERR_CUDA. */
+#define TVS_POINTS_SDEM   0
+#define TVS_POINTS_DIRECT 1
+
+int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, int cols, double step_m, double obs_height_m,
+                        int n_sectors, double max_range_m, const int32_t* pov_ij, int npov, int mode, float* d_area,
+                        void* cuda_stream);
+
 /* ------------------------------------------------------- request server --
  * Serving total viewsheds to callers that submit DEMs as they arrive (the
  * paper computes one DEM at a time; this is an addition).  A server owns one

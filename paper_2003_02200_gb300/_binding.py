@@ -131,6 +131,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             "tvs_debug_rowmap": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, i32p], C.c_int),
             "tvs_debug_direction_cv": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
+            "tvs_viewshed_points": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
+                                     C.c_int, C.c_int, vp, vp], C.c_int),
             "tvs_server_create": ([C.c_int, C.POINTER(ServerConfig), C.POINTER(vp)], C.c_int),
             "tvs_server_submit": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
                                    i64p], C.c_int),
@@ -322,6 +324,27 @@ class Context:
         if stream is None:
             stream = torch.cuda.current_stream()
         _check(self._lib.tvs_total_viewshed_batch(self.handle, arr, len(arr), stream.cuda_stream))
+
+    def viewshed_points(self, dem, step_m: float, obs_height_m: float, n_sectors: int, max_range_m: float,
+                        povs, mode: str = "sdem", out=None, stream=None):
+        """tvs_viewshed_points: visible area (m^2) of each POV (row, col) of
+        `povs` on a torch CUDA DEM; mode "sdem" (the total viewshed map's value
+        at the cell) or "direct" (Alg. 1-3, lines through the cell itself).
+        Returns a float32 CUDA tensor of len(povs) areas."""
+        import torch
+        if not (isinstance(dem, torch.Tensor) and dem.is_cuda and dem.dtype == torch.float32
+                and dem.dim() == 2 and dem.is_contiguous()):
+            raise ValueError("dem must be a contiguous 2-D float32 CUDA tensor")
+        p = np.ascontiguousarray(povs, dtype=np.int32).reshape(-1, 2)
+        if out is None:
+            out = torch.empty(len(p), dtype=torch.float32, device=dem.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(dem.device)
+        m = {"sdem": 0, "direct": 1}[mode]
+        _check(self._lib.tvs_viewshed_points(self.handle, dem.data_ptr(), dem.shape[0], dem.shape[1], step_m,
+                                             obs_height_m, n_sectors, max_range_m, p.ctypes.data, len(p), m,
+                                             out.data_ptr(), stream.cuda_stream))
+        return out
 
     def get_tuning(self) -> dict:
         t = Tuning()

@@ -1,0 +1,93 @@
+"""Singular and multiple viewsheds of a list of POVs (tvs_viewshed_points):
+the sDEM mode gives the total viewshed map's value at each cell bit for bit,
+the direct mode (Alg. 1-3, lines through the cell itself) matches the
+oracle's definition."""
+import numpy as np
+import pytest
+
+import paper_2003_02200_gb300 as tvs
+from paper_2003_02200_gb300 import terrain
+from paper_2003_02200_gb300._binding import TVS_ERR_ARG
+
+pytestmark = pytest.mark.gpu
+
+FP32_RTOL = 4e-6
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    c = tvs.Context(0)
+    yield c
+    c.close()
+
+
+def _povs(rows, cols, count, seed):
+    rng = np.random.default_rng(seed)
+    p = np.stack([rng.integers(0, rows, count), rng.integers(0, cols, count)], 1)
+    corners = np.array([[0, 0], [0, cols - 1], [rows - 1, 0], [rows - 1, cols - 1], [rows // 2, 0]])
+    return np.concatenate([p, corners]).astype(np.int32)
+
+
+@pytest.mark.parametrize("rows,cols,n,rng,h0", [(120, 90, 180, 0.0, 1.5), (64, 200, 36, 900.0, 10.0),
+                                                (3, 257, 16, 0.0, 1.0), (150, 150, 45, 0.0, 0.0)])
+def test_sdem_points_equal_the_total_map(ctx, rows, cols, n, rng, h0):
+    import torch
+    dem = terrain.fractal_dem(rows, cols, 0.8, 600.0, seed=rows + cols)
+    d = torch.from_numpy(dem).cuda()
+    full = ctx.total_viewshed_device(d, 10.0, h0, n, rng)
+    povs = _povs(rows, cols, 40, seed=n)
+    got = ctx.viewshed_points(d, 10.0, h0, n, rng, povs, mode="sdem")
+    torch.cuda.synchronize()
+    want = full.cpu().numpy()[povs[:, 0], povs[:, 1]]
+    assert np.array_equal(got.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("rows,cols,n,rng,h0", [(90, 70, 180, 0.0, 1.5), (60, 130, 24, 700.0, 8.0)])
+def test_direct_points_match_the_oracle_definition(ctx, orc, rows, cols, n, rng, h0):
+    import torch
+    dem = terrain.fractal_dem(rows, cols, 0.75, 500.0, seed=rows * cols)
+    d = torch.from_numpy(dem).cuda()
+    povs = _povs(rows, cols, 30, seed=rows)
+    got = ctx.viewshed_points(d, 10.0, h0, n, rng, povs, mode="direct").cpu().numpy()
+    cells = povs[:, 0].astype(np.int64) * cols + povs[:, 1]
+    o32 = orc.direct_viewshed(dem, 10.0, h0, n, rng, prec=32, cells=cells)
+    np.testing.assert_allclose(got, o32, rtol=FP32_RTOL, atol=0)
+    o64 = orc.direct_viewshed(dem, 10.0, h0, n, rng, prec=64, cells=cells)
+    rel = np.abs(got - o64) / o64
+    assert np.mean(rel <= 1e-4) >= 0.9 and rel.max() <= 5e-2
+
+
+def test_direct_equals_sdem_when_lines_hit_cell_centres(ctx):
+    import torch
+    dem = terrain.fractal_dem(80, 95, 0.8, 400.0, seed=3)
+    d = torch.from_numpy(dem).cuda()
+    povs = _povs(80, 95, 50, seed=4)
+    for n in (1, 2, 4):
+        a = ctx.viewshed_points(d, 10.0, 1.5, n, 0.0, povs, mode="sdem").cpu().numpy()
+        b = ctx.viewshed_points(d, 10.0, 1.5, n, 0.0, povs, mode="direct").cpu().numpy()
+        assert np.array_equal(a, b)
+
+
+def test_multiple_viewshed_of_ten_povs_at_paper_scale(ctx):
+    """The paper's first experiment: the viewsheds of 10 random POVs of the
+    2000 x 2000 DEM; each equals the total viewshed map's value."""
+    import torch
+    w = terrain.WORKLOADS["tvs2000"]
+    dem = terrain.workload_dem("tvs2000")
+    d = torch.from_numpy(dem).cuda()
+    povs = _povs(2000, 2000, 10, seed=2003)[:10]
+    got = ctx.viewshed_points(d, w["step"], w["h0"], w["n"], 0.0, povs).cpu().numpy()
+    full = ctx.total_viewshed_device(d, w["step"], w["h0"], w["n"], 0.0).cpu().numpy()
+    assert np.array_equal(got, full[povs[:, 0], povs[:, 1]])
+    direct = ctx.viewshed_points(d, w["step"], w["h0"], w["n"], 0.0, povs, mode="direct").cpu().numpy()
+    assert np.all(np.isfinite(direct)) and np.all(direct > 0)
+
+
+def test_points_refuse_bad_arguments(ctx):
+    import torch
+    d = torch.zeros((10, 12), device="cuda")
+    with pytest.raises(tvs.TvsError) as ei:
+        ctx.viewshed_points(d, 10.0, 1.5, 8, 0.0, [[10, 0]])
+    assert ei.value.code == TVS_ERR_ARG and "outside" in str(ei.value)
+    with pytest.raises(tvs.TvsError):
+        ctx.viewshed_points(d, 10.0, 1.5, 8, 0.0, np.zeros((0, 2)))
