@@ -301,7 +301,7 @@ typedef struct tvs_server* tvs_server_handle;
 typedef struct {
     size_t  hbm_budget_bytes;  /* whole server; 0 = min(80 GiB, 85% of free memory) */
     size_t  step_slot_bytes;   /* scratch of one lane; 0 = min(4 GiB, budget / 8) */
-    double  step_evals;        /* evaluations per step; 0 = 4e10 */
+    double  step_evals;        /* evaluations per step (work count, before pruning); 0 = 1.6e11 */
     double  rate_hint;         /* evaluations per second the deadline policy assumes; 0 = 5e12 */
     int32_t max_active;        /* admitted requests at once; 0 = 256 */
     int32_t policy;            /* TVS_POLICY_*; 0 = deadline */

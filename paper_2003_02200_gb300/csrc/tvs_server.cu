@@ -510,7 +510,7 @@ int tvs_server_create(int device, const tvs_server_config* cfg_in, tvs_server_ha
     if (cfg.step_slot_bytes == 0)
         cfg.step_slot_bytes = std::min<size_t>((size_t)4 << 30, cfg.hbm_budget_bytes / 8);
     cfg.step_slot_bytes = align256(cfg.step_slot_bytes);
-    if (cfg.step_evals == 0) cfg.step_evals = 4e10;
+    if (cfg.step_evals == 0) cfg.step_evals = 1.6e11;
     if (cfg.rate_hint == 0) cfg.rate_hint = 5e12;
     if (cfg.max_active == 0) cfg.max_active = 256;
     const int num_sms = prop.multiProcessorCount;
