@@ -13,7 +13,7 @@ namespace tvs {
 constexpr int SMALL_POV = 4;
 constexpr int SMALL_UNROLL = 16;
 constexpr int LARGE_POV = 8;
-constexpr int LARGE_UNROLL = 24;
+constexpr int LARGE_UNROLL = 28;
 #ifndef TVS_SWEEP_MAX_WARPS
 #define TVS_SWEEP_MAX_WARPS 16
 #endif

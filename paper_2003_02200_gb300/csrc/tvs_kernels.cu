@@ -216,10 +216,10 @@ __device__ __forceinline__ void sweep_block(const float* w, const float4* __rest
 // range beyond it) move their FP32 partial measures into integers every
 // FLUSH_STEPS steps: a measure is a sum of odd integers 2d + 1 and stays exact
 // in FP32 only below 2^24 (a walk of D steps sums to at most D^2 + 2D, and
-// FLUSH_STEPS steps at d < 16384 add at most 1.3e7).  Shorter walks never
+// FLUSH_STEPS steps at d < 16384 add at most 1.1e7).  Shorter walks never
 // flush (the LONG = false instantiation).
 constexpr int LONG_WALK = 4000;
-constexpr int FLUSH_STEPS = 384;   // a multiple of SMALL_UNROLL and LARGE_UNROLL
+constexpr int FLUSH_STEPS = 336;   // a multiple of SMALL_UNROLL and LARGE_UNROLL
 // Suffix maxima of a staged row are kept at every ZS_STRIDE-th sample; pruning
 // checks every PRUNE_EVERY blocks.
 constexpr int ZS_STRIDE = 4;
