@@ -70,6 +70,9 @@ def load() -> C.CDLL:
             lib.orc_direct_viewshed.argtypes = [
                 C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int,
                 C.c_void_p, C.c_int64, C.c_void_p]
+            lib.orc_visibility_map.argtypes = [
+                C.c_void_p, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, C.c_int,
+                C.c_void_p, C.c_int, C.c_void_p]
             lib.orc_count_evals.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double]
             lib.orc_count_evals.restype = C.c_int64
             _lib = lib
@@ -126,6 +129,17 @@ def direct_viewshed(dem, step: float, h0: float, n: int, max_range: float = 0.0,
     _check(load().orc_direct_viewshed(a.ctypes.data, a.shape[0], a.shape[1], step, h0, n, max_range, prec,
                                       idx.ctypes.data, idx.size, out.ctypes.data), "direct_viewshed")
     return out
+
+
+def visibility_map(dem, step: float, h0: float, n: int, max_range: float = 0.0, prec: int = 64,
+                   povs=((0, 0),)) -> np.ndarray:
+    """Number of the POVs (row, col) that see each cell (int32 map)."""
+    a = _dem(dem)
+    p = np.ascontiguousarray(povs, dtype=np.int32).reshape(-1, 2)
+    count = np.zeros(a.shape, dtype=np.int32)
+    _check(load().orc_visibility_map(a.ctypes.data, a.shape[0], a.shape[1], step, h0, n, max_range, prec,
+                                     p.ctypes.data, len(p), count.ctypes.data), "visibility_map")
+    return count
 
 
 def cell_direction(dem, step, h0, n, max_range, prec, i, j, k) -> list[dict]:

@@ -576,4 +576,109 @@ int orc_direct_viewshed(const float* dem, int rows, int cols, double step, doubl
     return ORC_OK;
 }
 
+/*
+ * Visibility map (the boolean result of a singular viewshed, section 1; for
+ * several POVs, how many of them see each cell: a multiple viewshed).  Reading
+ * (the paper gives no cell rule): the 2n half-lines of Alg. 1 split the plane
+ * into sectors of width pi/n around their axes theta = k' pi/n, k' = 0..2n-1
+ * (k' >= n is the backward half of direction k' - n; in the D4 views that
+ * mirror the DEM, walking +j of the view goes along k' + n).  A cell belongs to the
+ * sector whose axis is nearest to the direction from the POV, with
+ * q = atan2(di, dj) * n / pi and k' = floor(q + 1/2) mod 2n (di south, dj east,
+ * in double precision).  Within the sector, the cell is visible iff the
+ * sample of the half-line through the POV cell (as in orc_direct_viewshed) at
+ * the cell's walk-axis column is visible (its slope strictly above every
+ * earlier one on the half-line); cells past the line's usable samples or past
+ * the walk limit are not visible, and the POV's own cell is.  count[c] (int32,
+ * rows*cols, accumulated) gains one for each POV that sees cell c.
+ */
+static void half_line_flags(const orc_ctx* c, const orc_dir* d, int64_t i, int64_t j0, int dir,
+                            unsigned char* vis, int64_t cap)
+{
+    double h64 = (double)view_at(c->dem, c->cols, d, i, j0) + c->h0;
+    float h32 = view_at(c->dem, c->cols, d, i, j0) + (float)c->h0;
+    double maxth = -INFINITY;
+    float maxth32 = -INFINITY;
+    for (int64_t dd = 1; dd <= d->K && dd < cap; ++dd) {
+        int64_t j = j0 + dir * dd;
+        if (!direct_ok(d, i, j0, j)) break;
+        int64_t a; uint32_t fr;
+        direct_pos(d, i, j0, j, &a, &fr);
+        if (c->prec == 64) {
+            double z = (double)view_at(c->dem, c->cols, d, a, j);
+            if (fr != 0) {
+                double r = (double)fr / TWO32;
+                z = (1.0 - r) * z + r * (double)view_at(c->dem, c->cols, d, a + 1, j);
+            }
+            double th = (z - h64) / (double)dd;
+            vis[dd] = th > maxth;
+            if (th > maxth) maxth = th;
+        } else {
+            float z = view_at(c->dem, c->cols, d, a, j);
+            if (fr != 0) {
+                float r = (float)fr * 0x1p-32f;
+                float pa = (1.0f - r) * z;
+                float pb = r * view_at(c->dem, c->cols, d, a + 1, j);
+                z = pa + pb;
+            }
+            float diff = z - h32;
+            float th = diff * c->rcp[dd];
+            vis[dd] = th > maxth32;
+            if (th > maxth32) maxth32 = th;
+        }
+    }
+}
+
+int orc_visibility_map(const float* dem, int rows, int cols, double step, double h0, int n, double max_range,
+                       int prec, const int32_t* pov_ij, int npov, int32_t* count)
+{
+    orc_ctx c;
+    int rc = ctx_init(&c, dem, rows, cols, step, h0, n, max_range, prec);
+    if (rc) return rc;
+    if (!pov_ij || !count || npov < 1) { ctx_free(&c); return ORC_ERR_ARG; }
+    for (int q = 0; q < npov; ++q)
+        if (pov_ij[2 * q] < 0 || pov_ij[2 * q] >= rows || pov_ij[2 * q + 1] < 0 || pov_ij[2 * q + 1] >= cols) {
+            ctx_free(&c);
+            return ORC_ERR_ARG;
+        }
+    int64_t cap = (rows > cols ? rows : cols) + 1;
+    unsigned char* vis = (unsigned char*)calloc((size_t)(2 * n) * (size_t)cap, 1);
+    if (!vis) { ctx_free(&c); return ORC_ERR_OOM; }
+    for (int q = 0; q < npov; ++q) {
+        int64_t i0 = pov_ij[2 * q], jj0 = pov_ij[2 * q + 1];
+        memset(vis, 0, (size_t)(2 * n) * (size_t)cap);
+        for (int k = 0; k < n; ++k) {
+            int64_t i, j;
+            to_view(&c.dirs[k], i0, jj0, &i, &j);
+            /* slot k: the walk along +j of the view, slot n + k: along -j */
+            half_line_flags(&c, &c.dirs[k], i, j, +1, vis + (size_t)k * cap, cap);
+            half_line_flags(&c, &c.dirs[k], i, j, -1, vis + (size_t)(n + k) * cap, cap);
+        }
+        for (int64_t iD = 0; iD < rows; ++iD)
+            for (int64_t jD = 0; jD < cols; ++jD) {
+                int seen;
+                if (iD == i0 && jD == jj0) {
+                    seen = 1;
+                } else {
+                    double qq = atan2((double)(iD - i0), (double)(jD - jj0)) * (double)n / M_PI;
+                    int64_t kp = (int64_t)floor(qq + 0.5);
+                    kp = ((kp % (2 * n)) + 2 * n) % (2 * n);
+                    int k = (int)(kp % n);
+                    /* +j of the view points along theta_k in views 0 and 1 (identity,
+                     * transpose) and along theta_k + pi in views 2 and 3 (mirrored) */
+                    int plus = (c.dirs[k].frame <= 1) == (kp < n);
+                    int64_t iv, jv, iv0, jv0;
+                    to_view(&c.dirs[k], iD, jD, &iv, &jv);
+                    to_view(&c.dirs[k], i0, jj0, &iv0, &jv0);
+                    int64_t dd = plus ? jv - jv0 : jv0 - jv;
+                    seen = dd >= 1 && dd < cap && vis[(size_t)(plus ? k : n + k) * cap + dd];
+                }
+                count[iD * cols + jD] += seen;
+            }
+    }
+    free(vis);
+    ctx_free(&c);
+    return ORC_OK;
+}
+
 int orc_abi_version(void) { return 1; }

@@ -243,3 +243,44 @@ def brute_direct_viewshed(dem: np.ndarray, step: float, h0: float, n: int, max_r
             acc += (1.0 + t * t) * cv
         out.append(math.pi / (2 * n) * step * step * acc)
     return np.array(out)
+
+
+def sector_of(n: int, di: int, dj: int) -> tuple[int, float]:
+    """Half-line sector k' (0..2n-1) nearest to the direction (di south, dj
+    east) and the fraction of q = atan2(di, dj) n / pi (ties at 0.5)."""
+    q = math.atan2(di, dj) * n / math.pi
+    kp = math.floor(q + 0.5) % (2 * n)
+    return kp, q - math.floor(q)
+
+
+def brute_visibility_map(dem: np.ndarray, step: float, h0: float, n: int, povs, max_range: float = 0.0):
+    """Visibility counts by rescanning: a cell is seen from a POV when the
+    target at its walk-axis column on its sector's half-line through the POV
+    is strictly above every earlier target's slope."""
+    rows, cols = dem.shape
+    count = np.zeros((rows, cols), np.int32)
+    for (i0, j0) in povs:
+        for iD in range(rows):
+            for jD in range(cols):
+                if (iD, jD) == (i0, j0):
+                    count[iD, jD] += 1
+                    continue
+                kp, _ = sector_of(n, iD - i0, jD - j0)
+                k = kp % n
+                frame, m = frame_of(n, k)
+                t = tan_of(n, m)
+                view = View(dem, frame)
+                vi0, vj0 = view.cell_to_view(i0, j0)
+                vi, vj = view.cell_to_view(iD, jD)
+                plus = (frame <= 1) == (kp < n)
+                d = (vj - vj0) if plus else (vj0 - vj)
+                if d < 1:
+                    continue
+                prof = direct_profile(view, t, vi0, vj0, 1 if plus else -1, walk_limit(step, max_range, t))
+                if d > len(prof):
+                    continue
+                h = float(view.V[vi0, vj0]) + h0
+                slopes = [(prof[x] - h) / (x + 1) for x in range(d)]
+                if all(slopes[d - 1] > s for s in slopes[: d - 1]):
+                    count[iD, jD] += 1
+    return count

@@ -91,3 +91,38 @@ def test_points_refuse_bad_arguments(ctx):
     assert ei.value.code == TVS_ERR_ARG and "outside" in str(ei.value)
     with pytest.raises(tvs.TvsError):
         ctx.viewshed_points(d, 10.0, 1.5, 8, 0.0, np.zeros((0, 2)))
+
+
+def _ambiguous(rows, cols, n, povs, eps=1e-9):
+    """Cells within eps of a sector boundary for some POV (numpy's and the
+    device's double atan2 may round those either way)."""
+    ii, jj = np.mgrid[0:rows, 0:cols]
+    amb = np.zeros((rows, cols), bool)
+    for (i0, j0) in povs:
+        q = np.arctan2((ii - i0).astype(np.float64), (jj - j0).astype(np.float64)) * n / np.pi
+        f = q - np.floor(q)
+        amb |= (np.abs(f - 0.5) < eps) & ~((ii == i0) & (jj == j0))
+    return amb
+
+
+@pytest.mark.parametrize("rows,cols,n,rng,h0,npov", [(120, 90, 180, 0.0, 1.5, 3), (64, 200, 36, 900.0, 10.0, 5),
+                                                     (2000, 2000, 180, 0.0, 1.5, 2)])
+def test_visibility_map_matches_the_oracle(ctx, orc, rows, cols, n, rng, h0, npov):
+    import torch
+    dem = terrain.fractal_dem(rows, cols, 0.8, 900.0 if rows < 1000 else 1500.0, seed=rows + n)
+    d = torch.from_numpy(dem).cuda()
+    povs = _povs(rows, cols, npov, seed=rows + 1)[:npov]
+    got = ctx.visibility_map(d, 10.0, h0, n, rng, povs).cpu().numpy()
+    want = orc.visibility_map(dem, 10.0, h0, n, rng, prec=32, povs=povs)
+    amb = _ambiguous(rows, cols, n, povs)
+    assert amb.mean() < 1e-3
+    assert np.array_equal(got[~amb], want[~amb])
+    assert got.max() <= npov and all(got[p[0], p[1]] >= 1 for p in povs)
+
+
+def test_visibility_map_refuses_bad_arguments(ctx):
+    import torch
+    d = torch.zeros((10, 12), device="cuda")
+    with pytest.raises(tvs.TvsError) as ei:
+        ctx.visibility_map(d, 10.0, 1.5, 8, 0.0, [[0, 12]])
+    assert ei.value.code == TVS_ERR_ARG

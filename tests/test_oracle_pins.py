@@ -468,3 +468,68 @@ def test_direct_differs_from_sdem_only_by_discretisation(orc):
     rel = np.abs(a - b) / b
     assert not np.array_equal(a, b)
     assert np.median(rel) < 0.05
+
+
+# --- visibility map (which cells a POV sees; counts for several POVs) --------
+
+def _ambiguous_cells(rows, cols, n, povs, eps=1e-9):
+    amb = np.zeros((rows, cols), bool)
+    for (i0, j0) in povs:
+        for iD in range(rows):
+            for jD in range(cols):
+                if (iD, jD) != (i0, j0):
+                    _, f = refgeom.sector_of(n, iD - i0, jD - j0)
+                    amb[iD, jD] |= abs(f - 0.5) < eps
+    return amb
+
+
+@pytest.mark.parametrize("n,rows,cols,rng", [(8, 13, 17, 0.0), (36, 15, 12, 0.0), (7, 11, 11, 0.0),
+                                              (20, 16, 14, 75.0)])
+def test_visibility_map_brute_force(orc, n, rows, cols, rng):
+    dem = rand_dem(rows, cols, seed=n + rows)
+    povs = [(rows // 2, cols // 3), (0, cols - 1), (rows - 1, 2)]
+    got = orc.visibility_map(dem, 10.0, 1.5, n, rng, prec=64, povs=povs)
+    want = refgeom.brute_visibility_map(dem, 10.0, 1.5, n, povs, rng)
+    amb = _ambiguous_cells(rows, cols, n, povs)
+    assert np.array_equal(got[~amb], want[~amb])
+
+
+@pytest.mark.parametrize("n", [4, 9, 36])
+def test_visibility_map_flat_ground_reach(orc, n):
+    """Flat ground, h0 > 0: every reached target is visible, so a cell is seen
+    iff its sector's half-line through the POV still lies in the DEM at the
+    cell's walk-axis column (exact rational geometry)."""
+    from fractions import Fraction
+    rows, cols = 12, 15
+    dem = np.zeros((rows, cols), np.float32)
+    i0, j0 = 5, 9
+    got = orc.visibility_map(dem, 10.0, 2.0, n, 0.0, prec=64, povs=[(i0, j0)])
+    amb = _ambiguous_cells(rows, cols, n, [(i0, j0)])
+    for iD in range(rows):
+        for jD in range(cols):
+            if amb[iD, jD]:
+                continue
+            if (iD, jD) == (i0, j0):
+                assert got[iD, jD] == 1
+                continue
+            kp, _ = refgeom.sector_of(n, iD - i0, jD - j0)
+            d = orc.direction(n, kp % n, rows, cols)
+            view = refgeom.View(dem, d["frame"])
+            vi0, vj0 = view.cell_to_view(i0, j0)
+            vi, vj = view.cell_to_view(iD, jD)
+            plus = (d["frame"] <= 1) == (kp < n)
+            dd = (vj - vj0) if plus else (vj0 - vj)
+            t = Fraction(d["t_fx"], 1 << 32)
+            reach = dd >= 1 and all(0 <= vi0 + (x if plus else -x) * t <= view.H - 1 for x in range(1, dd + 1))
+            assert got[iD, jD] == int(reach), (iD, jD)
+
+
+def test_visibility_map_counts_add_over_povs(orc):
+    """The map of several POVs is the sum of their single maps (each cell
+    counts the POVs that see it)."""
+    dem = rand_dem(14, 13, seed=4)
+    povs = [(1, 1), (7, 6), (13, 12), (3, 10)]
+    together = orc.visibility_map(dem, 10.0, 1.5, 24, 0.0, prec=32, povs=povs)
+    apart = sum(orc.visibility_map(dem, 10.0, 1.5, 24, 0.0, prec=32, povs=[p]) for p in povs)
+    assert np.array_equal(together, apart)
+    assert all(together[p] >= 1 for p in povs)
