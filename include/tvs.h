@@ -275,6 +275,22 @@ int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, int cols, do
                         int n_sectors, double max_range_m, const int32_t* pov_ij, int npov, int mode, float* d_area,
                         void* cuda_stream);
 
+/* Visibility map of a list of POVs (the boolean map of a singular viewshed,
+ * section 1; with several POVs, how many see each cell).  Reading (the paper
+ * gives no cell rule): the 2n half-lines of Alg. 1 cut the plane into sectors
+ * of width pi/n around their axes; a cell belongs to the sector whose axis is
+ * nearest to the direction from the POV (a double-precision angle) and is
+ * visible iff the sample of that half-line, drawn through the POV cell as in
+ * TVS_POINTS_DIRECT, at the cell's walk-axis column is visible (slope
+ * strictly above every earlier one); cells the half-line does not reach
+ * (past the DEM or the walk limit) are not visible, the POV's own cell is.
+ * d_count: rows*cols int32 on the device, written with the number of the
+ * npov POVs (pov_ij: HOST (row, col) pairs) that see each cell.
+ * Stream-ordered.  Errors: TVS_ERR_ARG, TVS_ERR_OOM, TVS_ERR_CUDA. */
+int tvs_visibility_map(tvs_handle h, const float* d_dem, int rows, int cols, double step_m, double obs_height_m,
+                       int n_sectors, double max_range_m, const int32_t* pov_ij, int npov, int32_t* d_count,
+                       void* cuda_stream);
+
 /* ------------------------------------------------------- request server --
  * Serving total viewsheds to callers that submit DEMs as they arrive (the
  * paper computes one DEM at a time; this is an addition).  A server owns one

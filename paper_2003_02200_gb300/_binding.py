@@ -133,6 +133,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
                                         C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
             "tvs_viewshed_points": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
                                      C.c_int, C.c_int, vp, vp], C.c_int),
+            "tvs_visibility_map": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
+                                    C.c_int, vp, vp], C.c_int),
             "tvs_server_create": ([C.c_int, C.POINTER(ServerConfig), C.POINTER(vp)], C.c_int),
             "tvs_server_submit": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
                                    i64p], C.c_int),
@@ -344,6 +346,24 @@ class Context:
         _check(self._lib.tvs_viewshed_points(self.handle, dem.data_ptr(), dem.shape[0], dem.shape[1], step_m,
                                              obs_height_m, n_sectors, max_range_m, p.ctypes.data, len(p), m,
                                              out.data_ptr(), stream.cuda_stream))
+        return out
+
+    def visibility_map(self, dem, step_m: float, obs_height_m: float, n_sectors: int, max_range_m: float, povs,
+                       out=None, stream=None):
+        """tvs_visibility_map: int32 CUDA map of how many of the POVs (row, col)
+        see each cell of the torch CUDA DEM."""
+        import torch
+        if not (isinstance(dem, torch.Tensor) and dem.is_cuda and dem.dtype == torch.float32
+                and dem.dim() == 2 and dem.is_contiguous()):
+            raise ValueError("dem must be a contiguous 2-D float32 CUDA tensor")
+        p = np.ascontiguousarray(povs, dtype=np.int32).reshape(-1, 2)
+        if out is None:
+            out = torch.empty(dem.shape, dtype=torch.int32, device=dem.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(dem.device)
+        _check(self._lib.tvs_visibility_map(self.handle, dem.data_ptr(), dem.shape[0], dem.shape[1], step_m,
+                                            obs_height_m, n_sectors, max_range_m, p.ctypes.data, len(p),
+                                            out.data_ptr(), stream.cuda_stream))
         return out
 
     def get_tuning(self) -> dict:

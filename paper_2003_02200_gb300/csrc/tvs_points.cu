@@ -206,10 +206,151 @@ __global__ void points_finalize(PointsParams pp)
     pp.area[q] = area_of(tot, pp.scale);
 }
 
+// ------------------------------------------------------------ visibility map --
+// flags[(q * 2n + slot) * cap + d] = 1 when target d of a half-line of POV q
+// is visible: slot k walks +j of direction k's view, slot n + k walks -j, both
+// along the line through the POV cell itself (the direct reading).
+struct MapParams {
+    const float* dem;
+    const DirDev* dirs;
+    const int* pov;
+    unsigned char* flags;
+    int* count;
+    int rows, cols, n, npov, cap;
+    float h0;
+};
+
+__global__ void __launch_bounds__(64) map_flags_kernel(MapParams mp)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (q, slot)
+    if (t >= (long long)mp.npov * 2 * mp.n) return;
+    const int q = (int)(t / (2 * mp.n)), slot = (int)(t % (2 * mp.n));
+    const int k = slot % mp.n, dir = slot < mp.n ? 1 : -1;
+    const DirDev d = mp.dirs[k];
+    const int iD = mp.pov[2 * q], jD = mp.pov[2 * q + 1];
+    int i, j0;
+    switch (d.frame) {
+    case 0:  i = iD; j0 = jD; break;
+    case 1:  i = jD; j0 = iD; break;
+    case 2:  i = jD; j0 = d.W - 1 - iD; break;
+    default: i = d.H - 1 - iD; j0 = jD; break;
+    }
+    unsigned char* f = mp.flags + t * mp.cap;
+    const float h = __fadd_rn(view_at(mp.dem, mp.cols, d, i, j0), mp.h0);
+    float M = __int_as_float(0xff800000);
+    for (int dd = 1; dd <= d.K && dd < mp.cap; ++dd) {
+        const int j = j0 + dir * dd;
+        long long a;
+        unsigned fr;
+        line_pos(d, true, i, j0, j, &a, &fr);
+        if (!usable(d, a, fr, j)) break;
+        const float z = sample_at(mp.dem, mp.cols, d, a, fr, j);
+        const float th = __fmul_rn(__fsub_rn(z, h), __frcp_rn((float)dd));
+        f[dd] = th > M ? 1 : 0;
+        M = fmaxf(M, th);
+    }
+}
+
+// View coordinates of DEM cell (iD, jD) in direction d's view.
+__device__ __forceinline__ void to_view(const DirDev& d, int iD, int jD, int* i, int* j)
+{
+    switch (d.frame) {
+    case 0:  *i = iD; *j = jD; break;
+    case 1:  *i = jD; *j = iD; break;
+    case 2:  *i = jD; *j = d.W - 1 - iD; break;
+    default: *i = d.H - 1 - iD; *j = jD; break;
+    }
+}
+
+// One thread per cell: the sector of each POV it falls in (nearest of the 2n
+// half-line axes k' pi / n, from a double-precision angle) and the flag of
+// the target at the cell's walk-axis column.
+__global__ void map_raster_kernel(MapParams mp)
+{
+    const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= (long long)mp.rows * mp.cols) return;
+    const int iD = (int)(c / mp.cols), jD = (int)(c % mp.cols);
+    int seen = 0;
+    for (int q = 0; q < mp.npov; ++q) {
+        const int i0 = mp.pov[2 * q], j0 = mp.pov[2 * q + 1];
+        if (iD == i0 && jD == j0) { ++seen; continue; }
+        const double qq = atan2((double)(iD - i0), (double)(jD - j0)) * (double)mp.n / 3.141592653589793;
+        long long kp = (long long)floor(qq + 0.5);
+        kp = ((kp % (2 * mp.n)) + 2 * mp.n) % (2 * mp.n);
+        const int k = (int)(kp % mp.n);
+        const DirDev d = mp.dirs[k];
+        // +j of the view points along theta_k in views 0 and 1, along theta_k + pi in views 2 and 3
+        const bool plus = (d.frame <= 1) == (kp < mp.n);
+        int iv, jv, iv0, jv0;
+        to_view(d, iD, jD, &iv, &jv);
+        to_view(d, i0, j0, &iv0, &jv0);
+        const int dd = plus ? jv - jv0 : jv0 - jv;
+        const long long slot = plus ? k : mp.n + k;
+        if (dd >= 1 && dd < mp.cap) seen += mp.flags[((long long)q * 2 * mp.n + slot) * mp.cap + dd];
+    }
+    mp.count[c] = seen;
+}
+
 }  // namespace
 }  // namespace tvs
 
 using namespace tvs;
+
+extern "C" int tvs_visibility_map(tvs_handle h, const float* d_dem, int rows, int cols, double step_m,
+                                  double obs_height_m, int n_sectors, double max_range_m, const int32_t* pov_ij,
+                                  int npov, int32_t* d_count, void* cuda_stream)
+{
+    if (!h) return fail(TVS_ERR_ARG, "handle is NULL");
+    if (!d_dem || !pov_ij || !d_count) return fail(TVS_ERR_ARG, "d_dem, pov_ij or d_count is NULL");
+    int rc = check_job(rows, cols, step_m, obs_height_m, n_sectors, max_range_m);
+    if (rc) return rc;
+    if (npov < 1) return fail(TVS_ERR_ARG, "npov must be >= 1");
+    for (int q = 0; q < npov; ++q)
+        if (pov_ij[2 * q] < 0 || pov_ij[2 * q] >= rows || pov_ij[2 * q + 1] < 0 || pov_ij[2 * q + 1] >= cols)
+            return fail(TVS_ERR_ARG, "POV " + std::to_string(q) + " lies outside the DEM");
+    const int cap = std::max(rows, cols) + 1;
+    const size_t flag_bytes = (size_t)npov * 2 * n_sectors * cap;
+    if (flag_bytes > ((size_t)1 << 34)) return fail(TVS_ERR_OOM, "too many POVs x directions for the flag table");
+    DeviceGuard g(h->device);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    std::vector<DirDev> dirs(n_sectors);
+    for (int k = 0; k < n_sectors; ++k) {
+        HostDir d;
+        make_direction(n_sectors, k, rows, cols, step_m, max_range_m, &d);
+        DirDev& v = dirs[k];
+        std::memset(&v, 0, sizeof(v));
+        v.t_fx = d.t_fx; v.frame = d.frame; v.H = d.H; v.W = d.W; v.Wp = (d.W + 3) & ~3; v.D = d.D; v.R = d.R;
+        v.K = d.K == LLONG_MAX ? d.W : (int)std::min<long long>(d.K, d.W);
+        v.gidx = k; v.g = (float)d.g; v.h0 = (float)obs_height_m;
+    }
+    const size_t o_dirs = 0, o_pov = align256((size_t)n_sectors * sizeof(DirDev));
+    const size_t hdr = o_pov + align256((size_t)npov * 8);
+    const size_t o_flags = hdr;
+    const size_t total = o_flags + align256(flag_bytes);
+    rc = ensure_scratch(h, total);
+    if (rc) return rc;
+    std::vector<char> img(hdr, 0);
+    std::memcpy(img.data() + o_dirs, dirs.data(), dirs.size() * sizeof(DirDev));
+    std::memcpy(img.data() + o_pov, pov_ij, (size_t)npov * 8);
+    rc = upload_header(h, img, h->ws, s);
+    if (rc) return rc;
+    TVS_CUDA(cudaMemsetAsync(h->ws + o_flags, 0, flag_bytes, s), "clear visibility flags");
+    MapParams mp{};
+    mp.dem = d_dem;
+    mp.dirs = reinterpret_cast<const DirDev*>(h->ws + o_dirs);
+    mp.pov = reinterpret_cast<const int*>(h->ws + o_pov);
+    mp.flags = reinterpret_cast<unsigned char*>(h->ws + o_flags);
+    mp.count = d_count;
+    mp.rows = rows; mp.cols = cols; mp.n = n_sectors; mp.npov = npov; mp.cap = cap;
+    mp.h0 = (float)obs_height_m;
+    const long long walks = (long long)npov * 2 * n_sectors;
+    map_flags_kernel<<<(unsigned)((walks + 63) / 64), 64, 0, s>>>(mp);
+    TVS_CUDA(cudaGetLastError(), "visibility flags launch");
+    const long long cells = (long long)rows * cols;
+    map_raster_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(mp);
+    TVS_CUDA(cudaGetLastError(), "visibility raster launch");
+    return TVS_OK;
+}
 
 extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, int cols, double step_m,
                                    double obs_height_m, int n_sectors, double max_range_m, const int32_t* pov_ij,
