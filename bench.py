@@ -574,6 +574,8 @@ def run_serve_bench(args) -> int:
         for t in tickets:
             srv.wait(t)
         infos = [srv.query(t) for t in tickets]
+        for t in tickets:
+            srv.forget(t)
         lat = [q["t_done"] - (c0 + arrivals[i] * scale) for i, q in enumerate(infos)]
         return lat, max(q["t_done"] for q in infos) - c0
 

@@ -379,6 +379,12 @@ int tvs_server_wait(tvs_server_handle s, int64_t ticket, double timeout_s);
 /* State and timestamps of a request. */
 int tvs_server_query(tvs_server_handle s, int64_t ticket, tvs_request_info* info);
 
+/* Drop the record of a finished (DONE or FAILED) request: its ticket becomes
+ * unknown.  A server keeps every record until then, so long-running callers
+ * forget the requests they have collected.  TVS_ERR_STATE while the request
+ * is still in flight. */
+int tvs_server_forget(tvs_server_handle s, int64_t ticket);
+
 /* Counters of the server. */
 int tvs_server_get_stats(tvs_server_handle s, tvs_server_stats* stats);
 

@@ -141,6 +141,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             "tvs_server_wait": ([vp, C.c_int64, C.c_double], C.c_int),
             "tvs_server_query": ([vp, C.c_int64, C.POINTER(RequestInfo)], C.c_int),
             "tvs_server_get_stats": ([vp, C.POINTER(ServerStats)], C.c_int),
+            "tvs_server_forget": ([vp, C.c_int64], C.c_int),
             "tvs_server_clock": ([vp], C.c_double),
             "tvs_server_destroy": ([vp], None),
             "tvs_profile_enable": ([vp, C.c_int], C.c_int),
@@ -483,6 +484,12 @@ class Server:
         d["message"] = i.message.decode()
         d["state_name"] = REQUEST_STATES.get(i.state, str(i.state))
         return d
+
+    def forget(self, ticket: int) -> None:
+        """Drop the record of a finished request (tvs_server_forget)."""
+        _check(self._lib.tvs_server_forget(self.handle, ticket))
+        with self._mu:
+            self._live.pop(ticket, None)
 
     def stats(self) -> dict:
         st = ServerStats()

@@ -660,6 +660,24 @@ int tvs_server_query(tvs_server_handle S, int64_t ticket, tvs_request_info* info
     return TVS_OK;
 }
 
+int tvs_server_forget(tvs_server_handle S, int64_t ticket)
+{
+    if (!S) return fail(TVS_ERR_ARG, "server is NULL");
+    std::lock_guard<std::mutex> lk(S->mu);
+    auto it = S->reqs.find(ticket);
+    if (it == S->reqs.end()) return fail(TVS_ERR_ARG, "unknown ticket");
+    Request* r = it->second.get();
+    if (r->state != TVS_REQ_DONE && r->state != TVS_REQ_FAILED)
+        return fail(TVS_ERR_STATE, "the request is not finished");
+    for (Request* f : S->finishing)
+        if (f == r) return fail(TVS_ERR_STATE, "the request's download is still being waited for");
+    if (r->resident) return fail(TVS_ERR_STATE, "the request still holds arena space");
+    if (r->loaded) cudaEventDestroy(r->loaded);
+    if (r->finished) cudaEventDestroy(r->finished);
+    S->reqs.erase(it);
+    return TVS_OK;
+}
+
 int tvs_server_get_stats(tvs_server_handle S, tvs_server_stats* stats)
 {
     if (!S || !stats) return fail(TVS_ERR_ARG, "NULL argument");

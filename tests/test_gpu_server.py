@@ -140,6 +140,10 @@ def test_server_refuses_bad_requests_and_configs():
         t = srv.submit(dem, 10.0, 1.5, 24)
         assert srv.wait(t, timeout=60).shape == dem.shape
         assert srv.stats()["completed"] == 1
+        srv.forget(t)
+        with pytest.raises(tvs.TvsError) as ei:        # the record is gone
+            srv.query(t)
+        assert ei.value.code == TVS_ERR_ARG
 
 
 def test_close_with_requests_in_flight_finishes_admitted_ones():

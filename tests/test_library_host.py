@@ -72,6 +72,7 @@ def test_host_argument_errors(lib):
     assert lib.tvs_server_wait(None, 1, 0.0) == tvs._binding.TVS_ERR_ARG
     assert lib.tvs_server_query(None, 1, None) == tvs._binding.TVS_ERR_ARG
     assert lib.tvs_server_clock(None) == 0.0
+    assert lib.tvs_server_forget(None, 1) == tvs._binding.TVS_ERR_ARG
     lib.tvs_server_destroy(None)
 
 
