@@ -40,6 +40,11 @@
  * There is no skewed array here: every walk is taken directly in DEM (view)
  * coordinates, one cell and one direction at a time.
  *
+ * Besides the total viewshed (orc_total_viewshed and its per-direction and
+ * per-line detail), the oracle holds the singular viewshed by definition
+ * (orc_direct_viewshed: lines of sight through the POV cell itself, Alg. 1-3)
+ * and the visibility map of a list of POVs (orc_visibility_map).
+ *
  * Precision.  prec = 64 computes heights and slopes in double precision with a
  * true division.  prec = 32 takes every height and slope in single precision,
  * as the paper's kernels declare them ("float" in Alg. 6, 7 and 8): the blend

@@ -6,10 +6,11 @@
 
 namespace tvs {
 
-// Sweep tiling.  Each lane walks two groups of consecutive samples (a group
-// and its mirror), 32 lanes per warp item.  A row is swept with groups of
-// SMALL_POV samples (blocks of SMALL_UNROLL steps) or of LARGE_POV samples
-// (blocks of LARGE_UNROLL steps), chosen per row by row_pov.
+// Sweep tiling.  A warp item is one skewed row and one walk direction; the
+// row's POVs form groups of consecutive samples that the 32 lanes take from a
+// queue.  A row is swept with groups of SMALL_POV samples (blocks of
+// SMALL_UNROLL steps) or of LARGE_POV samples (blocks of LARGE_UNROLL steps),
+// chosen per row by row_pov.
 constexpr int SMALL_POV = 4;
 constexpr int SMALL_UNROLL = 16;
 constexpr int LARGE_POV = 8;

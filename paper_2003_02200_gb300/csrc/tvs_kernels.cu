@@ -5,7 +5,8 @@
 //   skew   : DEM -> skewed layout, one writer per sample (Kernel-1, Alg. 6,
 //            written as a gather instead of the paper's two-way scatter).
 //   sweep  : every usable sample of every skewed row walks its row forward and
-//            backward (Kernel-2, Alg. 7 and 8); the hot loop.
+//            backward (Kernel-2, Alg. 7 and 8); the hot loop, with exact
+//            horizon pruning as an option.
 //   unskew : blends the per-sample measures back onto DEM cells and sums the
 //            directions (Kernel-3, Alg. 9), with the Pappus / step^2 scale of
 //            Alg. 1 applied once at the end.
