@@ -322,7 +322,8 @@ typedef struct {
     int32_t max_active;        /* admitted requests at once; 0 = 256 */
     int32_t policy;            /* TVS_POLICY_*; 0 = deadline */
     int32_t lanes;             /* steps in flight, 1 or 2; 0 = 2 */
-    int32_t pad_;
+    int32_t fail_after_steps;  /* test hook: > 0 makes enqueueing step N+1 fail as a
+                                  CUDA error would (the host-side failure path); 0 = off */
 } tvs_server_config;
 
 #define TVS_REQ_QUEUED   0     /* submitted, waiting for arena room */

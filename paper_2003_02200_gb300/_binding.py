@@ -56,7 +56,7 @@ class Tuning(C.Structure):
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("step_slot_bytes", C.c_size_t), ("step_evals", C.c_double),
                 ("rate_hint", C.c_double), ("max_active", C.c_int32), ("policy", C.c_int32),
-                ("lanes", C.c_int32), ("pad_", C.c_int32)]
+                ("lanes", C.c_int32), ("fail_after_steps", C.c_int32)]
 
 
 class RequestInfo(C.Structure):
@@ -437,12 +437,12 @@ class Server:
 
     def __init__(self, device: int = 0, hbm_budget_bytes: int = 0, step_slot_bytes: int = 0,
                  step_evals: float = 0.0, rate_hint: float = 0.0, max_active: int = 0, policy: str = "deadline",
-                 lanes: int = 0):
+                 lanes: int = 0, fail_after_steps: int = 0):
         self._lib = load()
         if policy not in POLICIES:
             raise ValueError(f"policy must be one of {sorted(POLICIES)}")
         cfg = ServerConfig(hbm_budget_bytes, step_slot_bytes, step_evals, rate_hint, max_active, POLICIES[policy],
-                           lanes, 0)
+                           lanes, fail_after_steps)
         h = C.c_void_p()
         _check(self._lib.tvs_server_create(device, C.byref(cfg), C.byref(h)))
         self._s = h

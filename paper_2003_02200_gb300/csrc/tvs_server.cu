@@ -279,6 +279,8 @@ size_t lane_fixed_bytes(int num_sms)
 // Plan and enqueue one step on a free lane.  Called with the lock held.
 int enqueue_step(tvs_server* S, Lane& lane, const std::vector<Slice>& slices)
 {
+    if (S->cfg.fail_after_steps > 0 && S->st.steps >= S->cfg.fail_after_steps)
+        return fail(TVS_ERR_CUDA, "injected step failure (fail_after_steps)");
     std::vector<JobSpec> jobs;
     jobs.reserve(slices.size());
     for (const Slice& sl : slices) {
@@ -490,6 +492,7 @@ int tvs_server_create(int device, const tvs_server_config* cfg_in, tvs_server_ha
     tvs_server_config cfg{};
     if (cfg_in) cfg = *cfg_in;
     if (cfg.step_evals < 0 || cfg.rate_hint < 0 || cfg.max_active < 0 || cfg.lanes < 0 || cfg.lanes > 2 ||
+        cfg.fail_after_steps < 0 ||
         cfg.policy < 0 || cfg.policy > TVS_POLICY_SRPT || !std::isfinite(cfg.step_evals) ||
         !std::isfinite(cfg.rate_hint))
         return fail(TVS_ERR_ARG, "server config out of range");

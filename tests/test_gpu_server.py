@@ -154,3 +154,41 @@ def test_close_with_requests_in_flight_finishes_admitted_ones():
     t0 = time.time()
     srv.close()
     assert time.time() - t0 < 120
+
+
+def test_a_failed_step_fails_unfinished_requests_and_refuses_new_ones():
+    """Host-side failure injection (no GPU fault): enqueueing the third step
+    fails as a CUDA error would; every unfinished request fails with the
+    error, requests finished before stay done, new submissions are refused,
+    and shutdown does not hang."""
+    from paper_2003_02200_gb300._binding import TVS_ERR_CUDA, TVS_ERR_STATE
+    dems = _dems(900)
+    srv = tvs.Server(0, hbm_budget_bytes=2 * SLOT + (64 << 20), step_slot_bytes=SLOT, step_evals=2e8,
+                     policy="fifo", fail_after_steps=2)
+    # the large request first: it needs far more than two steps; the others may
+    # be refused already if the failure has happened by the time they arrive
+    tickets = []
+    for i in (BIG, 0, 1, 2):
+        try:
+            tickets.append(srv.submit(dems[i], REQS[i][3], REQS[i][4], REQS[i][2], REQS[i][5]))
+        except tvs.TvsError as e:
+            assert e.code == TVS_ERR_STATE and "injected" in str(e)
+    codes = []
+    for t in tickets:
+        try:
+            srv.wait(t, timeout=120)
+            codes.append(0)
+        except tvs.TvsError as e:
+            codes.append(e.code)
+            assert "injected" in str(e)
+    assert codes[0] == TVS_ERR_CUDA                 # the large request cannot finish in two steps
+    assert all(c in (0, TVS_ERR_CUDA) for c in codes)
+    infos = [srv.query(t) for t in tickets]
+    assert all(q["state_name"] in ("done", "failed") for q in infos)
+    assert srv.stats()["failed"] >= 1
+    with pytest.raises(tvs.TvsError) as ei:
+        srv.submit(dems[0], 10.0, 1.5, 8)
+    assert ei.value.code == TVS_ERR_STATE
+    t0 = time.time()
+    srv.close()
+    assert time.time() - t0 < 60
