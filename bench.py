@@ -177,6 +177,20 @@ def config_of(name: str, w: dict, E: int, world: int) -> dict:
             "parallelism": "replicas" if world > 1 else "single"}
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (first /proc/cpuinfo entry that has one)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key, _, val = line.partition(":")
+                if key.strip() in ("model name", "Model", "CPU part", "Hardware") and val.strip():
+                    return val.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -323,11 +337,17 @@ def run_ours(args) -> int:
     achieved = sweep["units"] / (sweep["total_ms"] / 1e3) if sweep.get("total_ms") else 0.0
     traffic = profiled_traffic(args.workload)
     launches = int(sum(v["launches"] for v in stats.values()))
+    hbm = peaks.get("hbm_gbs")
     kernels = {k: {"launches": v["launches"], "ms_per_launch": v["total_ms"] / max(v["launches"], 1),
                    "share": v["total_ms"] / max(sum(s["total_ms"] for s in stats.values()), 1e-12),
                    "rate": (v["units"] / (v["total_ms"] / 1e3) / 1e9) if v["total_ms"] else None,
                    "rate_unit": "G" + v["unit"] + "/s"}
                for k, v in stats.items() if v["launches"]}
+    for k, v in kernels.items():
+        # memory kernels against the measured copy bandwidth (algorithmic bytes)
+        if v["rate_unit"] == "Gbytes/s" and hbm and v["rate"] is not None:
+            v["frac_of_hbm"] = v["rate"] / hbm
+            v["hbm_peak_gbs"] = hbm
 
     if rank != 0:
         return 0
@@ -359,6 +379,7 @@ def run_ours(args) -> int:
         s = oracle_sample(w, dem_np, args.cpu_seconds)
         full_s = s["sec_per_cell"] * w["rows"] * w["cols"]
         line["cpu_baseline"] = {"value": E / full_s / 1e9, "unit": UNIT, "cores": s["threads"], "kind": "oracle",
+                                "cpu_model": cpu_model(),
                                 "sample": f"{s['cells']} random cells of the workload (all {w['n']} directions "
                                           f"each, FP64), {s['seconds']:.1f} s, extrapolated by cell count"}
     print(json.dumps(line), flush=True)
@@ -404,6 +425,7 @@ def run_reference(args) -> int:
         "data": "synthetic: seeded spectral-fractal DEM standing in for the paper's DEM10m datasets",
         "config": config_of(args.workload, w, E, world), "dems_per_s": 1.0 / full_s,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info.get("threads", 1), "kind": "oracle",
+                         "cpu_model": cpu_model(),
                          "sample": f"each step: {n_cells} random cells (all {w['n']} directions each, FP64), "
                                    "extrapolated to the whole DEM by cell count"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
