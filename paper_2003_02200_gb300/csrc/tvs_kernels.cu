@@ -568,9 +568,62 @@ __device__ __forceinline__ int find_chunk_job(const ChunkJob* __restrict__ cj, i
     return lo;
 }
 
+// 4-byte asynchronous global -> shared copies (the rows a CTA blends are not
+// 16-byte aligned in general, so no bulk copies).
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
+
+// The staged window of one direction for a tile: skewed rows pmin.. (np of
+// them) and view columns vj0.. (nj of them) of the direction's slabs.
+struct UnskewWin {
+    int pmin, np, vj0, nj;
+};
+
+__device__ __forceinline__ UnskewWin unskew_window(const DirDev& d, int iD0, int iD1, int jD0, int jD1)
+{
+    int vi0, vi1, vj0, vj1;
+    switch (d.frame) {
+    case 0:  vi0 = iD0; vi1 = iD1; vj0 = jD0; vj1 = jD1; break;
+    case 1:  vi0 = jD0; vi1 = jD1; vj0 = iD0; vj1 = iD1; break;
+    case 2:  vi0 = jD0; vi1 = jD1; vj0 = d.W - 1 - iD1; vj1 = d.W - 1 - iD0; break;
+    default: vi0 = d.H - 1 - iD1; vi1 = d.H - 1 - iD0; vj0 = jD0; vj1 = jD1; break;
+    }
+    UnskewWin w;
+    w.pmin = max(vi0 - dest_of(d.t_fx, vj1) + d.D - 1, 0);
+    const int pmax = min(vi1 - dest_of(d.t_fx, vj0) + d.D, d.R - 1);
+    w.np = pmax - w.pmin + 1;
+    w.vj0 = vj0;
+    w.nj = vj1 - vj0 + 1;
+    return w;
+}
+
+// Copies (asynchronously) the forward and backward measures of a window.
+__device__ __forceinline__ void unskew_stage(const UnskewParams& up, const DirDev& d, const UnskewWin& w, int* SF,
+                                             int* SB)
+{
+    const long long off = d.slab + (long long)w.pmin * d.Wp + w.vj0;
+    for (int idx = threadIdx.x; idx < w.np * 32; idx += UNSKEW_THREADS) {
+        const int r = idx >> 5, cc = idx & 31;
+        if (cc < w.nj) {
+            const long long a = off + (long long)r * d.Wp + cc;
+            cp_async4(SF + r * UNSKEW_PITCH + cc, up.cvf + a);
+            cp_async4(SB + r * UNSKEW_PITCH + cc, up.cvb + a);
+        }
+    }
+}
+
+// Directions are double-buffered: while the cells of a tile blend one
+// direction's staged rows, the next direction's rows are in flight.
 __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
 {
-    __shared__ float T[UNSKEW_ROWS * UNSKEW_PITCH];
+    __shared__ int SF[2][UNSKEW_ROWS * UNSKEW_PITCH];
+    __shared__ int SB[2][UNSKEW_ROWS * UNSKEW_PITCH];
     const ChunkJob c = up.cj[find_chunk_job(up.cj, up.ncj, blockIdx.x, false)];
     if ((int)blockIdx.z >= c.nsplit) return;
     const JobDev J = up.jobs[c.job];
@@ -588,32 +641,33 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
     for (int m = 0; m < UNSKEW_CELLS; ++m) { acc32[m] = 0.f; accx[m] = 0; }
     int group = kbeg < kend ? up.dirs[kbeg].gidx / FP32_GROUP : 0;
 
+    DirDev d_next;
+    UnskewWin w_next{0, 0, 0, 0};
+    if (kbeg < kend) {
+        d_next = up.dirs[kbeg];
+        w_next = unskew_window(d_next, iD0, iD1, jD0, jD1);
+        unskew_stage(up, d_next, w_next, SF[0], SB[0]);
+    }
+    cp_async_commit();
     for (int kk = kbeg; kk < kend; ++kk) {
-        const DirDev d = up.dirs[kk];
+        const int buf = (kk - kbeg) & 1;
+        const DirDev d = d_next;
+        const UnskewWin w = w_next;
+        if (kk + 1 < kend) {
+            d_next = up.dirs[kk + 1];
+            w_next = unskew_window(d_next, iD0, iD1, jD0, jD1);
+            unskew_stage(up, d_next, w_next, SF[buf ^ 1], SB[buf ^ 1]);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();          // every group but the one just issued has landed
+        __syncthreads();
         if (d.gidx / FP32_GROUP != group) {
 #pragma unroll
             for (int m = 0; m < UNSKEW_CELLS; ++m) { accx[m] += acc_of(acc32[m]); acc32[m] = 0.f; }
             group = d.gidx / FP32_GROUP;
         }
-        int vi0, vi1, vj0, vj1;
-        switch (d.frame) {
-        case 0:  vi0 = iD0; vi1 = iD1; vj0 = jD0; vj1 = jD1; break;
-        case 1:  vi0 = jD0; vi1 = jD1; vj0 = iD0; vj1 = iD1; break;
-        case 2:  vi0 = jD0; vi1 = jD1; vj0 = d.W - 1 - iD1; vj1 = d.W - 1 - iD0; break;
-        default: vi0 = d.H - 1 - iD1; vi1 = d.H - 1 - iD0; vj0 = jD0; vj1 = jD1; break;
-        }
-        const int pmin = max(vi0 - dest_of(d.t_fx, vj1) + d.D - 1, 0);
-        const int pmax = min(vi1 - dest_of(d.t_fx, vj0) + d.D, d.R - 1);
-        const int np = pmax - pmin + 1, nj = vj1 - vj0 + 1;
-        const long long off = d.slab + (long long)pmin * d.Wp + vj0;
-        for (int idx = threadIdx.x; idx < np * 32; idx += UNSKEW_THREADS) {
-            const int r = idx >> 5, cc = idx & 31;
-            if (cc < nj) {
-                const long long a = off + (long long)r * d.Wp + cc;
-                T[r * UNSKEW_PITCH + cc] = (float)(up.cvf[a] + up.cvb[a]);
-            }
-        }
-        __syncthreads();
+        const int* F = SF[buf];
+        const int* B = SB[buf];
 #pragma unroll
         for (int m = 0; m < UNSKEW_CELLS; ++m) {
             const int iD = iD0 + ly + 8 * m, jD = jD0 + lx;
@@ -628,27 +682,28 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
             const unsigned long long y = (unsigned long long)j * d.t_fx;
             const int dest = (int)(y >> 32);
             const unsigned fr = (unsigned)(y & 0xFFFFFFFFull);
-            const int rhi = i - dest + d.D - pmin;       // staged row of the line through i + r
-            const int cj = j - vj0;
+            const int hi = (i - dest + d.D - w.pmin) * UNSKEW_PITCH + (j - w.vj0);   // line through i + r
+            const int lo = hi - UNSKEW_PITCH;                                       // line through i - 1 + r
             float val;
             if (fr == 0u) {
-                val = T[rhi * UNSKEW_PITCH + cj];
+                val = (float)(F[hi] + B[hi]);
             } else {
                 const bool hi_ok = i <= d.H - 2, lo_ok = i >= 1;
                 if (hi_ok && lo_ok) {
                     const float r = __fmul_rn(__uint2float_rn(fr), 0x1p-32f);
-                    val = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, r), T[rhi * UNSKEW_PITCH + cj]),
-                                    __fmul_rn(r, T[(rhi - 1) * UNSKEW_PITCH + cj]));
+                    val = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, r), (float)(F[hi] + B[hi])),
+                                    __fmul_rn(r, (float)(F[lo] + B[lo])));
                 } else if (hi_ok) {
-                    val = T[rhi * UNSKEW_PITCH + cj];
+                    val = (float)(F[hi] + B[hi]);
                 } else {
-                    val = T[(rhi - 1) * UNSKEW_PITCH + cj];
+                    val = (float)(F[lo] + B[lo]);
                 }
             }
             acc32[m] = __fadd_rn(acc32[m], __fmul_rn(d.g, val));
         }
-        __syncthreads();
+        __syncthreads();             // the buffer is refilled two directions later
     }
+    cp_async_wait<0>();
     const long long cells = (long long)rows * cols;
 #pragma unroll
     for (int m = 0; m < UNSKEW_CELLS; ++m) {
