@@ -275,6 +275,14 @@ int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, int cols, do
                         int n_sectors, double max_range_m, const int32_t* pov_ij, int npov, int mode, float* d_area,
                         void* cuda_stream);
 
+/* Work count of tvs_viewshed_points: the number of targets its walks visit,
+ * sum over the npov POVs (pov_ij: HOST (row, col) pairs), the n_sectors
+ * directions, the lines (SDEM: the usable virtual POVs; DIRECT: the line
+ * through the cell) and both sides of min(usable targets, K).  Host only;
+ * returns a negative code on bad arguments. */
+int64_t tvs_count_point_evals(int rows, int cols, int n_sectors, double step_m, double max_range_m,
+                              const int32_t* pov_ij, int npov, int mode);
+
 /* Visibility map of a list of POVs (the boolean map of a singular viewshed,
  * section 1; with several POVs, how many see each cell).  Reading (the paper
  * gives no cell rule): the 2n half-lines of Alg. 1 cut the plane into sectors

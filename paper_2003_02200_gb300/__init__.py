@@ -5,9 +5,9 @@ ABI of ``include/tvs.h``); this package is its ctypes binding.  Importing the
 package does not load the library: the first call that needs it does, and
 raises if the library cannot be built or loaded.  There is no CPU fallback.
 """
-from ._binding import (Batch, Context, Server, TvsError, count_evals, declared_functions,  # noqa: F401
-                       direction, lib_path, load, total_viewshed_device_noalloc)
+from ._binding import (Batch, Context, Server, TvsError, count_evals, count_point_evals,  # noqa: F401
+                       declared_functions, direction, lib_path, load, total_viewshed_device_noalloc)
 from ._build import build  # noqa: F401
 
-__all__ = ["Batch", "Context", "Server", "TvsError", "build", "count_evals", "declared_functions", "direction", "lib_path",
-           "load", "total_viewshed_device_noalloc"]
+__all__ = ["Batch", "Context", "Server", "TvsError", "build", "count_evals", "count_point_evals", "declared_functions",
+           "direction", "lib_path", "load", "total_viewshed_device_noalloc"]

@@ -128,6 +128,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             "tvs_direction": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                C.POINTER(DirectionInfo)], C.c_int),
             "tvs_count_evals": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double], C.c_int64),
+            "tvs_count_point_evals": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, vp, C.c_int, C.c_int],
+                                      C.c_int64),
             "tvs_debug_rowmap": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, i32p], C.c_int),
             "tvs_debug_direction_cv": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
@@ -176,6 +178,17 @@ def direction(n_sectors: int, k: int, rows: int, cols: int, step_m: float = 1.0,
 
 def count_evals(rows: int, cols: int, n_sectors: int, step_m: float = 1.0, max_range_m: float = 0.0) -> int:
     E = load().tvs_count_evals(rows, cols, n_sectors, step_m, max_range_m)
+    if E < 0:
+        _check(int(E))
+    return int(E)
+
+
+def count_point_evals(rows: int, cols: int, n_sectors: int, povs, step_m: float = 1.0, max_range_m: float = 0.0,
+                      mode: str = "sdem") -> int:
+    """tvs_count_point_evals: targets visited by tvs_viewshed_points."""
+    p = np.ascontiguousarray(povs, dtype=np.int32).reshape(-1, 2)
+    E = load().tvs_count_point_evals(rows, cols, n_sectors, step_m, max_range_m, p.ctypes.data, len(p),
+                                     {"sdem": 0, "direct": 1}[mode])
     if E < 0:
         _check(int(E))
     return int(E)

@@ -112,81 +112,144 @@ __device__ __forceinline__ float area_of(__int128 v, double scale)
 }
 static_assert(ACC_FRAC_BITS == 56, "area_of scales by 2^-56");
 
-__global__ void __launch_bounds__(32) points_kernel(PointsParams pp)
-{
-    const int lane = threadIdx.x;
-    const int q = (int)(blockIdx.x / (unsigned)pp.ngroups), grp = (int)(blockIdx.x % (unsigned)pp.ngroups);
-    const int kk = lane >> 2, v = (lane >> 1) & 1, s = lane & 1;
-    const int k = grp * FP32_GROUP + kk;
-    const bool direct = pp.mode == TVS_POINTS_DIRECT;
-    int cv = 0;                      // this lane's half-line measure
-    bool valid = false;              // this lane's line exists
-    float r = 0.f;                   // blend weight of the lo line (SDEM)
-    bool hi_ok = true, lo_ok = false;
-    unsigned fr0 = 0u;
+// The line of one (direction k, virtual POV v) of POV q: its view, the POV's
+// view cell (i, j0), the line's base (SDEM: base row at column 0; DIRECT: the
+// cell row), and the blend data of the direction (fr0, r, hi_ok, lo_ok).
+struct PointLine {
     DirDev d;
-    if (k < pp.n) {
-        d = pp.dirs[k];
-        const int iD = pp.pov[2 * q], jD = pp.pov[2 * q + 1];
-        int i, j0;
-        switch (d.frame) {
-        case 0:  i = iD; j0 = jD; break;
-        case 1:  i = jD; j0 = iD; break;
-        case 2:  i = jD; j0 = d.W - 1 - iD; break;
-        default: i = d.H - 1 - iD; j0 = jD; break;
+    int i, j0;
+    long long base;
+    unsigned fr0;
+    float r;
+    bool hi_ok, lo_ok, valid;
+};
+
+__device__ __forceinline__ PointLine point_line(const PointsParams& pp, int q, int k, int v)
+{
+    PointLine L;
+    L.fr0 = 0u; L.r = 0.f; L.hi_ok = true; L.lo_ok = false; L.valid = false; L.base = 0; L.i = 0; L.j0 = 0;
+    if (k >= pp.n) return L;
+    L.d = pp.dirs[k];
+    const DirDev& d = L.d;
+    const int iD = pp.pov[2 * q], jD = pp.pov[2 * q + 1];
+    switch (d.frame) {
+    case 0:  L.i = iD; L.j0 = jD; break;
+    case 1:  L.i = jD; L.j0 = iD; break;
+    case 2:  L.i = jD; L.j0 = d.W - 1 - iD; break;
+    default: L.i = d.H - 1 - iD; L.j0 = jD; break;
+    }
+    if (pp.mode == TVS_POINTS_DIRECT) {
+        L.valid = v == 0;
+        L.base = L.i;
+    } else {
+        const unsigned long long y = (unsigned long long)L.j0 * d.t_fx;
+        const int dest = (int)(y >> 32);
+        L.fr0 = (unsigned)(y & 0xFFFFFFFFull);
+        L.hi_ok = L.fr0 == 0u || L.i <= d.H - 2;
+        L.lo_ok = L.fr0 != 0u && L.i >= 1;
+        L.r = __fmul_rn(__uint2float_rn(L.fr0), 0x1p-32f);
+        L.valid = v == 0 ? L.hi_ok : L.lo_ok;
+        L.base = (long long)L.i - dest - v;
+    }
+    return L;
+}
+
+// One half-line walked by a whole warp, 32 targets at a time: lane l takes
+// target d = c + l + 1 of chunk c, its FP32 slope is the serial walk's, and
+// a warp max-scan gives every lane the running maximum of the targets before
+// it (maximum is exact, so every visibility decision is the serial one).
+// The walk ends at the first unusable target or at K.  Returns the walk's measure
+// cv = 1 + sum_{d < n} v_d (2d + 1) (0 for n = 0) on every lane; with `flags`
+// each target's visibility is also stored at flags[d] (d < cap).
+__device__ __forceinline__ int walk_half_line(const float* dem, int cols, const DirDev& d, long long base, int j0,
+                                              bool direct, int dir, float h, unsigned char* flags, int cap, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    float M = __int_as_float(0xff800000);
+    int sum = 0;                      // this lane's sum of v_d (2d + 1) over every target it saw
+    int n = 0, lastvis = 0;           // targets so far; visibility of the latest one
+    for (int c = 0;; c += 32) {
+        const int dd = c + lane + 1;
+        bool ok = dd <= d.K;
+        long long a = 0;
+        unsigned fr = 0u;
+        const int j = j0 + dir * dd;
+        if (ok) {
+            line_pos(d, direct, base, j0, j, &a, &fr);
+            ok = usable(d, a, fr, j);
         }
-        long long base;              // the line: base row at column 0 (SDEM) or the cell row (DIRECT)
-        if (direct) {
-            valid = v == 0;
-            base = i;
-        } else {
-            const unsigned long long y = (unsigned long long)j0 * d.t_fx;
-            const int dest = (int)(y >> 32);
-            fr0 = (unsigned)(y & 0xFFFFFFFFull);
-            hi_ok = fr0 == 0u || i <= d.H - 2;
-            lo_ok = fr0 != 0u && i >= 1;
-            r = __fmul_rn(__uint2float_rn(fr0), 0x1p-32f);
-            valid = v == 0 ? hi_ok : lo_ok;
-            base = (long long)i - dest - v;
+        // the walk ends at the first unusable target, as the serial walk does
+        const unsigned okm = __ballot_sync(FULL, ok);
+        const int cnt = okm == FULL ? 32 : __ffs(~okm) - 1;
+        ok = lane < cnt;
+        float t = __int_as_float(0xff800000);
+        if (ok) t = __fmul_rn(__fsub_rn(sample_at(dem, cols, d, a, fr, j), h), __frcp_rn((float)dd));
+        float pm = t;                 // inclusive prefix maximum of the chunk
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float y = __shfl_up_sync(FULL, pm, o);
+            if (lane >= o) pm = fmaxf(pm, y);
         }
-        if (valid) {
+        const float before = __shfl_up_sync(FULL, pm, 1);
+        const float mx = lane == 0 ? M : fmaxf(M, before);
+        const bool vis = ok && t > mx;
+        if (vis) sum += 2 * dd + 1;
+        if (flags && ok && dd < cap) flags[dd] = vis ? 1 : 0;
+        if (cnt > 0) {
+            lastvis = __shfl_sync(FULL, vis ? 1 : 0, cnt - 1);
+            n = c + cnt;
+        }
+        M = fmaxf(M, __shfl_sync(FULL, pm, 31));
+        if (cnt < 32) break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+    // the last target only closes a segment: its own 2n + 1 is not counted
+    return n >= 1 ? 1 + sum - (lastvis ? 2 * n + 1 : 0) : 0;
+}
+
+// One CTA of 32 warps per (POV q, group of FP32_GROUP directions): warp
+// w = 4 kk + 2 v + s walks direction 8 g + kk, virtual POV v (hi / lo; DIRECT
+// uses v = 0 only), forward (s = 0) or backward (s = 1).  Warp 0 then forms
+// each direction's blend of its lines' measures and the group's FP32 sum in
+// direction order, stored as an exact partial.
+__global__ void __launch_bounds__(1024) points_kernel(PointsParams pp)
+{
+    __shared__ int cvs[32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int q = (int)(blockIdx.x / (unsigned)pp.ngroups), grp = (int)(blockIdx.x % (unsigned)pp.ngroups);
+    const bool direct = pp.mode == TVS_POINTS_DIRECT;
+    {
+        const int kk = w >> 2, v = (w >> 1) & 1, s = w & 1;
+        const PointLine L = point_line(pp, q, grp * FP32_GROUP + kk, v);
+        int cv = 0;
+        if (L.valid) {
             long long a;
             unsigned fr;
-            line_pos(d, direct, base, j0, j0, &a, &fr);
-            const float h = __fadd_rn(direct ? view_at(pp.dem, pp.cols, d, i, j0)
-                                             : sample_at(pp.dem, pp.cols, d, a, fr, j0), pp.h0);
-            const int dir = s ? -1 : 1;
-            // targets d = 1 .. n, n = min(usable samples, K); a target's 2d + 1 is
-            // committed once the next target exists (the last one only closes a segment)
-            int n = 0, pend = 0;
-            long long sum = 0;
-            float M = __int_as_float(0xff800000);
-            for (int dd = 1; dd <= d.K; ++dd) {
-                const int j = j0 + dir * dd;
-                line_pos(d, direct, base, j0, j, &a, &fr);
-                if (!usable(d, a, fr, j)) break;
-                sum += pend;
-                const float z = sample_at(pp.dem, pp.cols, d, a, fr, j);
-                const float t = __fmul_rn(__fsub_rn(z, h), __frcp_rn((float)dd));
-                pend = t > M ? 2 * dd + 1 : 0;
-                M = fmaxf(M, t);
-                n = dd;
-            }
-            cv = n >= 1 ? (int)(1 + sum) : 0;
+            line_pos(L.d, direct, L.base, L.j0, L.j0, &a, &fr);
+            const float h = __fadd_rn(direct ? view_at(pp.dem, pp.cols, L.d, L.i, L.j0)
+                                             : sample_at(pp.dem, pp.cols, L.d, a, fr, L.j0), pp.h0);
+            cv = walk_half_line(pp.dem, pp.cols, L.d, L.base, L.j0, direct, s ? -1 : 1, h, nullptr, 0, lane);
         }
+        if (lane == 0) cvs[w] = cv;
     }
+    __syncthreads();
+    if (w != 0) return;
+    const int kk = lane >> 2, v = (lane >> 1) & 1;
+    const int k = grp * FP32_GROUP + kk;
+    const PointLine L = point_line(pp, q, k, v);
     // cv_fwd + cv_bwd of each line, then the direction's blend (Kernel-3)
-    const int both = cv + __shfl_xor_sync(0xffffffffu, cv, 1);
+    const int both = cvs[lane] + cvs[lane ^ 1];
     const float T = (float)both;
     const float T_other = __shfl_xor_sync(0xffffffffu, T, 2);   // the other virtual POV of the direction
     float val = 0.f;
     if (lane % 4 == 0 && k < pp.n) {
-        if (direct || fr0 == 0u) val = T;
-        else if (hi_ok && lo_ok) val = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, r), T), __fmul_rn(r, T_other));
-        else if (hi_ok) val = T;
+        if (direct || L.fr0 == 0u) val = T;
+        else if (L.hi_ok && L.lo_ok) val = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, L.r), T), __fmul_rn(L.r, T_other));
+        else if (L.hi_ok) val = T;
         else val = T_other;
     }
-    const float term = (lane % 4 == 0 && k < pp.n) ? __fmul_rn(d.g, val) : 0.f;
+    const float term = (lane % 4 == 0 && k < pp.n) ? __fmul_rn(L.d.g, val) : 0.f;
     // FP32 sum of the group's terms in direction order, then one exact partial
     float acc = 0.f;
 #pragma unroll
@@ -220,10 +283,12 @@ struct MapParams {
     float h0;
 };
 
-__global__ void __launch_bounds__(64) map_flags_kernel(MapParams mp)
+// One warp per (POV, slot), walking the half-line as the points kernel does.
+__global__ void __launch_bounds__(256) map_flags_kernel(MapParams mp)
 {
-    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;   // (q, slot)
-    if (t >= (long long)mp.npov * 2 * mp.n) return;
+    const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // (q, slot)
+    const int lane = threadIdx.x & 31;
+    if (t >= (long long)mp.npov * 2 * mp.n) return;                                // warp-uniform
     const int q = (int)(t / (2 * mp.n)), slot = (int)(t % (2 * mp.n));
     const int k = slot % mp.n, dir = slot < mp.n ? 1 : -1;
     const DirDev d = mp.dirs[k];
@@ -235,20 +300,8 @@ __global__ void __launch_bounds__(64) map_flags_kernel(MapParams mp)
     case 2:  i = jD; j0 = d.W - 1 - iD; break;
     default: i = d.H - 1 - iD; j0 = jD; break;
     }
-    unsigned char* f = mp.flags + t * mp.cap;
     const float h = __fadd_rn(view_at(mp.dem, mp.cols, d, i, j0), mp.h0);
-    float M = __int_as_float(0xff800000);
-    for (int dd = 1; dd <= d.K && dd < mp.cap; ++dd) {
-        const int j = j0 + dir * dd;
-        long long a;
-        unsigned fr;
-        line_pos(d, true, i, j0, j, &a, &fr);
-        if (!usable(d, a, fr, j)) break;
-        const float z = sample_at(mp.dem, mp.cols, d, a, fr, j);
-        const float th = __fmul_rn(__fsub_rn(z, h), __frcp_rn((float)dd));
-        f[dd] = th > M ? 1 : 0;
-        M = fmaxf(M, th);
-    }
+    walk_half_line(mp.dem, mp.cols, d, i, j0, true, dir, h, mp.flags + t * mp.cap, mp.cap, lane);
 }
 
 // View coordinates of DEM cell (iD, jD) in direction d's view.
@@ -295,6 +348,54 @@ __global__ void map_raster_kernel(MapParams mp)
 }  // namespace tvs
 
 using namespace tvs;
+
+extern "C" int64_t tvs_count_point_evals(int rows, int cols, int n_sectors, double step_m, double max_range_m,
+                                         const int32_t* pov_ij, int npov, int mode)
+{
+    if (!pov_ij || npov < 1) return TVS_ERR_ARG;
+    if (mode != TVS_POINTS_SDEM && mode != TVS_POINTS_DIRECT) return TVS_ERR_ARG;
+    if (check_job(rows, cols, step_m, 0.0, n_sectors, max_range_m)) return TVS_ERR_ARG;
+    for (int q = 0; q < npov; ++q)
+        if (pov_ij[2 * q] < 0 || pov_ij[2 * q] >= rows || pov_ij[2 * q + 1] < 0 || pov_ij[2 * q + 1] >= cols)
+            return TVS_ERR_ARG;
+    int64_t total = 0;
+    for (int k = 0; k < n_sectors; ++k) {
+        HostDir d;
+        make_direction(n_sectors, k, rows, cols, step_m, max_range_m, &d);
+        const long long K = d.K == LLONG_MAX ? (long long)d.W : std::min<long long>(d.K, d.W);
+        for (int q = 0; q < npov; ++q) {
+            const int iD = pov_ij[2 * q], jD = pov_ij[2 * q + 1];
+            int i, j0;
+            switch (d.frame) {
+            case 0:  i = iD; j0 = jD; break;
+            case 1:  i = jD; j0 = iD; break;
+            case 2:  i = jD; j0 = d.W - 1 - iD; break;
+            default: i = d.H - 1 - iD; j0 = jD; break;
+            }
+            if (mode == TVS_POINTS_DIRECT) {
+                // 0 <= i + (j - j0) t <= H - 1 and 0 <= j < W, t = t_fx 2^-32
+                long long f = d.W - 1 - j0, b = j0;
+                if (d.t_fx != 0ull) {
+                    f = std::min<long long>(f, (long long)(((unsigned long long)(d.H - 1 - i) << 32) / d.t_fx));
+                    b = std::min<long long>(b, (long long)(((unsigned long long)i << 32) / d.t_fx));
+                }
+                total += std::min(f, K) + std::min(b, K);
+                continue;
+            }
+            const unsigned long long y = (unsigned long long)j0 * d.t_fx;
+            const int dest = (int)(y >> 32);
+            const bool frac = (y & 0xFFFFFFFFull) != 0ull;
+            for (int v = 0; v < 2; ++v) {
+                const bool ok = v == 0 ? (!frac || i <= d.H - 2) : (frac && i >= 1);
+                if (!ok) continue;
+                int lo, hi;
+                host_row_range(d, i - dest - v + d.D, &lo, &hi);
+                total += std::min<long long>(hi - j0, K) + std::min<long long>(j0 - lo, K);
+            }
+        }
+    }
+    return total;
+}
 
 extern "C" int tvs_visibility_map(tvs_handle h, const float* d_dem, int rows, int cols, double step_m,
                                   double obs_height_m, int n_sectors, double max_range_m, const int32_t* pov_ij,
@@ -344,7 +445,7 @@ extern "C" int tvs_visibility_map(tvs_handle h, const float* d_dem, int rows, in
     mp.rows = rows; mp.cols = cols; mp.n = n_sectors; mp.npov = npov; mp.cap = cap;
     mp.h0 = (float)obs_height_m;
     const long long walks = (long long)npov * 2 * n_sectors;
-    map_flags_kernel<<<(unsigned)((walks + 63) / 64), 64, 0, s>>>(mp);
+    map_flags_kernel<<<(unsigned)((walks * 32 + 255) / 256), 256, 0, s>>>(mp);
     TVS_CUDA(cudaGetLastError(), "visibility flags launch");
     const long long cells = (long long)rows * cols;
     map_raster_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(mp);
@@ -399,7 +500,7 @@ extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, i
     pp.scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
     pp.rows = rows; pp.cols = cols; pp.n = n_sectors; pp.ngroups = ngroups; pp.npov = npov; pp.mode = mode;
     pp.h0 = (float)obs_height_m;
-    points_kernel<<<(unsigned)(npov * ngroups), 32, 0, s>>>(pp);
+    points_kernel<<<(unsigned)(npov * ngroups), 1024, 0, s>>>(pp);
     TVS_CUDA(cudaGetLastError(), "points launch");
     points_finalize<<<(npov + 127) / 128, 128, 0, s>>>(pp);
     TVS_CUDA(cudaGetLastError(), "points finalize launch");

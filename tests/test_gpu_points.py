@@ -28,8 +28,12 @@ def _povs(rows, cols, count, seed):
     return np.concatenate([p, corners]).astype(np.int32)
 
 
+# walks of exactly 32 and 64 targets and around them (the warp walks 32
+# targets at a time): 2 x 65 and 33 x 64 strips, a range of exactly 32 steps
 @pytest.mark.parametrize("rows,cols,n,rng,h0", [(120, 90, 180, 0.0, 1.5), (64, 200, 36, 900.0, 10.0),
-                                                (3, 257, 16, 0.0, 1.0), (150, 150, 45, 0.0, 0.0)])
+                                                (3, 257, 16, 0.0, 1.0), (150, 150, 45, 0.0, 0.0),
+                                                (2, 65, 1, 0.0, 1.5), (33, 64, 4, 320.0, 2.0),
+                                                (97, 33, 8, 0.0, 3.0)])
 def test_sdem_points_equal_the_total_map(ctx, rows, cols, n, rng, h0):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.8, 600.0, seed=rows + cols)
@@ -42,7 +46,8 @@ def test_sdem_points_equal_the_total_map(ctx, rows, cols, n, rng, h0):
     assert np.array_equal(got.cpu().numpy(), want)
 
 
-@pytest.mark.parametrize("rows,cols,n,rng,h0", [(90, 70, 180, 0.0, 1.5), (60, 130, 24, 700.0, 8.0)])
+@pytest.mark.parametrize("rows,cols,n,rng,h0", [(90, 70, 180, 0.0, 1.5), (60, 130, 24, 700.0, 8.0),
+                                                (33, 64, 4, 320.0, 2.0), (2, 65, 1, 0.0, 1.5)])
 def test_direct_points_match_the_oracle_definition(ctx, orc, rows, cols, n, rng, h0):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.75, 500.0, seed=rows * cols)
@@ -106,7 +111,7 @@ def _ambiguous(rows, cols, n, povs, eps=1e-9):
 
 
 @pytest.mark.parametrize("rows,cols,n,rng,h0,npov", [(120, 90, 180, 0.0, 1.5, 3), (64, 200, 36, 900.0, 10.0, 5),
-                                                     (2000, 2000, 180, 0.0, 1.5, 2)])
+                                                     (2000, 2000, 180, 0.0, 1.5, 2), (33, 64, 4, 320.0, 2.0, 4)])
 def test_visibility_map_matches_the_oracle(ctx, orc, rows, cols, n, rng, h0, npov):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.8, 900.0 if rows < 1000 else 1500.0, seed=rows + n)

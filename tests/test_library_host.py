@@ -103,3 +103,48 @@ def test_terrain_generator_is_seeded_and_shaped():
     assert all(256 <= t["rows"] <= 1500 for t in tiles)
     reqs = terrain.request_stream(20)
     assert all(reqs[i]["arrival"] < reqs[i + 1]["arrival"] for i in range(19))
+
+
+def _walk_len(i, j0, dirn, H, W, t_fx, K, base, direct):
+    """Targets of one half-line, walked one by one with exact integers: the
+    sample at column j has row a = base + floor(y / 2^32) and fraction
+    y mod 2^32, y = j t_fx (SDEM, base row at column 0) or (j - j0) t_fx
+    (DIRECT, through the cell); it is usable iff 0 <= j < W, a >= 0 and
+    a <= H - 1 when the fraction is 0, a + 1 <= H - 1 otherwise."""
+    n = 0
+    for dd in range(1, K + 1):
+        j = j0 + dirn * dd
+        if not 0 <= j < W:
+            break
+        y = (j - j0 if direct else j) * t_fx
+        a, fr = base + (y >> 32), y & 0xFFFFFFFF
+        if a < 0 or (a > H - 1 if fr == 0 else a + 1 > H - 1):
+            break
+        n = dd
+    return n
+
+
+@pytest.mark.parametrize("rows,cols,n,step,rng", [(13, 29, 7, 10.0, 0.0), (40, 23, 16, 10.0, 120.0),
+                                                  (2, 9, 1, 1.0, 0.0), (17, 17, 180, 5.0, 0.0)])
+def test_point_eval_count_matches_brute_walks(orc, rows, cols, n, step, rng):
+    r = np.random.default_rng(rows * cols)
+    povs = np.concatenate([np.stack([r.integers(0, rows, 12), r.integers(0, cols, 12)], 1),
+                           [[0, 0], [rows - 1, cols - 1], [0, cols - 1], [rows - 1, 0]]]).astype(np.int32)
+    for mode in ("sdem", "direct"):
+        want = 0
+        for k in range(n):
+            d = orc.direction(n, k, rows, cols, step, rng)
+            H, W, t_fx, frame = d["H"], d["W"], d["t_fx"], d["frame"]
+            K = W if d["K"] < 0 or d["K"] > W else d["K"]
+            for iD, jD in povs.tolist():
+                i, j0 = [(iD, jD), (jD, iD), (jD, W - 1 - iD), (H - 1 - iD, jD)][frame]
+                if mode == "direct":
+                    want += sum(_walk_len(i, j0, s, H, W, t_fx, K, i, True) for s in (1, -1))
+                    continue
+                y0 = j0 * t_fx
+                frac = (y0 & 0xFFFFFFFF) != 0
+                for v, ok in ((0, not frac or i <= H - 2), (1, frac and i >= 1)):
+                    if ok:
+                        base = i - (y0 >> 32) - v
+                        want += sum(_walk_len(i, j0, s, H, W, t_fx, K, base, False) for s in (1, -1))
+        assert tvs.count_point_evals(rows, cols, n, povs, step, rng, mode) == want, mode
