@@ -721,8 +721,12 @@ def run_points_bench(args) -> int:
     peak_evals = props.multi_processor_count * FP32_LANES_PER_SM * sm_max_mhz * 1e6 / OPS_PER_EVAL
 
     def timed(fn):
+        """Median of the call (CUDA events around the API call on the stream,
+        so host work between the events counts) and the library's own
+        per-kernel CUDA events (kernel time per call)."""
         for _ in range(max(args.warmup, 3)):
             fn()
+        ctx.profile(True)
         ms = []
         for _ in range(args.steps):
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -731,20 +735,25 @@ def run_points_bench(args) -> int:
             b.record(stream)
             b.synchronize()
             ms.append(a.elapsed_time(b))
-        return statistics.median(ms)
+        st = ctx.profile_read()
+        ctx.profile(False)
+        kern = {k: v["total_ms"] / v["launches"] for k, v in st.items() if v["launches"]}
+        return statistics.median(ms), kern
 
-    times, evals = {}, {}
+    times, kms, evals = {}, {}, {}
     for name, povs in (("10", povs10), ("2000", povs_acc)):
         for mode in ("sdem", "direct"):
-            times[(name, mode)] = timed(lambda: ctx.viewshed_points(dem, w["step"], w["h0"], w["n"], 0.0, povs,
-                                                                    mode=mode))
+            times[(name, mode)], k = timed(lambda: ctx.viewshed_points(dem, w["step"], w["h0"], w["n"], 0.0, povs,
+                                                                       mode=mode))
+            kms[(name, mode)] = k["points"]
             evals[(name, mode)] = tvs.count_point_evals(w["rows"], w["cols"], w["n"], povs, w["step"], 0.0, mode)
-    map_ms = timed(lambda: ctx.visibility_map(dem, w["step"], w["h0"], w["n"], 0.0, povs10))
+    map_ms, map_k = timed(lambda: ctx.visibility_map(dem, w["step"], w["h0"], w["n"], 0.0, povs10))
 
     def rate(name, mode):
-        r = evals[(name, mode)] / (times[(name, mode)] / 1e3)
+        r = evals[(name, mode)] / (kms[(name, mode)] / 1e3)
         return {"povs": int(name), "ms": times[(name, mode)], "pov_per_s": int(name) / (times[(name, mode)] / 1e3),
-                "evals": evals[(name, mode)], "geval_per_s": r / 1e9, "frac_of_alu_roofline": r / peak_evals}
+                "kernel_ms": kms[(name, mode)], "evals": evals[(name, mode)], "geval_per_s": r / 1e9,
+                "frac_of_alu_roofline": r / peak_evals}
 
     disc = {}
     for h0 in (w["h0"], 10.0, 30.0):
@@ -769,11 +778,13 @@ def run_points_bench(args) -> int:
                        "povs": 10, "l2": "DEM (16 MB) L2-resident, as in use"},
             "roofline": {"bound": "alu", "achieved": r10["geval_per_s"], "peak": peak_evals / 1e9, "unit": UNIT,
                          "frac": r10["frac_of_alu_roofline"], "traffic": None, "kernel": "points",
-                         "note": "10 POVs are 3.6e6 evaluations in 7200 half-line walks of up to 2000 "
-                                 "dependent targets: latency-bound, not ALU-bound (see batch2000)"},
+                         "note": "kernel time (the library's CUDA events); 10 POVs are 6e6 evaluations in "
+                                 "7200 half-line walks of up to 2000 targets on 230 CTAs: latency-bound, "
+                                 "not ALU-bound (see batch2000)"},
             "sdem_10": r10, "direct_10": rate("10", "direct"),
             "batch2000": {"sdem": rate("2000", "sdem"), "direct": rate("2000", "direct")},
-            "visibility_map_10": {"ms": map_ms, "note": "flags of 3600 half-lines and the 4e6-cell raster"},
+            "visibility_map_10": {"ms": map_ms, "kernel_ms": map_k,
+                                  "note": "flags of 3600 half-lines and the 4e6-cell raster"},
             "discretisation": {"povs": int(len(povs_acc)), **disc,
                                "mean_neighbour_step_m": rough,
                                "note": "|sDEM - definition| per POV, relative to the POV's own area, to the "

@@ -69,7 +69,8 @@ typedef struct {
     int64_t  launches;
     double   total_ms;
     double   units;        /* algorithmic units summed over launches (see unit) */
-    char     unit[16];     /* "evals" for the sweep, "bytes" for the memory kernels */
+    char     unit[16];     /* "evals" for the sweep and the point walks, "bytes" for the
+                              memory kernels, "cells" (cell x POV pairs) for the map raster */
 } tvs_kernel_stats;
 
 /* ABI version of the loaded library (TVS_ABI_VERSION).  Host only. */

@@ -431,9 +431,9 @@ class Context:
         _check(self._lib.tvs_profile_enable(self.handle, 1 if on else 0))
 
     def profile_read(self) -> dict:
-        arr = (KernelStats * 8)()
+        arr = (KernelStats * 16)()
         cnt = C.c_int(0)
-        _check(self._lib.tvs_profile_read(self.handle, arr, 8, C.byref(cnt)))
+        _check(self._lib.tvs_profile_read(self.handle, arr, 16, C.byref(cnt)))
         return {arr[i].name.decode(): dict(launches=arr[i].launches, total_ms=arr[i].total_ms,
                                            units=arr[i].units, unit=arr[i].unit.decode())
                 for i in range(cnt.value)}

@@ -67,7 +67,7 @@ void job_work(int n, int rows, int cols, double step, double max_range, int k0, 
 int check_job(int rows, int cols, double step_m, double obs_height_m, int n_sectors, double max_range_m);
 
 // ------------------------------------------------------------ profiling --
-enum KernelId { K_ROWMAP = 0, K_SKEW, K_SWEEP, K_UNSKEW, K_FINAL, K_COUNT };
+enum KernelId { K_ROWMAP = 0, K_SKEW, K_SWEEP, K_UNSKEW, K_FINAL, K_POINTS, K_MAP_FLAGS, K_MAP_RASTER, K_COUNT };
 
 // Tunable launch choices (see tvs_tuning in tvs.h).
 struct Tuning {

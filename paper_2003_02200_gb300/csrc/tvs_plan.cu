@@ -33,8 +33,9 @@ namespace {
 
 constexpr double kTwo32 = 4294967296.0;
 
-const char* kKernelName[K_COUNT] = {"rowmap", "skew", "sweep", "unskew", "unskew_finalize"};
-const char* kKernelUnit[K_COUNT] = {"bytes", "bytes", "evals", "bytes", "bytes"};
+const char* kKernelName[K_COUNT] = {"rowmap", "skew", "sweep", "unskew", "unskew_finalize",
+                                   "points", "map_flags", "map_raster"};
+const char* kKernelUnit[K_COUNT] = {"bytes", "bytes", "evals", "bytes", "bytes", "evals", "evals", "cells"};
 
 long long sum_min(long long L, long long K)
 {

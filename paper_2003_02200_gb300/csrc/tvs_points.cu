@@ -154,53 +154,110 @@ __device__ __forceinline__ PointLine point_line(const PointsParams& pp, int q, i
     return L;
 }
 
-// One half-line walked by a whole warp, 32 targets at a time: lane l takes
-// target d = c + l + 1 of chunk c, its FP32 slope is the serial walk's, and
-// a warp max-scan gives every lane the running maximum of the targets before
-// it (maximum is exact, so every visibility decision is the serial one).
-// The walk ends at the first unusable target or at K.  Returns the walk's measure
+// Targets per lane per chunk of a warp's half-line walk.
+constexpr int WALK_TPL = 8;
+constexpr int WALK_CHUNK = 32 * WALK_TPL;
+
+// DEM offset of view cell (a, j) of a direction: o + a sa + j sj.
+struct ViewAddr {
+    int o, sa, sj;
+};
+
+__device__ __forceinline__ ViewAddr view_addr(const DirDev& d, int cols)
+{
+    switch (d.frame) {
+    case 0:  return {0, cols, 1};
+    case 1:  return {0, 1, cols};
+    case 2:  return {(d.W - 1) * cols, 1, -cols};
+    default: return {(d.H - 1) * cols, -cols, 1};
+    }
+}
+
+// Fills rtab[d] = rcp(d) for d = 1 .. dmax (the CTA's threads share it).
+__device__ __forceinline__ void fill_rcp(float* rtab, int dmax)
+{
+    for (int m = threadIdx.x + 1; m <= dmax; m += blockDim.x) rtab[m] = __frcp_rn((float)m);
+}
+
+// One half-line walked by a whole warp, WALK_CHUNK targets at a time: lane l
+// takes targets d = c + 8 l + 1 .. c + 8 l + 8 of chunk c (their samples are
+// independent loads), with each target's FP32 slope the serial walk's.  The
+// running maximum before a target is the maximum of the slopes before it:
+// a warp max-scan of the lanes' own maxima gives each lane the maximum before
+// its first target, and a serial pass over its 8 targets does the rest
+// (maximum is exact, so every visibility decision is the serial one).  The
+// walk ends at the first unusable target or at K.  Returns the walk's measure
 // cv = 1 + sum_{d < n} v_d (2d + 1) (0 for n = 0) on every lane; with `flags`
 // each target's visibility is also stored at flags[d] (d < cap).
-__device__ __forceinline__ int walk_half_line(const float* dem, int cols, const DirDev& d, long long base, int j0,
-                                              bool direct, int dir, float h, unsigned char* flags, int cap, int lane)
+__device__ __forceinline__ int walk_half_line(const float* __restrict__ dem, int cols, const DirDev& d,
+                                              const float* __restrict__ rtab, long long base, int j0, bool direct,
+                                              int dir, float h, unsigned char* flags, int cap, int lane)
 {
     const unsigned FULL = 0xffffffffu;
-    float M = __int_as_float(0xff800000);
-    int sum = 0;                      // this lane's sum of v_d (2d + 1) over every target it saw
+    const float NEG = __int_as_float(0xff800000);
+    const ViewAddr va = view_addr(d, cols);
+    float M = NEG;
+    int sum = 0;                      // this lane's sum of v_d (2d + 1) over its targets
     int n = 0, lastvis = 0;           // targets so far; visibility of the latest one
-    for (int c = 0;; c += 32) {
-        const int dd = c + lane + 1;
-        bool ok = dd <= d.K;
-        long long a = 0;
-        unsigned fr = 0u;
-        const int j = j0 + dir * dd;
-        if (ok) {
+    for (int c = 0;; c += WALK_CHUNK) {
+        float t[WALK_TPL];
+        int firstbad = WALK_TPL;      // the lane's first unusable target
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m) {
+            const int dd = c + WALK_TPL * lane + m + 1;
+            const int j = j0 + dir * dd;
+            long long a;
+            unsigned fr;
             line_pos(d, direct, base, j0, j, &a, &fr);
-            ok = usable(d, a, fr, j);
+            const bool ok = dd <= d.K && usable(d, a, fr, j);
+            t[m] = NEG;
+            if (ok) {
+                const int at = va.o + (int)a * va.sa + j * va.sj;
+                float z = dem[at];
+                if (fr != 0u) {
+                    const float r = __fmul_rn(__uint2float_rn(fr), 0x1p-32f);
+                    z = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, r), z), __fmul_rn(r, dem[at + va.sa]));
+                }
+                t[m] = __fmul_rn(__fsub_rn(z, h), rtab[dd]);
+            }
+            if (!ok && firstbad == WALK_TPL) firstbad = m;
         }
         // the walk ends at the first unusable target, as the serial walk does
-        const unsigned okm = __ballot_sync(FULL, ok);
-        const int cnt = okm == FULL ? 32 : __ffs(~okm) - 1;
-        ok = lane < cnt;
-        float t = __int_as_float(0xff800000);
-        if (ok) t = __fmul_rn(__fsub_rn(sample_at(dem, cols, d, a, fr, j), h), __frcp_rn((float)dd));
-        float pm = t;                 // inclusive prefix maximum of the chunk
+        const unsigned bad = __ballot_sync(FULL, firstbad < WALK_TPL);
+        const int badlane = bad ? __ffs(bad) - 1 : 32;
+        const int cnt = badlane == 32 ? WALK_CHUNK
+                                      : WALK_TPL * badlane + __shfl_sync(FULL, firstbad, badlane);
+        const int mine = min(max(cnt - WALK_TPL * lane, 0), WALK_TPL);
+        float lm = NEG;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m)
+            if (m < mine) lm = fmaxf(lm, t[m]);
+        float pm = lm;                // inclusive prefix maximum over the lanes
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const float y = __shfl_up_sync(FULL, pm, o);
             if (lane >= o) pm = fmaxf(pm, y);
         }
         const float before = __shfl_up_sync(FULL, pm, 1);
-        const float mx = lane == 0 ? M : fmaxf(M, before);
-        const bool vis = ok && t > mx;
-        if (vis) sum += 2 * dd + 1;
-        if (flags && ok && dd < cap) flags[dd] = vis ? 1 : 0;
+        float run = lane == 0 ? M : fmaxf(M, before);
+        unsigned vbits = 0u;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m) {
+            if (m < mine) {
+                const int dd = c + WALK_TPL * lane + m + 1;
+                const bool vis = t[m] > run;
+                run = fmaxf(run, t[m]);
+                if (vis) { sum += 2 * dd + 1; vbits |= 1u << m; }
+                if (flags && dd < cap) flags[dd] = vis ? 1 : 0;
+            }
+        }
         if (cnt > 0) {
-            lastvis = __shfl_sync(FULL, vis ? 1 : 0, cnt - 1);
+            const int last = cnt - 1;
+            lastvis = (__shfl_sync(FULL, vbits, last / WALK_TPL) >> (last % WALK_TPL)) & 1u;
             n = c + cnt;
         }
         M = fmaxf(M, __shfl_sync(FULL, pm, 31));
-        if (cnt < 32) break;
+        if (cnt < WALK_CHUNK) break;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
@@ -216,6 +273,9 @@ __device__ __forceinline__ int walk_half_line(const float* dem, int cols, const 
 __global__ void __launch_bounds__(1024) points_kernel(PointsParams pp)
 {
     __shared__ int cvs[32];
+    extern __shared__ float rtab[];   // rcp(d), d = 1 .. max(rows, cols)
+    fill_rcp(rtab, max(pp.rows, pp.cols));
+    __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const int q = (int)(blockIdx.x / (unsigned)pp.ngroups), grp = (int)(blockIdx.x % (unsigned)pp.ngroups);
     const bool direct = pp.mode == TVS_POINTS_DIRECT;
@@ -229,7 +289,7 @@ __global__ void __launch_bounds__(1024) points_kernel(PointsParams pp)
             line_pos(L.d, direct, L.base, L.j0, L.j0, &a, &fr);
             const float h = __fadd_rn(direct ? view_at(pp.dem, pp.cols, L.d, L.i, L.j0)
                                              : sample_at(pp.dem, pp.cols, L.d, a, fr, L.j0), pp.h0);
-            cv = walk_half_line(pp.dem, pp.cols, L.d, L.base, L.j0, direct, s ? -1 : 1, h, nullptr, 0, lane);
+            cv = walk_half_line(pp.dem, pp.cols, L.d, rtab, L.base, L.j0, direct, s ? -1 : 1, h, nullptr, 0, lane);
         }
         if (lane == 0) cvs[w] = cv;
     }
@@ -286,6 +346,9 @@ struct MapParams {
 // One warp per (POV, slot), walking the half-line as the points kernel does.
 __global__ void __launch_bounds__(256) map_flags_kernel(MapParams mp)
 {
+    extern __shared__ float rtab[];   // rcp(d), d = 1 .. max(rows, cols)
+    fill_rcp(rtab, max(mp.rows, mp.cols));
+    __syncthreads();
     const long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;   // (q, slot)
     const int lane = threadIdx.x & 31;
     if (t >= (long long)mp.npov * 2 * mp.n) return;                                // warp-uniform
@@ -301,7 +364,7 @@ __global__ void __launch_bounds__(256) map_flags_kernel(MapParams mp)
     default: i = d.H - 1 - iD; j0 = jD; break;
     }
     const float h = __fadd_rn(view_at(mp.dem, mp.cols, d, i, j0), mp.h0);
-    walk_half_line(mp.dem, mp.cols, d, i, j0, true, dir, h, mp.flags + t * mp.cap, mp.cap, lane);
+    walk_half_line(mp.dem, mp.cols, d, rtab, i, j0, true, dir, h, mp.flags + t * mp.cap, mp.cap, lane);
 }
 
 // View coordinates of DEM cell (iD, jD) in direction d's view.
@@ -316,19 +379,35 @@ __device__ __forceinline__ void to_view(const DirDev& d, int iD, int jD, int* i,
 }
 
 // One thread per cell: the sector of each POV it falls in (nearest of the 2n
-// half-line axes k' pi / n, from a double-precision angle) and the flag of
-// the target at the cell's walk-axis column.
+// half-line axes k' pi / n to the direction of the cell, the double-precision
+// decision kp = floor(atan2(di, dj) n / pi + 1/2) mod 2n) and the flag of the
+// target at the cell's walk-axis column.  The decision is taken from a
+// single-precision angle when it is far from a sector boundary: atan2f is
+// within a few ulp of the angle (|angle| <= pi, ulp 2^-22), so with the three
+// roundings of q = angle (n / pi) + 1/2 the single-precision q is within
+// about 4.1e-7 n of the double one; a cell whose q lies within
+// 4e-6 n + 1e-6 of a boundary takes the double-precision angle instead.
 __global__ void map_raster_kernel(MapParams mp)
 {
     const long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= (long long)mp.rows * mp.cols) return;
     const int iD = (int)(c / mp.cols), jD = (int)(c % mp.cols);
+    const float scale = (float)((double)mp.n / 3.141592653589793);
+    const float margin = 4e-6f * (float)mp.n + 1e-6f;
     int seen = 0;
     for (int q = 0; q < mp.npov; ++q) {
         const int i0 = mp.pov[2 * q], j0 = mp.pov[2 * q + 1];
         if (iD == i0 && jD == j0) { ++seen; continue; }
-        const double qq = atan2((double)(iD - i0), (double)(jD - j0)) * (double)mp.n / 3.141592653589793;
-        long long kp = (long long)floor(qq + 0.5);
+        const float x = __fadd_rn(__fmul_rn(atan2f((float)(iD - i0), (float)(jD - j0)), scale), 0.5f);
+        const float fl = floorf(x);
+        const float fx = x - fl;                  // exact
+        long long kp;
+        if (fx > margin && fx < 1.0f - margin) {
+            kp = (long long)fl;
+        } else {
+            const double qq = atan2((double)(iD - i0), (double)(jD - j0)) * (double)mp.n / 3.141592653589793;
+            kp = (long long)floor(qq + 0.5);
+        }
         kp = ((kp % (2 * mp.n)) + 2 * mp.n) % (2 * mp.n);
         const int k = (int)(kp % mp.n);
         const DirDev d = mp.dirs[k];
@@ -445,10 +524,22 @@ extern "C" int tvs_visibility_map(tvs_handle h, const float* d_dem, int rows, in
     mp.rows = rows; mp.cols = cols; mp.n = n_sectors; mp.npov = npov; mp.cap = cap;
     mp.h0 = (float)obs_height_m;
     const long long walks = (long long)npov * 2 * n_sectors;
-    map_flags_kernel<<<(unsigned)((walks * 32 + 255) / 256), 256, 0, s>>>(mp);
+    const size_t rtab_bytes = ((size_t)std::max(rows, cols) + 1) * sizeof(float);
+    TVS_CUDA(cudaFuncSetAttribute(map_flags_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rtab_bytes),
+             "visibility flags shared memory");
+    {
+        const double evals = h->profiling ? (double)tvs_count_point_evals(rows, cols, n_sectors, step_m, max_range_m,
+                                                                          pov_ij, npov, TVS_POINTS_DIRECT)
+                                          : 0.0;
+        Timer t(h, K_MAP_FLAGS, s, evals);
+        map_flags_kernel<<<(unsigned)((walks * 32 + 255) / 256), 256, rtab_bytes, s>>>(mp);
+    }
     TVS_CUDA(cudaGetLastError(), "visibility flags launch");
     const long long cells = (long long)rows * cols;
-    map_raster_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(mp);
+    {
+        Timer t(h, K_MAP_RASTER, s, (double)cells * npov);
+        map_raster_kernel<<<(unsigned)((cells + 255) / 256), 256, 0, s>>>(mp);
+    }
     TVS_CUDA(cudaGetLastError(), "visibility raster launch");
     return TVS_OK;
 }
@@ -500,9 +591,17 @@ extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, i
     pp.scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
     pp.rows = rows; pp.cols = cols; pp.n = n_sectors; pp.ngroups = ngroups; pp.npov = npov; pp.mode = mode;
     pp.h0 = (float)obs_height_m;
-    points_kernel<<<(unsigned)(npov * ngroups), 1024, 0, s>>>(pp);
+    const size_t rtab_bytes = ((size_t)std::max(rows, cols) + 1) * sizeof(float);
+    TVS_CUDA(cudaFuncSetAttribute(points_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rtab_bytes),
+             "points shared memory");
+    {
+        const double evals = h->profiling ? (double)tvs_count_point_evals(rows, cols, n_sectors, step_m, max_range_m,
+                                                                          pov_ij, npov, mode)
+                                          : 0.0;
+        Timer t(h, K_POINTS, s, evals);
+        points_kernel<<<(unsigned)(npov * ngroups), 1024, rtab_bytes, s>>>(pp);
+        points_finalize<<<(npov + 127) / 128, 128, 0, s>>>(pp);
+    }
     TVS_CUDA(cudaGetLastError(), "points launch");
-    points_finalize<<<(npov + 127) / 128, 128, 0, s>>>(pp);
-    TVS_CUDA(cudaGetLastError(), "points finalize launch");
     return TVS_OK;
 }

@@ -111,7 +111,8 @@ def _ambiguous(rows, cols, n, povs, eps=1e-9):
 
 
 @pytest.mark.parametrize("rows,cols,n,rng,h0,npov", [(120, 90, 180, 0.0, 1.5, 3), (64, 200, 36, 900.0, 10.0, 5),
-                                                     (2000, 2000, 180, 0.0, 1.5, 2), (33, 64, 4, 320.0, 2.0, 4)])
+                                                     (2000, 2000, 180, 0.0, 1.5, 2), (33, 64, 4, 320.0, 2.0, 4),
+                                                     (150, 170, 1000, 0.0, 5.0, 3), (41, 37, 12, 0.0, 1.5, 6)])
 def test_visibility_map_matches_the_oracle(ctx, orc, rows, cols, n, rng, h0, npov):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.8, 900.0 if rows < 1000 else 1500.0, seed=rows + n)
@@ -131,3 +132,19 @@ def test_visibility_map_refuses_bad_arguments(ctx):
     with pytest.raises(tvs.TvsError) as ei:
         ctx.visibility_map(d, 10.0, 1.5, 8, 0.0, [[0, 12]])
     assert ei.value.code == TVS_ERR_ARG
+
+
+def test_profiling_counts_point_and_map_work(ctx):
+    import torch
+    dem = terrain.fractal_dem(70, 90, 0.8, 500.0, seed=12)
+    d = torch.from_numpy(dem).cuda()
+    povs = _povs(70, 90, 7, seed=12)
+    ctx.profile(True)
+    ctx.viewshed_points(d, 10.0, 1.5, 24, 400.0, povs, mode="sdem")
+    ctx.visibility_map(d, 10.0, 1.5, 24, 400.0, povs)
+    st = ctx.profile_read()
+    ctx.profile(False)
+    assert st["points"]["launches"] == 1 and st["points"]["total_ms"] > 0
+    assert st["points"]["units"] == tvs.count_point_evals(70, 90, 24, povs, 10.0, 400.0, "sdem")
+    assert st["map_flags"]["units"] == tvs.count_point_evals(70, 90, 24, povs, 10.0, 400.0, "direct")
+    assert st["map_raster"]["units"] == 70 * 90 * len(povs)
