@@ -59,7 +59,7 @@ def parse_args(argv=None):
                     help="device scratch budget of the library handle (0 = library default)")
     ap.add_argument("--requests", type=int, default=240, help="serve: requests in the arrival stream")
     ap.add_argument("--rate", type=float, default=20.0, help="serve: nominal Poisson arrival rate (req/s)")
-    ap.add_argument("--rate-factors", default="1,1.5,2,2.25",
+    ap.add_argument("--rate-factors", default="0.75,1,1.5,2,2.25",
                     help="serve: offered rates swept, as multiples of --rate")
     ap.add_argument("--step-evals", default="0", help="serve: evaluations per server step, a comma list (0 = default)")
     ap.add_argument("--policies", default="fifo,deadline", help="serve: server scheduling policies to run")
