@@ -224,7 +224,7 @@ constexpr int FLUSH_STEPS = 336;   // a multiple of SMALL_UNROLL and LARGE_UNROL
 // Suffix maxima of a staged row are kept at every ZS_STRIDE-th sample; pruning
 // checks every PRUNE_EVERY blocks.
 constexpr int ZS_STRIDE = 4;
-constexpr int PRUNE_EVERY = 2;
+constexpr int PRUNE_EVERY = 1;
 
 // A warp item is one skewed row and one walk direction.  Its G groups of P
 // consecutive POVs are taken in order (longest walks first) from a warp-local
@@ -252,6 +252,9 @@ __device__ __forceinline__ void sweep_row(const float* __restrict__ F, const flo
                                           const float4* __restrict__ tab, int* __restrict__ cvrow,
                                           int* __restrict__ spill, int L, int K, float h0, bool rev, int lane)
 {
+    // the window is read as float4 from F + ROW_PADL + x0 + e (x0 = g P, e a
+    // multiple of U): both must keep it 16-byte aligned
+    static_assert(P % 4 == 0 && U % 4 == 0, "window loads must stay 16-byte aligned");
     const unsigned FULL = 0xffffffffu;
     const unsigned below = (1u << lane) - 1u;
     const float NEG = neg_inf();
