@@ -191,13 +191,23 @@ __device__ __forceinline__ float fset_gt(float a, float b)
 // POVs share one packed multiply and one packed accumulate; the comparison and
 // the maximum are scalar.  tab[e + u] holds (1/d, 1/d, 2d + 1, 2d + 1); a
 // range-limited walk's last block counts only its first `nvalid` steps.
-template <int P, int U, bool MASKED>
-__device__ __forceinline__ void sweep_block(const float* w, const float4* __restrict__ tab, const float* h,
+// Distance entry (1/d, 1/d, 2d + 1, 2d + 1) as the table holds it.
+__device__ __forceinline__ float4 dist_entry(int d)
+{
+    const float r = __frcp_rn((float)d);
+    const float c = (float)(2 * d + 1);
+    return make_float4(r, r, c, c);
+}
+
+// With FAR the block's entries are computed (distances e + 1 .. e + U, past
+// the end of a capped table) instead of read from tab[0 .. U).
+template <int P, int U, bool MASKED, bool FAR>
+__device__ __forceinline__ void sweep_block(const float* w, const float4* __restrict__ tab, int e, const float* h,
                                             float* M, float2* acc2, int nvalid)
 {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-        const float4 t4 = tab[u];
+        const float4 t4 = FAR ? dist_entry(e + u + 1) : tab[u];
         const float2 iv = make_float2(t4.x, t4.y);
         float2 cpair = make_float2(t4.z, t4.w);
         if (MASKED && u >= nvalid) cpair = make_float2(0.f, 0.f);
@@ -249,7 +259,7 @@ constexpr int PRUNE_EVERY = 1;
 // With LONG, `spill` is the lane's column (stride 32) of P integers.
 template <int P, int U, bool LONG, bool PRUNE>
 __device__ __forceinline__ void sweep_row(const float* __restrict__ F, const float* __restrict__ ZS,
-                                          const float4* __restrict__ tab, int* __restrict__ cvrow,
+                                          const float4* __restrict__ tab, int tabn, int* __restrict__ cvrow,
                                           int* __restrict__ spill, int L, int K, float h0, bool rev, int lane)
 {
     // the window is read as float4 from F + ROW_PADL + x0 + e (x0 = g P, e a
@@ -327,7 +337,8 @@ __device__ __forceinline__ void sweep_row(const float* __restrict__ F, const flo
             if (PRUNE && --pc < 0) {
                 pc = PRUNE_EVERY - 1;
                 const float A = __fsub_rn(ZS[(x0 + e + 1) / ZS_STRIDE], hmin);
-                const float B = A >= 0.f ? __fmul_rn(A, tab[e].x) : 0.f;
+                const float rd = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tab[e].x;
+                const float B = A >= 0.f ? __fmul_rn(A, rd) : 0.f;
                 float m = M[0];
 #pragma unroll
                 for (int q = 1; q < P; ++q) m = fminf(m, M[q]);
@@ -340,10 +351,15 @@ __device__ __forceinline__ void sweep_row(const float* __restrict__ F, const flo
                 const float4 v = *reinterpret_cast<const float4*>(base + m);
                 w[m] = v.x; w[m + 1] = v.y; w[m + 2] = v.z; w[m + 3] = v.w;
             }
-            if (klimited && e + U > dlim)
-                sweep_block<P, U, true>(w, tab + e, h, M, acc2, dlim - e);
-            else
-                sweep_block<P, U, false>(w, tab + e, h, M, acc2, U);
+            // long walks may run past a capped distance table (LONG only)
+            const bool far = LONG && e + U > tabn;
+            if (klimited && e + U > dlim) {
+                if (far) sweep_block<P, U, true, true>(w, tab, e, h, M, acc2, dlim - e);
+                else sweep_block<P, U, true, false>(w, tab + e, e, h, M, acc2, dlim - e);
+            } else {
+                if (far) sweep_block<P, U, false, true>(w, tab, e, h, M, acc2, U);
+                else sweep_block<P, U, false, false>(w, tab + e, e, h, M, acc2, U);
+            }
             e += U;
         }
     }
@@ -419,12 +435,14 @@ __device__ __forceinline__ void prefetch_row_l2(const float* p, int n)
 
 template <bool LONG, bool PRUNE>
 __device__ __forceinline__ void sweep_item(const ItemRow& it, const float* F, const float* ZS, const float4* tab,
-                                           int* cvrow, int* spill, int lane)
+                                           int tabn, int* cvrow, int* spill, int lane)
 {
     if (it.pov == SMALL_POV)
-        sweep_row<SMALL_POV, SMALL_UNROLL, LONG, PRUNE>(F, ZS, tab, cvrow, spill, it.L, it.K, it.h0, it.rev, lane);
+        sweep_row<SMALL_POV, SMALL_UNROLL, LONG, PRUNE>(F, ZS, tab, tabn, cvrow, spill, it.L, it.K, it.h0, it.rev,
+                                                       lane);
     else
-        sweep_row<LARGE_POV, LARGE_UNROLL, LONG, PRUNE>(F, ZS, tab, cvrow, spill, it.L, it.K, it.h0, it.rev, lane);
+        sweep_row<LARGE_POV, LARGE_UNROLL, LONG, PRUNE>(F, ZS, tab, tabn, cvrow, spill, it.L, it.K, it.h0, it.rev,
+                                                       lane);
 }
 
 // PRUNE: exact horizon pruning; LONG: the launch holds rows with walks of
@@ -496,7 +514,7 @@ __global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepPar
             __syncwarp();
         }
         int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
-        sweep_item<LONG, PRUNE>(it, F, ZS, tab, cvrow, spill, lane);
+        sweep_item<LONG, PRUNE>(it, F, ZS, tab, sp.inv_len, cvrow, spill, lane);
     }
 }
 
@@ -768,6 +786,11 @@ cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, in
     return cudaGetLastError();
 }
 
+// A long-walk launch keeps at least this many warps per CTA, shrinking the
+// distance table (to no fewer than MIN_TABLE entries) when both do not fit.
+constexpr int LONG_MIN_WARPS = 2;
+constexpr int MIN_TABLE = 1024;
+
 cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
                          const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
                          int wmax, int dmax, int prune, unsigned* counter, int num_sms, int smem_optin,
@@ -789,8 +812,21 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir
     sp.per_warp = sp.half + sp.zs_len + (longw ? 32 * LARGE_POV : 0);
     void (*kern)(SweepParams) = prune ? (longw ? sweep_kernel<true, true> : sweep_kernel<true, false>)
                                       : (longw ? sweep_kernel<false, true> : sweep_kernel<false, false>);
-    const size_t fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
     const size_t per_warp = (size_t)sp.per_warp * 4;
+    size_t fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
+    if (longw && fixed + (size_t)LONG_MIN_WARPS * per_warp > (size_t)smem_optin) {
+        // Rows of more than about 10^4 samples: the whole table and several
+        // staged rows do not fit together.  Keep LONG_MIN_WARPS warps (or as
+        // many as fit) and a table of what is left (at least MIN_TABLE
+        // entries); the long-walk sweep computes the entries past its end.
+        const size_t base = (size_t)sp.istart_len * 4;
+        int w = LONG_MIN_WARPS;
+        while (w > 1 && base + (size_t)MIN_TABLE * 16 + (size_t)w * per_warp > (size_t)smem_optin) --w;
+        if (base + (size_t)w * per_warp >= (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+        const size_t room = ((size_t)smem_optin - base - (size_t)w * per_warp) / 16;
+        sp.inv_len = (int)std::min<size_t>((size_t)sp.inv_len, room) & ~1;
+        fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
+    }
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
     // As many resident warps as shared memory and registers allow, in one CTA per SM
     // (each warp stages its own row; the 1/d table is shared by the CTA).

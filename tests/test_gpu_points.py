@@ -28,12 +28,13 @@ def _povs(rows, cols, count, seed):
     return np.concatenate([p, corners]).astype(np.int32)
 
 
-# walks of exactly 32 and 64 targets and around them (the warp walks 32
-# targets at a time): 2 x 65 and 33 x 64 strips, a range of exactly 32 steps
+# walks around multiples of the warp walk's chunk: 2 x 65 and 33 x 64 strips,
+# a range of exactly 32 steps; and the longest rows (16384 samples: a 64 KB
+# table of 1/d in shared memory)
 @pytest.mark.parametrize("rows,cols,n,rng,h0", [(120, 90, 180, 0.0, 1.5), (64, 200, 36, 900.0, 10.0),
                                                 (3, 257, 16, 0.0, 1.0), (150, 150, 45, 0.0, 0.0),
                                                 (2, 65, 1, 0.0, 1.5), (33, 64, 4, 320.0, 2.0),
-                                                (97, 33, 8, 0.0, 3.0)])
+                                                (97, 33, 8, 0.0, 3.0), (3, 16384, 4, 0.0, 1.5)])
 def test_sdem_points_equal_the_total_map(ctx, rows, cols, n, rng, h0):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.8, 600.0, seed=rows + cols)
@@ -112,7 +113,8 @@ def _ambiguous(rows, cols, n, povs, eps=1e-9):
 
 @pytest.mark.parametrize("rows,cols,n,rng,h0,npov", [(120, 90, 180, 0.0, 1.5, 3), (64, 200, 36, 900.0, 10.0, 5),
                                                      (2000, 2000, 180, 0.0, 1.5, 2), (33, 64, 4, 320.0, 2.0, 4),
-                                                     (150, 170, 1000, 0.0, 5.0, 3), (41, 37, 12, 0.0, 1.5, 6)])
+                                                     (150, 170, 1000, 0.0, 5.0, 3), (41, 37, 12, 0.0, 1.5, 6),
+                                                     (3, 16384, 4, 0.0, 1.5, 3)])
 def test_visibility_map_matches_the_oracle(ctx, orc, rows, cols, n, rng, h0, npov):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.8, 900.0 if rows < 1000 else 1500.0, seed=rows + n)
