@@ -44,6 +44,7 @@ struct PointsParams {
     const float* dem;
     const DirDev* dirs;     // the job's n directions (t_fx, frame, H, W, K, g)
     const int* pov;         // npov (row, col) pairs of DEM cells
+    float* term;            // npov x n direction terms g * blend(cv)
     __int128* part;         // npov x ngroups exact group sums
     float* area;            // npov visible areas
     double scale;           // (pi / (2n)) step^2
@@ -202,13 +203,17 @@ __device__ __forceinline__ int walk_half_line(const float* __restrict__ dem, int
     for (int c = 0;; c += WALK_CHUNK) {
         float t[WALK_TPL];
         int firstbad = WALK_TPL;      // the lane's first unusable target
+        // the lane's first target and its line position y = (j, or j - j0) t_fx,
+        // stepped by +-t_fx from target to target: row base + floor(y / 2^32)
+        const int d0 = c + WALK_TPL * lane + 1;
+        int j = j0 + dir * d0;
+        long long y = (long long)(direct ? dir * d0 : j) * (long long)d.t_fx;
+        const long long ystep = dir * (long long)d.t_fx;
 #pragma unroll
         for (int m = 0; m < WALK_TPL; ++m) {
-            const int dd = c + WALK_TPL * lane + m + 1;
-            const int j = j0 + dir * dd;
-            long long a;
-            unsigned fr;
-            line_pos(d, direct, base, j0, j, &a, &fr);
+            const int dd = d0 + m;
+            const long long a = base + (y >> 32);
+            const unsigned fr = (unsigned)y;
             const bool ok = dd <= d.K && usable(d, a, fr, j);
             t[m] = NEG;
             if (ok) {
@@ -221,6 +226,8 @@ __device__ __forceinline__ int walk_half_line(const float* __restrict__ dem, int
                 t[m] = __fmul_rn(__fsub_rn(z, h), rtab[dd]);
             }
             if (!ok && firstbad == WALK_TPL) firstbad = m;
+            y += ystep;
+            j += dir;
         }
         // the walk ends at the first unusable target, as the serial walk does
         const unsigned bad = __ballot_sync(FULL, firstbad < WALK_TPL);
@@ -265,23 +272,28 @@ __device__ __forceinline__ int walk_half_line(const float* __restrict__ dem, int
     return n >= 1 ? 1 + sum - (lastvis ? 2 * n + 1 : 0) : 0;
 }
 
-// One CTA of 32 warps per (POV q, group of FP32_GROUP directions): warp
-// w = 4 kk + 2 v + s walks direction 8 g + kk, virtual POV v (hi / lo; DIRECT
-// uses v = 0 only), forward (s = 0) or backward (s = 1).  Warp 0 then forms
-// each direction's blend of its lines' measures and the group's FP32 sum in
-// direction order, stored as an exact partial.
-__global__ void __launch_bounds__(1024) points_kernel(PointsParams pp)
+// Directions per CTA of the points kernel (4 warps each: 2 lines x 2 sides).
+constexpr int POINTS_DIRS = 2;
+
+// One CTA of 4 POINTS_DIRS warps per (POV q, POINTS_DIRS consecutive
+// directions): warp 4 kk + 2 v + s walks direction k0 + kk, virtual POV v
+// (hi / lo; DIRECT uses v = 0 only), forward (s = 0) or backward (s = 1).
+// Then one thread per direction blends its lines' measures (Kernel-3) and
+// stores the direction's term g * blend.
+__global__ void __launch_bounds__(128 * POINTS_DIRS) points_kernel(PointsParams pp)
 {
-    __shared__ int cvs[32];
+    __shared__ int cvs[4 * POINTS_DIRS];
     extern __shared__ float rtab[];   // rcp(d), d = 1 .. max(rows, cols)
     fill_rcp(rtab, max(pp.rows, pp.cols));
     __syncthreads();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-    const int q = (int)(blockIdx.x / (unsigned)pp.ngroups), grp = (int)(blockIdx.x % (unsigned)pp.ngroups);
+    const int per_pov = (pp.n + POINTS_DIRS - 1) / POINTS_DIRS;
+    const int q = (int)(blockIdx.x / (unsigned)per_pov);
+    const int k0 = (int)(blockIdx.x % (unsigned)per_pov) * POINTS_DIRS;
     const bool direct = pp.mode == TVS_POINTS_DIRECT;
     {
         const int kk = w >> 2, v = (w >> 1) & 1, s = w & 1;
-        const PointLine L = point_line(pp, q, grp * FP32_GROUP + kk, v);
+        const PointLine L = point_line(pp, q, k0 + kk, v);
         int cv = 0;
         if (L.valid) {
             long long a;
@@ -294,30 +306,33 @@ __global__ void __launch_bounds__(1024) points_kernel(PointsParams pp)
         if (lane == 0) cvs[w] = cv;
     }
     __syncthreads();
-    if (w != 0) return;
-    const int kk = lane >> 2, v = (lane >> 1) & 1;
-    const int k = grp * FP32_GROUP + kk;
-    const PointLine L = point_line(pp, q, k, v);
+    if (threadIdx.x >= POINTS_DIRS) return;
+    const int kk = threadIdx.x, k = k0 + kk;
+    if (k >= pp.n) return;
     // cv_fwd + cv_bwd of each line, then the direction's blend (Kernel-3)
-    const int both = cvs[lane] + cvs[lane ^ 1];
-    const float T = (float)both;
-    const float T_other = __shfl_xor_sync(0xffffffffu, T, 2);   // the other virtual POV of the direction
-    float val = 0.f;
-    if (lane % 4 == 0 && k < pp.n) {
-        if (direct || L.fr0 == 0u) val = T;
-        else if (L.hi_ok && L.lo_ok) val = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, L.r), T), __fmul_rn(L.r, T_other));
-        else if (L.hi_ok) val = T;
-        else val = T_other;
-    }
-    const float term = (lane % 4 == 0 && k < pp.n) ? __fmul_rn(L.d.g, val) : 0.f;
-    // FP32 sum of the group's terms in direction order, then one exact partial
+    const PointLine L = point_line(pp, q, k, 0);
+    const float T = (float)(cvs[4 * kk] + cvs[4 * kk + 1]);             // hi line
+    const float T_other = (float)(cvs[4 * kk + 2] + cvs[4 * kk + 3]);   // lo line
+    float val;
+    if (direct || L.fr0 == 0u) val = T;
+    else if (L.hi_ok && L.lo_ok) val = __fadd_rn(__fmul_rn(__fsub_rn(1.0f, L.r), T), __fmul_rn(L.r, T_other));
+    else if (L.hi_ok) val = T;
+    else val = T_other;
+    pp.term[(long long)q * pp.n + k] = __fmul_rn(L.d.g, val);
+}
+
+// One thread per (POV, group of FP32_GROUP directions): the FP32 sum of the
+// group's terms in direction order, stored as one exact partial (the total
+// viewshed map's unskew adds its groups the same way).
+__global__ void points_groups(PointsParams pp)
+{
+    const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= (long long)pp.npov * pp.ngroups) return;
+    const int q = (int)(t / pp.ngroups), grp = (int)(t % pp.ngroups);
+    const float* term = pp.term + (long long)q * pp.n;
     float acc = 0.f;
-#pragma unroll
-    for (int m = 0; m < FP32_GROUP; ++m) {
-        const float tm = __shfl_sync(0xffffffffu, term, 4 * m);
-        if (grp * FP32_GROUP + m < pp.n) acc = __fadd_rn(acc, tm);
-    }
-    if (lane == 0) pp.part[(long long)q * pp.ngroups + grp] = acc_of(acc);
+    for (int k = grp * FP32_GROUP; k < min(pp.n, (grp + 1) * FP32_GROUP); ++k) acc = __fadd_rn(acc, term[k]);
+    pp.part[t] = acc_of(acc);
 }
 
 __global__ void points_finalize(PointsParams pp)
@@ -558,7 +573,7 @@ extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, i
         if (pov_ij[2 * q] < 0 || pov_ij[2 * q] >= rows || pov_ij[2 * q + 1] < 0 || pov_ij[2 * q + 1] >= cols)
             return fail(TVS_ERR_ARG, "POV " + std::to_string(q) + " lies outside the DEM");
     const int ngroups = (n_sectors + FP32_GROUP - 1) / FP32_GROUP;
-    if ((long long)npov * ngroups >= (1LL << 31)) return fail(TVS_ERR_ARG, "too many POVs x directions");
+    if ((long long)npov * n_sectors >= (1LL << 31)) return fail(TVS_ERR_ARG, "too many POVs x directions");
     DeviceGuard g(h->device);
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
     std::vector<DirDev> dirs(n_sectors);
@@ -574,7 +589,8 @@ extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, i
     const size_t o_dirs = 0, o_pov = align256((size_t)n_sectors * sizeof(DirDev));
     const size_t hdr = o_pov + align256((size_t)npov * 8);
     const size_t o_part = hdr;
-    const size_t total = o_part + align256((size_t)npov * ngroups * 16);
+    const size_t o_term = o_part + align256((size_t)npov * ngroups * 16);
+    const size_t total = o_term + align256((size_t)npov * n_sectors * 4);
     rc = ensure_scratch(h, total);
     if (rc) return rc;
     std::vector<char> img(hdr, 0);
@@ -587,6 +603,7 @@ extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, i
     pp.dirs = reinterpret_cast<const DirDev*>(h->ws + o_dirs);
     pp.pov = reinterpret_cast<const int*>(h->ws + o_pov);
     pp.part = reinterpret_cast<__int128*>(h->ws + o_part);
+    pp.term = reinterpret_cast<float*>(h->ws + o_term);
     pp.area = d_area;
     pp.scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
     pp.rows = rows; pp.cols = cols; pp.n = n_sectors; pp.ngroups = ngroups; pp.npov = npov; pp.mode = mode;
@@ -599,7 +616,10 @@ extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, i
                                                                           pov_ij, npov, mode)
                                           : 0.0;
         Timer t(h, K_POINTS, s, evals);
-        points_kernel<<<(unsigned)(npov * ngroups), 1024, rtab_bytes, s>>>(pp);
+        const long long ctas = (long long)npov * ((n_sectors + POINTS_DIRS - 1) / POINTS_DIRS);
+        points_kernel<<<(unsigned)ctas, 128 * POINTS_DIRS, rtab_bytes, s>>>(pp);
+        const long long groups = (long long)npov * ngroups;
+        points_groups<<<(unsigned)((groups + 127) / 128), 128, 0, s>>>(pp);
         points_finalize<<<(npov + 127) / 128, 128, 0, s>>>(pp);
     }
     TVS_CUDA(cudaGetLastError(), "points launch");
