@@ -332,6 +332,42 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
         plan->chunks.push_back(c);
         i = ii;
     }
+    // Cost-sorted queue: within each chunk the jobs are ordered by their longest
+    // side, largest first, so that the sweep's persistent warps, which claim
+    // items in order, end the launch on the short rows of the smallest DEMs.
+    // A job's instances stay contiguous and in direction order.
+    for (const Chunk& c : plan->chunks) {
+        std::vector<std::pair<int, int>> blocks;   // [t, u) of one job
+        for (int t = c.i0; t < c.i1;) {
+            int u = t;
+            while (u < c.i1 && plan->inst_job[u] == plan->inst_job[t]) ++u;
+            blocks.emplace_back(t, u);
+            t = u;
+        }
+        if (blocks.size() < 2) continue;
+        auto side = [&](const std::pair<int, int>& b) {
+            const JobSpec& J = jobs[plan->inst_job[b.first]];
+            return std::max(J.rows, J.cols);
+        };
+        std::stable_sort(blocks.begin(), blocks.end(),
+                         [&](const std::pair<int, int>& a, const std::pair<int, int>& b) { return side(a) > side(b); });
+        std::vector<HostDir> hd;
+        std::vector<int> ij, ik;
+        std::vector<DirWork> iw;
+        for (const auto& b : blocks)
+            for (int t = b.first; t < b.second; ++t) {
+                hd.push_back(plan->hdirs[t]);
+                ij.push_back(plan->inst_job[t]);
+                ik.push_back(plan->inst_k[t]);
+                iw.push_back(inst_work[t]);
+            }
+        for (int t = c.i0; t < c.i1; ++t) {
+            plan->hdirs[t] = hd[t - c.i0];
+            plan->inst_job[t] = ij[t - c.i0];
+            plan->inst_k[t] = ik[t - c.i0];
+            inst_work[t] = iw[t - c.i0];
+        }
+    }
     std::vector<int> first_chunk(njobs, -1), last_chunk(njobs, -1);
     for (int q = 0; q < (int)plan->chunks.size(); ++q)
         for (int t = plan->chunks[q].i0; t < plan->chunks[q].i1; ++t) {
