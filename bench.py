@@ -498,6 +498,7 @@ def run_batch_bench(args) -> int:
     b.record(stream)
     torch.cuda.synchronize(device)
     one_s = a.elapsed_time(b) / 1e3
+    small = _small_tiles_batch(tvs, torch, device, stream, args)
     if rank != 0:
         return 0
     mean_s = max_s / args.steps
@@ -515,6 +516,7 @@ def run_batch_bench(args) -> int:
         "dems_per_s": len(jobs) * world / mean_s,
         "one_at_a_time": {"dems_per_s": len(jobs) / one_s, "value": E / one_s / 1e9, "unit": UNIT,
                           "api": "tvs_total_viewshed_device per tile, same tuning"},
+        "small_tiles": small,
         "gpu_launches": info["kernels_per_launch"] * args.steps,
         "clocks": clocks,
     }
@@ -523,6 +525,47 @@ def run_batch_bench(args) -> int:
     single.close()
     ctx.close()
     return 0
+
+
+def _small_tiles_batch(tvs, torch, device, stream, args, count: int = 256) -> dict:
+    """Many small tiles (side log-uniform 64-256), where one tile cannot fill
+    the GPU: one prepared batch per step against the tiles one at a time,
+    both with the library's default tuning, CUDA events on the stream."""
+    tiles = terrain.batch_tiles(count, seed=terrain.SEED_BASE + 5, side_lo=64, side_hi=256)
+    jobs, E = [], 0
+    for t in tiles:
+        d = torch.from_numpy(terrain.tile_dem(t)).to(device)
+        jobs.append(dict(dem=d, out=torch.empty_like(d), step_m=t["step"], obs_height_m=t["h0"], n_sectors=t["n"],
+                         max_range_m=t["max_range"]))
+        E += tvs.count_evals(t["rows"], t["cols"], t["n"], t["step"], t["max_range"])
+    ctx = tvs.Context(device.index, hbm_budget_bytes=args.hbm_budget_mb << 20)
+    batch = ctx.prepare_batch(jobs)
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 1)):
+            fn()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize(device)
+        return a.elapsed_time(b) / 1e3 / reps
+
+    def one_at_a_time():
+        for j in jobs:
+            ctx.total_viewshed_device(j["dem"], j["step_m"], j["obs_height_m"], j["n_sectors"], j["max_range_m"],
+                                      out=j["out"], stream=stream)
+
+    b_s = timed(lambda: batch.launch(stream), max(args.steps, 3))
+    o_s = timed(one_at_a_time, max(args.steps, 3))
+    info = batch.info()
+    batch.close()
+    ctx.close()
+    return {"tiles": count, "sides": "log-uniform 64-256", "evals_per_step": E, "chunks": info["chunks"],
+            "batched_dems_per_s": count / b_s, "one_at_a_time_dems_per_s": count / o_s,
+            "batched_value": E / b_s / 1e9, "one_at_a_time_value": E / o_s / 1e9, "unit": UNIT,
+            "tuning": "library default on both arms"}
 
 
 def _pct(xs, q):

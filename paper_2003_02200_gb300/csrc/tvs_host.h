@@ -27,7 +27,7 @@ int cuda_fail(cudaError_t e, const char* where);
     } while (0)
 
 constexpr int kMaxDim = 16384;        // longest walk axis the staged sweep supports
-constexpr int kMaxChunkDirs = 1024;   // directions per chunk (bounds the item table in smem)
+constexpr int kMaxChunkDirs = 4096;   // directions per chunk (bounds the item table in smem)
 constexpr long long kMaxChunkItems = 1LL << 30;  // sweep warp items per chunk
 
 inline size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
