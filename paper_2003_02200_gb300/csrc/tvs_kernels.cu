@@ -76,6 +76,7 @@ __global__ void colmap_kernel(const DirDev* __restrict__ dir, int* __restrict__ 
 // segments are read along DEM rows (coalesced) and transposed on the way into
 // shared memory (row pitch SKEW_TJ + 1: no bank conflicts either way).
 constexpr int SKEW_ROWS = SKEW_TP + SKEW_TJ + 3;
+constexpr int SKEW_TILES_PER_CTA = 8;   // tiles of one direction per CTA, at most
 constexpr int SKEW_PITCH = SKEW_TJ + 1;
 
 __global__ void __launch_bounds__(256) skew_kernel(const JobDev* __restrict__ jobs,
@@ -88,72 +89,79 @@ __global__ void __launch_bounds__(256) skew_kernel(const JobDev* __restrict__ jo
     const int cols = jobs[d.job].cols;
     const int tiles_j = (d.W + SKEW_TJ - 1) / SKEW_TJ;
     const int tiles_p = (d.R + SKEW_TP - 1) / SKEW_TP;
-    if ((int)blockIdx.x >= tiles_j * tiles_p) return;
-    const int pt = blockIdx.x / tiles_j, jt = blockIdx.x - pt * tiles_j;
-    const int p0 = pt * SKEW_TP, j0 = jt * SKEW_TJ;
-    const int p1 = min(p0 + SKEW_TP, d.R) - 1;
-    const int j1 = min(j0 + SKEW_TJ, d.W) - 1;
-    const int nj = j1 - j0 + 1;
-    int amin = p0 - d.D + dest_of(d.t_fx, j0);
-    int amax = p1 - d.D + dest_of(d.t_fx, j1) + 1;
-    amin = max(amin, 0);
-    amax = min(amax, d.H - 1);
-    if (amin > amax) return;
-    const int na = amax - amin + 1;
-
-    if (d.frame == 0 || d.frame == 3) {
-        const bool vec = ((cols & 3) == 0) && nj == SKEW_TJ;
-        if (vec) {
-            // 8 lanes x 16 B per 128 B row segment, 4 row segments per warp instruction
-            for (int idx = threadIdx.x; idx < na * (SKEW_TJ / 4); idx += blockDim.x) {
-                const int r = idx / (SKEW_TJ / 4), c4 = (idx - r * (SKEW_TJ / 4)) * 4;
-                const int a = amin + r;
-                const int drow = d.frame == 0 ? a : d.H - 1 - a;
-                const float4 v = *reinterpret_cast<const float4*>(dem + (long long)drow * cols + j0 + c4);
-                float* s = S + r * SKEW_PITCH + c4;
-                s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+    // the CTAs of a direction stride over its tiles (directions differ in
+    // tile count; a grid sized for the largest would launch idle CTAs)
+    for (int tile = blockIdx.x; tile < tiles_j * tiles_p; tile += gridDim.x) {
+        const int pt = tile / tiles_j, jt = tile - pt * tiles_j;
+        const int p0 = pt * SKEW_TP, j0 = jt * SKEW_TJ;
+        const int p1 = min(p0 + SKEW_TP, d.R) - 1;
+        const int j1 = min(j0 + SKEW_TJ, d.W) - 1;
+        const int nj = j1 - j0 + 1;
+        int amin = p0 - d.D + dest_of(d.t_fx, j0);
+        int amax = p1 - d.D + dest_of(d.t_fx, j1) + 1;
+        amin = max(amin, 0);
+        amax = min(amax, d.H - 1);
+        if (amin > amax) continue;        // uniform over the CTA
+        const int na = amax - amin + 1;
+        __syncthreads();                  // the previous tile's blends are done with S
+        if (d.frame == 0 || d.frame == 3) {
+            const bool vec = ((cols & 3) == 0) && nj == SKEW_TJ;
+            if (vec) {
+                // 8 lanes x 16 B per 128 B row segment, 4 row segments per warp instruction
+                for (int idx = threadIdx.x; idx < na * (SKEW_TJ / 4); idx += blockDim.x) {
+                    const int r = idx / (SKEW_TJ / 4), c4 = (idx - r * (SKEW_TJ / 4)) * 4;
+                    const int a = amin + r;
+                    const int drow = d.frame == 0 ? a : d.H - 1 - a;
+                    const float4 v = *reinterpret_cast<const float4*>(dem + (long long)drow * cols + j0 + c4);
+                    float* s = S + r * SKEW_PITCH + c4;
+                    s[0] = v.x; s[1] = v.y; s[2] = v.z; s[3] = v.w;
+                }
+            } else {
+                for (int idx = threadIdx.x; idx < na * SKEW_TJ; idx += blockDim.x) {
+                    const int r = idx / SKEW_TJ, c = idx - r * SKEW_TJ;
+                    const int a = amin + r;
+                    const int drow = d.frame == 0 ? a : d.H - 1 - a;
+                    if (c < nj) S[r * SKEW_PITCH + c] = dem[(long long)drow * cols + j0 + c];
+                }
             }
         } else {
-            for (int idx = threadIdx.x; idx < na * SKEW_TJ; idx += blockDim.x) {
-                const int r = idx / SKEW_TJ, c = idx - r * SKEW_TJ;
-                const int a = amin + r;
-                const int drow = d.frame == 0 ? a : d.H - 1 - a;
-                if (c < nj) S[r * SKEW_PITCH + c] = dem[(long long)drow * cols + j0 + c];
+            // warp w stages view columns w, w + 8, ... (DEM rows), its lanes
+            // consecutive view rows (DEM columns): coalesced reads, conflict-free
+            // transposed stores (pitch 33)
+            const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+            for (int c = warp; c < nj; c += nwarps) {
+                const int j = j0 + c;
+                const int drow = d.frame == 1 ? j : d.W - 1 - j;
+                const float* src = dem + (long long)drow * cols + amin;
+                for (int r = lane; r < na; r += 32) S[r * SKEW_PITCH + c] = src[r];
             }
         }
-    } else {
-        for (int idx = threadIdx.x; idx < nj * na; idx += blockDim.x) {
-            const int c = idx / na, r = idx - c * na;
-            const int j = j0 + c;
-            const int drow = d.frame == 1 ? j : d.W - 1 - j;
-            S[r * SKEW_PITCH + c] = dem[(long long)drow * cols + amin + r];
-        }
-    }
-    __syncthreads();
+        __syncthreads();
 
-    const int c = threadIdx.x % SKEW_TJ;
-    const int j = j0 + c;
-    if (j > j1) return;
-    const unsigned long long y = (unsigned long long)j * d.t_fx;
-    const int dest = (int)(y >> 32);
-    const unsigned fr = (unsigned)(y & 0xFFFFFFFFull);
-    // Blend weights of Alg. 6 in single precision: r = frac * 2^-32.
-    const float r = __fmul_rn(__uint2float_rn(fr), 0x1p-32f);
-    const float wa = __fsub_rn(1.0f, r);
-    float* out = sdem + d.slab + j;
-    for (int pp = threadIdx.x / SKEW_TJ; pp < SKEW_TP; pp += blockDim.x / SKEW_TJ) {
-        const int p = p0 + pp;
-        if (p > p1) break;
-        const int a = p - d.D + dest;
-        const bool ok = a >= 0 && (fr == 0u ? a <= d.H - 1 : a + 1 <= d.H - 1);
-        if (!ok) continue;
-        const float va = S[(a - amin) * SKEW_PITCH + c];
-        float z = va;
-        if (fr != 0u) {
-            const float vb = S[(a + 1 - amin) * SKEW_PITCH + c];
-            z = __fadd_rn(__fmul_rn(wa, va), __fmul_rn(r, vb));
+        const int c = threadIdx.x % SKEW_TJ;
+        const int j = j0 + c;
+        if (j > j1) continue;
+        const unsigned long long y = (unsigned long long)j * d.t_fx;
+        const int dest = (int)(y >> 32);
+        const unsigned fr = (unsigned)(y & 0xFFFFFFFFull);
+        // Blend weights of Alg. 6 in single precision: r = frac * 2^-32.
+        const float r = __fmul_rn(__uint2float_rn(fr), 0x1p-32f);
+        const float wa = __fsub_rn(1.0f, r);
+        float* out = sdem + d.slab + j;
+        for (int pp = threadIdx.x / SKEW_TJ; pp < SKEW_TP; pp += blockDim.x / SKEW_TJ) {
+            const int p = p0 + pp;
+            if (p > p1) break;
+            const int a = p - d.D + dest;
+            const bool ok = a >= 0 && (fr == 0u ? a <= d.H - 1 : a + 1 <= d.H - 1);
+            if (!ok) continue;
+            const float va = S[(a - amin) * SKEW_PITCH + c];
+            float z = va;
+            if (fr != 0u) {
+                const float vb = S[(a + 1 - amin) * SKEW_PITCH + c];
+                z = __fadd_rn(__fmul_rn(wa, va), __fmul_rn(r, vb));
+            }
+            out[(long long)p * d.Wp] = z;
         }
-        out[(long long)p * d.Wp] = z;
     }
 }
 
@@ -589,13 +597,27 @@ __device__ __forceinline__ int find_chunk_job(const ChunkJob* __restrict__ cj, i
     return lo;
 }
 
-// 4-byte asynchronous global -> shared copies (the rows a CTA blends are not
-// 16-byte aligned in general, so no bulk copies).
+// Asynchronous global -> shared copies of 4 bytes and of 16 bytes (both
+// addresses 16-byte aligned).
 __device__ __forceinline__ void cp_async4(void* smem, const void* gmem)
 {
     const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" :: "r"(sa), "l"(gmem) : "memory");
 }
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem)
+{
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" :: "r"(sa), "l"(gmem) : "memory");
+}
+
+// Row pitch of a staged window.  In views 0 and 3 a warp's lanes blend 32
+// consecutive view columns of one view row, whose skewed rows step down with
+// the column: pitch 32 keeps each lane on its own bank, and rows of 128 bytes
+// take 16-byte copies (the window starts at a tile column, a multiple of 32,
+// in rows padded to a multiple of 4).  In views 1 and 2 the lanes blend 32
+// consecutive view rows at one column: pitch 33 keeps them on distinct banks
+// (4-byte copies).
+__device__ __forceinline__ int unskew_pitch(int frame) { return frame == 0 || frame == 3 ? 32 : UNSKEW_PITCH; }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" :: "n"(N) : "memory"); }
@@ -629,22 +651,36 @@ __device__ __forceinline__ void unskew_stage(const UnskewParams& up, const DirDe
                                              int* SB)
 {
     const long long off = d.slab + (long long)w.pmin * d.Wp + w.vj0;
-    for (int idx = threadIdx.x; idx < w.np * 32; idx += UNSKEW_THREADS) {
-        const int r = idx >> 5, cc = idx & 31;
-        if (cc < w.nj) {
-            const long long a = off + (long long)r * d.Wp + cc;
-            cp_async4(SF + r * UNSKEW_PITCH + cc, up.cvf + a);
-            cp_async4(SB + r * UNSKEW_PITCH + cc, up.cvb + a);
+    if (d.frame == 0 || d.frame == 3) {
+        // 8 chunks of 4 columns per row; the last may read up to 3 padding
+        // columns of the row (vj0 + 4 ceil(nj / 4) <= Wp)
+        for (int idx = threadIdx.x; idx < w.np * 8; idx += UNSKEW_THREADS) {
+            const int r = idx >> 3, q4 = (idx & 7) * 4;
+            if (q4 < w.nj) {
+                const long long a = off + (long long)r * d.Wp + q4;
+                cp_async16(SF + r * 32 + q4, up.cvf + a);
+                cp_async16(SB + r * 32 + q4, up.cvb + a);
+            }
+        }
+    } else {
+        for (int idx = threadIdx.x; idx < w.np * 32; idx += UNSKEW_THREADS) {
+            const int r = idx >> 5, cc = idx & 31;
+            if (cc < w.nj) {
+                const long long a = off + (long long)r * d.Wp + cc;
+                cp_async4(SF + r * UNSKEW_PITCH + cc, up.cvf + a);
+                cp_async4(SB + r * UNSKEW_PITCH + cc, up.cvb + a);
+            }
         }
     }
 }
 
 // Directions are double-buffered: while the cells of a tile blend one
 // direction's staged rows, the next direction's rows are in flight.
-__global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
+__global__ void __launch_bounds__(UNSKEW_THREADS, 4) unskew_kernel(UnskewParams up)
 {
-    __shared__ int SF[2][UNSKEW_ROWS * UNSKEW_PITCH];
-    __shared__ int SB[2][UNSKEW_ROWS * UNSKEW_PITCH];
+    __shared__ __align__(16) int SF[2][UNSKEW_ROWS * UNSKEW_PITCH];
+    __shared__ __align__(16) int SB[2][UNSKEW_ROWS * UNSKEW_PITCH];
+    static_assert((UNSKEW_ROWS * UNSKEW_PITCH * 4) % 16 == 0, "second buffers stay 16-byte aligned");
     const ChunkJob c = up.cj[find_chunk_job(up.cj, up.ncj, blockIdx.x, false)];
     if ((int)blockIdx.z >= c.nsplit) return;
     const JobDev J = up.jobs[c.job];
@@ -689,6 +725,7 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
         }
         const int* F = SF[buf];
         const int* B = SB[buf];
+        const int pitch = unskew_pitch(d.frame);
 #pragma unroll
         for (int m = 0; m < UNSKEW_CELLS; ++m) {
             const int iD = iD0 + ly + 8 * m, jD = jD0 + lx;
@@ -703,8 +740,8 @@ __global__ void __launch_bounds__(UNSKEW_THREADS) unskew_kernel(UnskewParams up)
             const unsigned long long y = (unsigned long long)j * d.t_fx;
             const int dest = (int)(y >> 32);
             const unsigned fr = (unsigned)(y & 0xFFFFFFFFull);
-            const int hi = (i - dest + d.D - w.pmin) * UNSKEW_PITCH + (j - w.vj0);   // line through i + r
-            const int lo = hi - UNSKEW_PITCH;                                       // line through i - 1 + r
+            const int hi = (i - dest + d.D - w.pmin) * pitch + (j - w.vj0);   // line through i + r
+            const int lo = hi - pitch;                                       // line through i - 1 + r
             float val;
             if (fr == 0u) {
                 val = (float)(F[hi] + B[hi]);
@@ -781,7 +818,7 @@ cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, in
                         cudaStream_t stream)
 {
     if (ndir <= 0 || max_tiles <= 0) return cudaSuccess;
-    dim3 grid(max_tiles, ndir);
+    dim3 grid((max_tiles + SKEW_TILES_PER_CTA - 1) / SKEW_TILES_PER_CTA, ndir);
     skew_kernel<<<grid, 256, 0, stream>>>(d_jobs, d_dirs, sdem);
     return cudaGetLastError();
 }
