@@ -322,3 +322,19 @@ def test_tvs4000_range_limited_sampled_parity(ctx, orc):
     assert_fp64_tolerance(got[cells], o64, w["step"])
     # nothing farther than the range: bounded by the full disc of 10 km radius
     assert got.max() <= math.pi * w["max_range"] ** 2 * 1.01
+
+
+@pytest.mark.parametrize("rows,cols,n", [(3, 16384, 8), (16384, 3, 8)])
+def test_longest_rows_sampled_parity(ctx, orc, rows, cols, n):
+    """Rows of the longest supported length (16384 samples): walks beyond
+    LONG_WALK, measures beyond 2^24, and a distance table too large to stay
+    whole beside the staged rows (the sweep computes the entries past it) —
+    in a row-major and a transposed view."""
+    dem = make_dem(rows, cols, "frac", seed=rows + cols)
+    got = ctx.total_viewshed(dem, 10.0, 1.5, n, 0.0)
+    cells = sample_cells(rows, cols, 60, seed=5)
+    o32 = orc.total_viewshed(dem, 10.0, 1.5, n, 0.0, prec=32, cells=cells)
+    np.testing.assert_allclose(got.ravel()[cells], o32, rtol=FP32_RTOL, atol=0)
+    o64 = orc.total_viewshed(dem, 10.0, 1.5, n, 0.0, prec=64, cells=cells)
+    rel = np.abs(got.ravel()[cells] - o64) / np.maximum(np.abs(o64), 100.0)
+    assert rel.max() <= FP64_MAX_REL
