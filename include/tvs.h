@@ -44,7 +44,8 @@ extern "C" {
 #define TVS_ERR_ARG     (-1)  /* bad pointer, size, step, height, count or non-finite value */
 #define TVS_ERR_OOM     (-2)  /* the work does not fit the HBM budget, or cudaMalloc failed */
 #define TVS_ERR_CUDA    (-3)  /* CUDA runtime error (no device, launch failure, ...) */
-#define TVS_ERR_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define TVS_ERR_TIMEOUT (-4)  /* a bounded wait gave up (tvs_server_wait); no kernel of the
+                                 library waits on a flag or a barrier of another CTA */
 #define TVS_ERR_STATE   (-5)  /* handle in a state that cannot serve the call */
 
 typedef struct tvs_ctx* tvs_handle;
