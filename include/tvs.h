@@ -123,10 +123,15 @@ int tvs_total_viewshed_device(tvs_handle h, const float* d_dem, int rows, int co
  * (a cudaStream_t, NULL = legacy default stream); d_dem, d_out (rows*cols
  * float32 each, not overlapping) and the stream must belong to that device.
  * The first call on a device resolves the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * (cudaGetSymbolAddress).  The entry point cannot be captured into a CUDA
+ * graph: its tables reach the device through copies from host memory that the
+ * next call reuses, so a call on a capturing stream returns TVS_ERR_ARG.
  * Every call shares the one array (it keeps the last call's contents; the
  * entry point resets what must start at zero), so calls that overlap on the
- * GPU race: order them on one stream or synchronise between them.
+ * GPU race: order them on one stream or synchronise between them.  Its host
+ * tables are static too (not on the calling thread's stack, so a worker
+ * thread with a small stack may call it), and host threads take turns
+ * through the entry point.
  * Limits: n_sectors <= 1024, and the job must fit 64 MiB: 16 bytes per DEM
  * cell (exact running totals) plus 12 bytes per skewed sample of at least one
  * direction (a diagonal direction of an S x S DEM has about 2 S^2 samples, so

@@ -267,6 +267,20 @@ namespace {
 std::mutex g_noalloc_mu;
 char* g_noalloc_base[kNoAllocMaxDevices] = {};
 
+// Host-side planning tables of the no-allocation entry point.  They live in
+// static storage rather than on the calling thread's stack (about 140 KB at
+// 1024 directions, more than some worker threads have) and are used by one
+// call at a time under g_noalloc_call_mu.  That is host memory, so the entry
+// point still allocates nothing on the device.
+struct NoAllocTables {
+    DirDev dirs[kNoAllocMaxDirs];
+    int istart[2 * kNoAllocMaxDirs + 1];
+    int chunk_k0[kNoAllocMaxDirs + 1];
+    ChunkJob cjs[kNoAllocMaxDirs];
+};
+std::mutex g_noalloc_call_mu;
+NoAllocTables g_noalloc_tables;
+
 // Device address of the scratch array on `device` (current), resolved once per
 // device.  A host-side reference to g_noalloc_scratch is only a stand-in, so
 // host code must pass this address to kernels.
@@ -300,6 +314,16 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     const char* b = reinterpret_cast<const char*>(d_out);
     if (a < b + cells * 4 && b < a + cells * 4) return fail(TVS_ERR_ARG, "d_dem and d_out overlap");
     cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+    // The tables below reach the device through copies from host memory that
+    // is reused by the next call, so a captured call would replay stale
+    // tables: refuse capture.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    const cudaError_t ce = cudaStreamIsCapturing(s, &cap);
+    if (ce == cudaErrorStreamCaptureImplicit || (ce == cudaSuccess && cap != cudaStreamCaptureStatusNone)) {
+        cudaGetLastError();
+        return fail(TVS_ERR_ARG, "the no-allocation entry point cannot be captured into a CUDA graph");
+    }
+    TVS_CUDA(ce, "cudaStreamIsCapturing");
     int device = 0;
     TVS_CUDA(cudaGetDevice(&device), "cudaGetDevice");
     char* base = nullptr;
@@ -310,12 +334,14 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     TVS_CUDA(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device),
              "device attribute");
 
-    // Direction table and chunking, on the stack: chunks of consecutive
-    // directions whose skewed slabs fit what the fixed part leaves.
-    DirDev dirs[kNoAllocMaxDirs];
-    int istart[2 * kNoAllocMaxDirs + 1];
-    int chunk_k0[kNoAllocMaxDirs + 1];
-    ChunkJob cjs[kNoAllocMaxDirs];
+    // Direction table and chunking: chunks of consecutive directions whose
+    // skewed slabs fit what the fixed part leaves.  The tables are static
+    // host storage used by one call at a time.
+    std::lock_guard<std::mutex> call_lock(g_noalloc_call_mu);
+    DirDev* dirs = g_noalloc_tables.dirs;
+    int* istart = g_noalloc_tables.istart;
+    int* chunk_k0 = g_noalloc_tables.chunk_k0;
+    ChunkJob* cjs = g_noalloc_tables.cjs;
     int nchunks = 0;
     const int tiles = unskew_tiles(rows, cols);
     const Tuning tn;
@@ -342,7 +368,10 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 make_direction(n_sectors, kk, rows, cols, step_m, max_range_m, &d);
                 const size_t wp = (size_t)((d.W + 3) & ~3);
                 const size_t s2 = slab + (size_t)d.R * wp, r2 = nrows + d.R;
-                const size_t need = 2 * align256(r2 * 4) + 3 * align256(s2 * 4);
+                // every chunk uses one layout sized by the largest row count
+                // and the largest slab of all chunks, which may come from
+                // different chunks: check the layout this chunk will really get
+                const size_t need = 2 * align256(std::max(max_rows, r2) * 4) + 3 * align256(std::max(max_slab, s2) * 4);
                 if (need > avail || 2LL * (long long)r2 > kMaxChunkItems) break;
                 DirDev& v = dirs[kk];
                 std::memset(&v, 0, sizeof(v));
@@ -407,8 +436,11 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     float* d_sdem = reinterpret_cast<float*>(base + o_sdem);
     int* d_cvf = reinterpret_cast<int*>(base + o_sdem + align256(max_slab * 4));
     int* d_cvb = reinterpret_cast<int*>(base + o_sdem + 2 * align256(max_slab * 4));
+    if (o_sdem + 3 * align256(max_slab * 4) > kNoAllocScratchBytes)
+        return fail(TVS_ERR_OOM, "the job's layout does not fit the 64 MiB no-allocation scratch");
 
-    // Stack tables are staged by the runtime before these calls return.
+    // Copies from pageable host memory: the runtime has staged the tables
+    // before each call returns, so the next call may reuse them.
     TVS_CUDA(cudaMemcpyAsync(d_dirs, dirs, (size_t)n_sectors * sizeof(DirDev), cudaMemcpyHostToDevice, s),
              "copy direction table");
     TVS_CUDA(cudaMemcpyAsync(d_job, &job, sizeof(JobDev), cudaMemcpyHostToDevice, s), "copy job table");

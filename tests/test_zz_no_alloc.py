@@ -72,3 +72,67 @@ def test_noalloc_refuses_a_job_larger_than_its_array():
                                                torch.cuda.current_stream().cuda_stream)
     assert rc == tvs._binding.TVS_ERR_OOM
     assert b"64 MiB" in lib.tvs_last_error(None)
+
+
+@pytest.mark.parametrize("rows,cols,n", [(2000, 100, 180), (2000, 100, 360), (100, 2000, 360), (128, 2048, 180)])
+def test_noalloc_elongated_dems_stay_inside_the_array(rows, cols, n):
+    """Elongated DEMs: the chunks with the most skewed rows and the chunk with
+    the largest slab are different chunks, and the layout sized by both must
+    still fit the array (the entry point checks the layout it really uses)."""
+    import torch
+    lib = tvs.load()
+    dem = terrain.fractal_dem(rows, cols, 0.8, 600.0, seed=rows * 7 + cols)
+    d = torch.from_numpy(dem).cuda()
+    want = _reference(d, 10.0, 1.5, n, 0.0)
+    for _ in range(2):
+        got = _noalloc(lib, d, 10.0, 1.5, n, 0.0)
+        np.testing.assert_allclose(got, want, rtol=RTOL_INSIDE_GROUPS, atol=0)
+
+
+def test_noalloc_from_a_thread_with_a_small_stack():
+    """A worker thread with a 256 KB stack, at the 1024-direction limit: the
+    entry point keeps its planning tables off the caller's stack."""
+    import threading
+    import torch
+    lib = tvs.load()
+    dem = terrain.fractal_dem(48, 40, 0.8, 300.0, seed=11)
+    d = torch.from_numpy(dem).cuda()
+    want = _reference(d, 10.0, 1.5, 1024, 0.0)
+    box = {}
+
+    def work():
+        try:
+            torch.cuda.set_device(0)
+            box["got"] = _noalloc(lib, d, 10.0, 1.5, 1024, 0.0)
+        except BaseException as e:   # reported on the main thread
+            box["err"] = e
+
+    old = threading.stack_size(256 * 1024)
+    try:
+        t = threading.Thread(target=work)
+        t.start()
+        t.join()
+    finally:
+        threading.stack_size(old)
+    assert "err" not in box, box.get("err")
+    np.testing.assert_array_equal(box["got"], want)
+
+
+def test_noalloc_refuses_stream_capture():
+    import torch
+    lib = tvs.load()
+    d = torch.rand(32, 32, device="cuda")
+    out = torch.empty_like(d)
+    x = torch.zeros(4, device="cuda")
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.stream(s):
+        g.capture_begin()
+        x.add_(1.0)
+        rc = lib.tvs_total_viewshed_device_noalloc(d.data_ptr(), 32, 32, 10.0, 1.5, 8, 0.0, out.data_ptr(),
+                                                   s.cuda_stream)
+        g.capture_end()
+    torch.cuda.current_stream().wait_stream(s)
+    assert rc == tvs._binding.TVS_ERR_ARG
+    assert b"captured" in lib.tvs_last_error(None)
