@@ -533,3 +533,40 @@ def test_visibility_map_counts_add_over_povs(orc):
     apart = sum(orc.visibility_map(dem, 10.0, 1.5, 24, 0.0, prec=32, povs=[p]) for p in povs)
     assert np.array_equal(together, apart)
     assert all(together[p] >= 1 for p in povs)
+
+
+def _fp32_tie_cases():
+    with open(os.path.join(GOLDEN, "fp32_ties.txt")) as f:
+        lines = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    tfx = int(lines[0][1])
+    cases, cur = [], None
+    for ln in lines[1:]:
+        if ln[0] == "case":
+            cur = {"h0": float.fromhex(ln[2]), "rows": []}
+            cases.append(cur)
+        elif ln[0] == "row":
+            cur["rows"].append([float.fromhex(v) for v in ln[1:]])
+        elif ln[0] in ("cv32", "cv64"):
+            cur[ln[0]] = [int(v) for v in ln[1:]]
+    return tfx, cases
+
+
+def test_golden_fp32_near_ties(orc):
+    """tests/golden/fp32_ties.txt: near-tie lines of sight (direction 1 of 8,
+    blended samples) whose measures were derived in exact rational arithmetic
+    from the operation order of the FP32-decision reading (reading 19:
+    (1-r) a + r b, h = z + float(h0), (z - h) * rcp(d), all in single
+    precision) and of the FP64 reading.  The generator kept cases that a
+    division instead of rcp, a fused blend, h0 added unrounded, or the blend
+    weight taken from the exact r would each change, so any of those mistakes
+    in the oracle's FP32 mode fails here."""
+    tfx, cases = _fp32_tie_cases()
+    assert orc.direction(8, 1, 4, 8)["t_fx"] == tfx
+    assert len(cases) >= 4
+    for c in cases:
+        dem = np.array(c["rows"], dtype=np.float32)
+        assert np.array_equal(dem.astype(np.float64), np.array(c["rows"]))   # exact float32 values
+        for prec in (32, 64):
+            got = orc.line_cv(dem, 1.0, c["h0"], 8, 0.0, prec, 1, 0)
+            assert got.tolist() == c[f"cv{prec}"], (prec, got.tolist(), c[f"cv{prec}"])
+        assert c["cv32"] != c["cv64"]          # every case is a real FP32 / FP64 split
