@@ -133,9 +133,9 @@ int tvs_total_viewshed_device(tvs_handle h, const float* d_dem, int rows, int co
  * thread with a small stack may call it), and host threads take turns
  * through the entry point.
  * Limits: n_sectors <= 1024, and the job must fit 64 MiB: 16 bytes per DEM
- * cell (exact running totals) plus 12 bytes per skewed sample of at least one
+ * cell (exact running totals) plus 8 bytes per skewed sample of at least one
  * direction (a diagonal direction of an S x S DEM has about 2 S^2 samples, so
- * S <= 1290 fits; larger jobs return TVS_ERR_OOM with a message).
+ * S <= 1440 fits; larger jobs return TVS_ERR_OOM with a message).
  * Errors: TVS_ERR_ARG, TVS_ERR_OOM, TVS_ERR_CUDA. */
 int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, int cols, double step_m,
                                       double obs_height_m, int n_sectors, double max_range_m, float* d_out,
@@ -192,7 +192,8 @@ int tvs_batch_launch(tvs_batch_handle b, void* cuda_stream);
 int tvs_batch_get_info(tvs_batch_handle b, tvs_batch_info* info);
 void tvs_batch_destroy(tvs_batch_handle b);
 
-/* Launch choices of a handle (no effect on results, only on speed).
+/* Launch choices of a handle (no effect on results, only on speed, except
+ * fp32_decisions).
  * small_pov_below_w: every skewed row of a direction whose walk axis is
  *   shorter than this is swept with 4 POVs per lane group (default 0: none);
  * p4_cost_pct: the other rows pick 4 or 8 POVs per lane group row by row,
@@ -206,15 +207,24 @@ void tvs_batch_destroy(tvs_batch_handle b);
  * prune: exact horizon pruning in the sweep (1, default) or none (0): a group
  *   of POVs stops walking once no remaining target can rise above its running
  *   maximum elevation angle (bounded through the row's suffix maximum with
- *   monotone FP32 rounding), which leaves every result bit for bit the same;
- *   the work count (evaluations) stays the unpruned one. */
+ *   monotone rounding), which leaves every result bit for bit the same;
+ *   the work count (evaluations) stays the unpruned one.
+ * fp32_decisions: 0 (default) takes every visibility decision (Alg. 8's
+ *   comparison of a target's elevation angle with the running maximum) as
+ *   exact arithmetic on the blended heights takes it -- FP32 decisions proved
+ *   by an error bound, double-float and FP64 walks where the bound does not
+ *   settle one -- so each per-sample measure equals the FP64 definition's;
+ *   1 takes them in single precision as the paper's kernels declare heights
+ *   and slopes (float in Alg. 6-8): (1 - r) a + r b, h = z + h0,
+ *   (z - h) * (1/d) rounded at every step, which flips near-ties.  This
+ *   field changes results (by such flips only). */
 typedef struct {
     int32_t small_pov_below_w;
     int32_t sweep_max_warps;
     int32_t unskew_ctas_per_sm;
     int32_t p4_cost_pct;
     int32_t prune;
-    int32_t pad_;
+    int32_t fp32_decisions;
 } tvs_tuning;
 
 int tvs_get_tuning(tvs_handle h, tvs_tuning* t);
@@ -251,6 +261,14 @@ int tvs_debug_rowmap(tvs_handle h, int rows, int cols, int n_sectors, int k, int
 int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, double step_m,
                            double obs_height_m, int n_sectors, double max_range_m, int k,
                            int32_t* cv, int32_t* R, int32_t* W);
+
+/* Test hook: the sweep checks the indices of its staging, per-block margins,
+ * flagged-POV list and exact walks against their buffers; the first violation
+ * on the current device (code, index, bound, CTA; all zero when none) is
+ * copied to out[0..3] after a device synchronisation, and cleared when
+ * `clear` is non-zero.  A violation means a library bug: the access was
+ * skipped instead of faulting.  Errors: TVS_ERR_ARG, TVS_ERR_CUDA. */
+int tvs_debug_sweep_check(int32_t* out, int clear);
 
 /* Turn per-kernel timing on (1) or off (0); turning it on clears the counters.
  * While on, each launch is bracketed by CUDA events on its stream. */

@@ -50,7 +50,7 @@ class BatchInfo(C.Structure):
 class Tuning(C.Structure):
     _fields_ = [("small_pov_below_w", C.c_int32), ("sweep_max_warps", C.c_int32),
                 ("unskew_ctas_per_sm", C.c_int32), ("p4_cost_pct", C.c_int32), ("prune", C.c_int32),
-                ("pad_", C.c_int32)]
+                ("fp32_decisions", C.c_int32)]
 
 
 class ServerConfig(C.Structure):
@@ -133,6 +133,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             "tvs_debug_rowmap": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, i32p], C.c_int),
             "tvs_debug_direction_cv": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
+            "tvs_debug_sweep_check": ([i32p, C.c_int], C.c_int),
             "tvs_viewshed_points": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
                                      C.c_int, C.c_int, vp, vp], C.c_int),
             "tvs_visibility_map": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
@@ -174,6 +175,14 @@ def direction(n_sectors: int, k: int, rows: int, cols: int, step_m: float = 1.0,
     info = DirectionInfo()
     _check(load().tvs_direction(n_sectors, k, rows, cols, step_m, max_range_m, C.byref(info)))
     return {f: getattr(info, f) for f, _ in DirectionInfo._fields_}
+
+
+def sweep_check(clear: bool = True) -> list[int]:
+    """tvs_debug_sweep_check: the sweep's first out-of-range index on the
+    current device as [code, index, bound, CTA] (all zero when none)."""
+    out = (C.c_int32 * 4)()
+    _check(load().tvs_debug_sweep_check(out, int(clear)))
+    return list(out)
 
 
 def count_evals(rows: int, cols: int, n_sectors: int, step_m: float = 1.0, max_range_m: float = 0.0) -> int:
@@ -389,7 +398,7 @@ class Context:
         cur = self.get_tuning()
         cur.update(kw)
         t = Tuning(cur["small_pov_below_w"], cur["sweep_max_warps"], cur["unskew_ctas_per_sm"], cur["p4_cost_pct"],
-                   int(cur["prune"]), 0)
+                   int(cur["prune"]), int(cur["fp32_decisions"]))
         _check(self._lib.tvs_set_tuning(self.handle, C.byref(t)))
 
     def autotune(self, jobs) -> tuple[dict, float]:

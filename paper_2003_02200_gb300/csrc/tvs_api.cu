@@ -195,16 +195,14 @@ int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, d
     const JobDev* d_jobs = reinterpret_cast<const JobDev*>(ws + L.jobs);
     int* d_lo = reinterpret_cast<int*>(ws + L.rowlo);
     int* d_hi = reinterpret_cast<int*>(ws + L.rowhi);
-    float* d_s = reinterpret_cast<float*>(ws + L.sdem);
     int* d_cv = reinterpret_cast<int*>(ws + L.cvf);
     int* d_cb = reinterpret_cast<int*>(ws + L.cvb);
     unsigned* d_cnt = reinterpret_cast<unsigned*>(ws + L.counter);
     TVS_CUDA(launch_rowmap(d_dir, 1, v.R, d_lo, d_hi, s), "rowmap launch");
-    TVS_CUDA(launch_skew(d_jobs, d_dir, 1, c.max_tiles, d_s, s), "skew launch");
     TVS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), s), "reset work counter");
-    TVS_CUDA(launch_sweep(d_dir, reinterpret_cast<const int*>(ws + L.istart), 1, c.items, d_s, d_lo, d_hi, d_cv,
-                          d_cb, v.W, v.K, h->tuning.prune, d_cnt, h->num_sms, h->smem_optin,
-                          h->tuning.sweep_max_warps, s),
+    TVS_CUDA(launch_sweep(d_dir, d_jobs, reinterpret_cast<const int*>(ws + L.istart), 1, c.items, d_lo, d_hi, d_cv,
+                          d_cb, v.W, v.K, h->tuning.prune, !h->tuning.fp32_decisions, d_cnt, h->num_sms,
+                          h->smem_optin, h->tuning.sweep_max_warps, s),
              "sweep launch");
     std::vector<int> slab(c.slab_elems), slabb(c.slab_elems), lo(v.R), hi(v.R);
     TVS_CUDA(cudaMemcpyAsync(slab.data(), d_cv, c.slab_elems * 4, cudaMemcpyDeviceToHost, s), "copy cv");
@@ -371,7 +369,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 // every chunk uses one layout sized by the largest row count
                 // and the largest slab of all chunks, which may come from
                 // different chunks: check the layout this chunk will really get
-                const size_t need = 2 * align256(std::max(max_rows, r2) * 4) + 3 * align256(std::max(max_slab, s2) * 4);
+                const size_t need = 2 * align256(std::max(max_rows, r2) * 4) + 2 * align256(std::max(max_slab, s2) * 4);
                 if (need > avail || 2LL * (long long)r2 > kMaxChunkItems) break;
                 DirDev& v = dirs[kk];
                 std::memset(&v, 0, sizeof(v));
@@ -382,6 +380,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
                 v.p4_pct = tn.p4_cost_pct;
                 v.row_off = (int)nrows; v.gidx = kk; v.job = 0;
                 v.g = (float)d.g; v.h0 = (float)obs_height_m;
+                v.h0_lo = (float)(obs_height_m - (double)v.h0);
                 slab = s2;
                 nrows = r2;
                 ++kk;
@@ -422,6 +421,7 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     job.out = d_out;
     job.acc = nchunks > 1 ? reinterpret_cast<__int128*>(base + o_acc) : nullptr;
     job.scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
+    job.h0 = obs_height_m;
     job.rows = rows;
     job.cols = cols;
     DirDev* d_dirs = reinterpret_cast<DirDev*>(base + o_dirs);
@@ -432,11 +432,10 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     unsigned* d_counter = reinterpret_cast<unsigned*>(base + o_counter);
     int* d_rowlo = reinterpret_cast<int*>(base + o_chunk);
     int* d_rowhi = reinterpret_cast<int*>(base + o_chunk + align256(max_rows * 4));
-    const size_t o_sdem = o_chunk + 2 * align256(max_rows * 4);
-    float* d_sdem = reinterpret_cast<float*>(base + o_sdem);
-    int* d_cvf = reinterpret_cast<int*>(base + o_sdem + align256(max_slab * 4));
-    int* d_cvb = reinterpret_cast<int*>(base + o_sdem + 2 * align256(max_slab * 4));
-    if (o_sdem + 3 * align256(max_slab * 4) > kNoAllocScratchBytes)
+    const size_t o_slabs = o_chunk + 2 * align256(max_rows * 4);
+    int* d_cvf = reinterpret_cast<int*>(base + o_slabs);
+    int* d_cvb = reinterpret_cast<int*>(base + o_slabs + align256(max_slab * 4));
+    if (o_slabs + 2 * align256(max_slab * 4) > kNoAllocScratchBytes)
         return fail(TVS_ERR_OOM, "the job's layout does not fit the 64 MiB no-allocation scratch");
 
     // Copies from pageable host memory: the runtime has staged the tables
@@ -451,20 +450,19 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
     int at = 0;
     for (int c = 0; c < nchunks; ++c) {
         const int k0 = chunk_k0[c], nd = chunk_k0[c + 1] - k0;
-        int max_R = 0, max_tiles = 0, wmax = 0, dmax = 0;
+        int max_R = 0, wmax = 0, dmax = 0;
         for (int q = k0; q < k0 + nd; ++q) {
             dmax = std::max(dmax, dirs[q].K);
             max_R = std::max(max_R, dirs[q].R);
-            max_tiles = std::max(max_tiles, ((dirs[q].R + SKEW_TP - 1) / SKEW_TP) * ((dirs[q].W + SKEW_TJ - 1) / SKEW_TJ));
             wmax = std::max(wmax, dirs[q].W);
         }
         const DirDev* cd = d_dirs + k0;
         TVS_CUDA(launch_rowmap(cd, nd, max_R, d_rowlo, d_rowhi, s), "rowmap launch");
-        TVS_CUDA(launch_skew(d_job, cd, nd, max_tiles, d_sdem, s), "skew launch");
         // the shared array keeps the previous call's contents: the work counter must start at zero
         TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
-        TVS_CUDA(launch_sweep(cd, d_istart + at, nd, istart[at + nd], d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                              wmax, dmax, tn.prune, d_counter, num_sms, smem_optin, tn.sweep_max_warps, s),
+        TVS_CUDA(launch_sweep(cd, d_job, d_istart + at, nd, istart[at + nd], d_rowlo, d_rowhi, d_cvf, d_cvb, wmax,
+                              dmax, tn.prune, !tn.fp32_decisions, d_counter, num_sms, smem_optin,
+                              tn.sweep_max_warps, s),
                  "sweep launch");
         TVS_CUDA(launch_unskew(d_cvf, d_cvb, d_job, cd, d_cj + c, 1, tiles, cjs[c].nsplit, d_part, s),
                  "unskew launch");
@@ -614,6 +612,7 @@ int tvs_get_tuning(tvs_handle h, tvs_tuning* t)
     t->unskew_ctas_per_sm = h->tuning.unskew_ctas_per_sm;
     t->p4_cost_pct = h->tuning.p4_cost_pct;
     t->prune = h->tuning.prune;
+    t->fp32_decisions = h->tuning.fp32_decisions;
     return TVS_OK;
 }
 
@@ -622,13 +621,14 @@ int tvs_set_tuning(tvs_handle h, const tvs_tuning* t)
     if (!h || !t) return fail(TVS_ERR_ARG, "NULL argument");
     if (t->small_pov_below_w < 0 || t->sweep_max_warps < 0 || t->sweep_max_warps > SWEEP_MAX_WARPS ||
         t->unskew_ctas_per_sm < 1 || t->unskew_ctas_per_sm > 4 || t->p4_cost_pct < 0 || t->p4_cost_pct > (1 << 20) ||
-        t->prune < 0 || t->prune > 1)
+        t->prune < 0 || t->prune > 1 || t->fp32_decisions < 0 || t->fp32_decisions > 1)
         return fail(TVS_ERR_ARG, "tuning out of range");
     h->tuning.small_pov_below_w = t->small_pov_below_w;
     h->tuning.sweep_max_warps = t->sweep_max_warps;
     h->tuning.unskew_ctas_per_sm = t->unskew_ctas_per_sm;
     h->tuning.p4_cost_pct = t->p4_cost_pct ? t->p4_cost_pct : Tuning().p4_cost_pct;
     h->tuning.prune = t->prune;
+    h->tuning.fp32_decisions = t->fp32_decisions;
     return TVS_OK;
 }
 

@@ -67,7 +67,7 @@ void job_work(int n, int rows, int cols, double step, double max_range, int k0, 
 int check_job(int rows, int cols, double step_m, double obs_height_m, int n_sectors, double max_range_m);
 
 // ------------------------------------------------------------ profiling --
-enum KernelId { K_ROWMAP = 0, K_SKEW, K_SWEEP, K_UNSKEW, K_FINAL, K_POINTS, K_MAP_FLAGS, K_MAP_RASTER, K_COUNT };
+enum KernelId { K_ROWMAP = 0, K_SWEEP, K_UNSKEW, K_FINAL, K_POINTS, K_MAP_FLAGS, K_MAP_RASTER, K_COUNT };
 
 // Tunable launch choices (see tvs_tuning in tvs.h).
 struct Tuning {
@@ -76,6 +76,7 @@ struct Tuning {
     int unskew_ctas_per_sm = 2;    // split a chunk's directions below this many unskew CTAs per SM
     int p4_cost_pct = 107;         // per-row group choice: SMALL_POV step cost relative to LARGE_POV, percent
     int prune = 1;                 // exact horizon pruning in the sweep
+    int fp32_decisions = 0;        // 1: FP32 visibility decisions, 0: certified (exact) ones
 };
 
 // Group-size mode of a direction (DirDev::pov): forced SMALL_POV below the
@@ -109,12 +110,12 @@ struct Chunk {
     size_t slab_elems;       // sum of R * Wp over the chunk
     long long rows;          // sum of R
     int items;               // sweep warp items
-    int max_R, max_tiles, wmax, dmax;
+    int max_R, wmax, dmax;
     int cj_beg, ncj;         // the chunk's entries of the chunk-job table
     int total_tiles, max_split;
     long long total_cells, part_elems;
     int istart_at;           // offset of the chunk's item table
-    double evals, skew_bytes, unskew_bytes, rowmap_bytes, final_bytes;
+    double evals, unskew_bytes, rowmap_bytes, final_bytes;
 };
 
 struct BatchPlan {
@@ -148,7 +149,7 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
 // block, uploaded with one copy.
 struct Layout {
     size_t hdr, dirs, jobs, cj, istart, hdr_bytes;
-    size_t io_dem, io_out, counter, acc, part, rowlo, rowhi, sdem, cvf, cvb, total;
+    size_t io_dem, io_out, counter, acc, part, rowlo, rowhi, cvf, cvb, total;
 };
 
 Layout make_layout(const BatchPlan& plan, bool host_io);

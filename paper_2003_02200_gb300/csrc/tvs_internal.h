@@ -26,9 +26,6 @@ constexpr int ROW_PADR = LARGE_POV + 2 * LARGE_UNROLL + 8;
 // Directions whose FP32 partial sums are added once into the FP64 total.
 constexpr int FP32_GROUP = 8;
 
-// Skew tile: rows x columns of the skewed layout per CTA.
-constexpr int SKEW_TP = 64;
-constexpr int SKEW_TJ = 32;
 // Unskew tile: DEM cells per CTA (rows x columns).
 constexpr int UNSKEW_TI = 32;
 constexpr int UNSKEW_TJ = 32;
@@ -48,7 +45,8 @@ struct DirDev {
     int gidx;                  // direction index k within its job
     int job;                   // index of the job in the job table
     float g;                   // 1 + t^2
-    float h0;                  // observer height of the job
+    float h0;                  // observer height of the job, rounded to single precision
+    float h0_lo;               // h0 - (double)h0 above, rounded (h0 to about 2^-48)
     int pov;                   // group size of every row (SMALL_POV or LARGE_POV), 0 = chosen per row
     int p4_pct;                // row_pov's relative cost of a SMALL_POV step, percent
 };
@@ -103,6 +101,7 @@ struct JobDev {
     float* out;                // rows x cols visible areas (device)
     __int128* acc;             // exact running totals when the job spans several chunks, else NULL
     double scale;              // (pi / (2n)) * step^2
+    double h0;                 // observer height (the FP64 walks of the certified sweep)
     int rows, cols;
 };
 
@@ -124,14 +123,14 @@ struct ChunkJob {
 cudaError_t launch_rowmap(const DirDev* d_dirs, int ndir, int max_R, int* rowlo, int* rowhi,
                           cudaStream_t stream);
 cudaError_t launch_colmap(const DirDev* d_dir, int* dest, unsigned* frac, cudaStream_t stream);
-cudaError_t launch_skew(const JobDev* d_jobs, const DirDev* d_dirs, int ndir, int max_tiles, float* sdem,
-                        cudaStream_t stream);
-// Sweep of a chunk: one warp item per skewed row and walk direction (items
-// 2p and 2p + 1 of a direction are row p forward and backward); `prune` turns
-// exact horizon pruning on.
-cudaError_t launch_sweep(const DirDev* d_dirs, const int* d_item_start, int ndir, int total_items,
-                         const float* sdem, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd,
-                         int wmax, int dmax, int prune, unsigned* counter, int num_sms, int smem_optin,
+// Sweep of a chunk (tvs_sweep.cu): one warp item per skewed row and walk
+// direction (items 2p and 2p + 1 of a direction are row p forward and
+// backward), its row gathered from the job's DEM; `prune` turns exact horizon
+// pruning on, `cert` certified (exact) visibility decisions instead of FP32
+// ones.
+cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* d_item_start, int ndir,
+                         int total_items, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd, int wmax,
+                         int dmax, int prune, int cert, unsigned* counter, int num_sms, int smem_optin,
                          int max_warps, cudaStream_t stream);
 // Unskew of a chunk: `total_tiles` flattened cell tiles over the chunk's jobs
 // (ncj entries of d_cj, sorted by tile_beg), `max_split` the largest nsplit.

@@ -33,9 +33,9 @@ namespace {
 
 constexpr double kTwo32 = 4294967296.0;
 
-const char* kKernelName[K_COUNT] = {"rowmap", "skew", "sweep", "unskew", "unskew_finalize",
+const char* kKernelName[K_COUNT] = {"rowmap", "sweep", "unskew", "unskew_finalize",
                                    "points", "map_flags", "map_raster"};
-const char* kKernelUnit[K_COUNT] = {"bytes", "bytes", "evals", "bytes", "bytes", "evals", "evals", "cells"};
+const char* kKernelUnit[K_COUNT] = {"bytes", "evals", "bytes", "bytes", "evals", "evals", "cells"};
 
 long long sum_min(long long L, long long K)
 {
@@ -247,8 +247,9 @@ namespace tvs {
 
 size_t chunk_bytes(size_t slab, long long rows, int ninst)
 {
-    // skewed heights + forward measures + backward measures, row tables, item table
-    return align256(slab * 4) * 3 + align256((size_t)rows * 4) * 2 + align256((size_t)(ninst + 1) * 4);
+    // forward measures + backward measures, row tables, item table (the sweep
+    // gathers its rows from the DEM: no skewed heights are stored)
+    return align256(slab * 4) * 2 + align256((size_t)rows * 4) * 2 + align256((size_t)(ninst + 1) * 4);
 }
 
 // A chunk splits only when its jobs have fewer than c = unskew_ctas_per_sm
@@ -408,17 +409,16 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
             v.job = plan->inst_job[t];
             v.g = (float)d.g;
             v.h0 = (float)J.h0;
+            v.h0_lo = (float)(J.h0 - (double)v.h0);
             off += (size_t)d.R * v.Wp;
             roff += d.R;
             c.items += 2 * d.R;
             plan->istart.push_back(c.items);
             c.max_R = std::max(c.max_R, d.R);
-            c.max_tiles = std::max(c.max_tiles, ((d.R + SKEW_TP - 1) / SKEW_TP) * ((d.W + SKEW_TJ - 1) / SKEW_TJ));
             c.wmax = std::max(c.wmax, d.W);
             c.dmax = std::max(c.dmax, v.K);
             const DirWork w = inst_work[t];
             c.evals += (double)w.evals;
-            c.skew_bytes += 4.0 * J.rows * J.cols + 4.0 * (double)w.samples;
             c.unskew_bytes += 8.0 * (double)w.samples;
             c.rowmap_bytes += 8.0 * d.R;
         }
@@ -492,7 +492,6 @@ Layout make_layout(const BatchPlan& plan, bool host_io)
     L.part = o;    o += align256((size_t)plan.max_part * 16);
     L.rowlo = o;   o += align256((size_t)plan.max_rows * 4);
     L.rowhi = o;   o += align256((size_t)plan.max_rows * 4);
-    L.sdem = o;    o += align256(plan.max_slab * 4);
     L.cvf = o;     o += align256(plan.max_slab * 4);
     L.cvb = o;     o += align256(plan.max_slab * 4);
     L.total = o;
@@ -524,6 +523,7 @@ void build_header(const BatchPlan& plan, const Layout& L, char* base, bool host_
                           : plan.acc_off[j] >= 0 ? reinterpret_cast<__int128*>(base + L.acc) + plan.acc_off[j]
                                                  : nullptr;
         jd[j].scale = (M_PI / (2.0 * (double)J.n)) * (J.step * J.step);
+        jd[j].h0 = J.h0;
         jd[j].rows = J.rows;
         jd[j].cols = J.cols;
     }
@@ -543,7 +543,6 @@ int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* bas
     __int128* d_part = reinterpret_cast<__int128*>(base + L.part);
     int* d_rowlo = reinterpret_cast<int*>(base + L.rowlo);
     int* d_rowhi = reinterpret_cast<int*>(base + L.rowhi);
-    float* d_sdem = reinterpret_cast<float*>(base + L.sdem);
     int* d_cvf = reinterpret_cast<int*>(base + L.cvf);
     int* d_cvb = reinterpret_cast<int*>(base + L.cvb);
     int launched = 0;
@@ -554,15 +553,12 @@ int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* bas
             Timer t(h, K_ROWMAP, s, c.rowmap_bytes);
             TVS_CUDA(launch_rowmap(cd, nd, c.max_R, d_rowlo, d_rowhi, s), "rowmap launch");
         }
-        {
-            Timer t(h, K_SKEW, s, c.skew_bytes);
-            TVS_CUDA(launch_skew(d_jobs, cd, nd, c.max_tiles, d_sdem, s), "skew launch");
-        }
         TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
         {
             Timer t(h, K_SWEEP, s, c.evals);
-            TVS_CUDA(launch_sweep(cd, d_istart + c.istart_at, nd, c.items, d_sdem, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                                  c.wmax, c.dmax, tn.prune, d_counter, num_sms, smem_optin, tn.sweep_max_warps, s),
+            TVS_CUDA(launch_sweep(cd, d_jobs, d_istart + c.istart_at, nd, c.items, d_rowlo, d_rowhi, d_cvf, d_cvb,
+                                  c.wmax, c.dmax, tn.prune, !tn.fp32_decisions, d_counter, num_sms, smem_optin,
+                                  tn.sweep_max_warps, s),
                      "sweep launch");
         }
         if (before_unskew) {
@@ -575,7 +571,7 @@ int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* bas
                                    d_part, s),
                      "unskew launch");
         }
-        launched += 4;
+        launched += 3;
         if (c.max_split > 1) {
             Timer t(h, K_FINAL, s, c.final_bytes);
             TVS_CUDA(launch_unskew_finalize(d_jobs, d_cj + c.cj_beg, c.ncj, c.total_cells, d_part, s),

@@ -1,0 +1,1172 @@
+// tvs_sweep.cu -- the sweep of the sDEM total viewshed (Kernel-2, Alg. 7 and
+// 8) with the relocation of Kernel-1 (Alg. 6) fused into its row staging.
+//
+// A warp item is one skewed row and one walk direction.  The warp gathers the
+// row's samples straight from the DEM (section 4.1 step 1(a): sample j of
+// line b blends view rows a = b + dest(j) and a + 1 with weights 1 - r(j) and
+// r(j)), so the skewed DEM never reaches HBM, then every usable sample of the
+// row walks it (forward items walk the row, backward items its reverse).
+//
+// Two decision modes:
+//
+//  * FP32 decisions (the paper's kernel precision: "float" heights and
+//    slopes in Alg. 6-8): the staged height is (1-r)*a + r*b in single
+//    precision and a target is visible iff fl(fl(z - h) * fl(1/d)) is
+//    strictly above the running maximum.
+//
+//  * Certified decisions (the default): every visibility decision is the one
+//    exact arithmetic takes on the exact blended heights, which is what the
+//    FP64 definition decides (it rounds some 10^-16 away from exact).  The
+//    row is staged as a double-float (hi + lo) pair per sample.  The fast
+//    path still decides in FP32, on height differences formed against a
+//    per-group reference, and proves each decision with a margin derived
+//    below; a decision inside the margin flags its POV, and flagged POVs are
+//    walked again exactly (double-float slopes with their own margin, and the
+//    FP64 definition itself for what that margin cannot settle).
+#include "tvs.h"
+#include "tvs_internal.h"
+
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+namespace tvs {
+
+// Index checks of the sweep.  Every index the staging, the per-block margins,
+// the flagged-POV list and the exact walks use is checked against its buffer
+// (not the inner step loop, whose indices follow from the block's): a
+// violation records the first offending index in g_sweep_check (code, index,
+// bound, CTA) and skips the access instead of faulting.  Read and cleared by
+// tvs_debug_sweep_check.
+__device__ int g_sweep_check[4];
+
+__device__ __forceinline__ bool in_range(long long idx, long long bound, int code)
+{
+    if (idx >= 0 && idx < bound) return true;
+    if (atomicCAS(&g_sweep_check[0], 0, code) == 0) {
+        g_sweep_check[1] = (int)idx;
+        g_sweep_check[2] = (int)bound;
+        g_sweep_check[3] = (int)blockIdx.x;
+    }
+    return false;
+}
+
+namespace {
+
+__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
+__device__ __forceinline__ float pos_inf() { return __int_as_float(0x7f800000); }
+
+struct SweepParams {
+    const DirDev* dirs;
+    const JobDev* jobs;
+    const int* item_start;
+    const int* rowlo;
+    const int* rowhi;
+    int* cv_fwd;       // forward measure of every sample (slab layout)
+    int* cv_bwd;       // backward measure of every sample (slab layout)
+    unsigned* counter;
+    int ndir;
+    int total_items;
+    int inv_len;       // entries of the per-distance table (float4 each)
+    int istart_len;    // ints of the item-start table (multiple of 4)
+    int half;          // floats of one staged row array (multiple of 4)
+    int zs_len;        // floats of the row's suffix maxima (0 without pruning)
+    int wm_len;        // floats of the row's window maxima (certified only)
+    int fl_cap;        // entries of the flagged-POV list (certified only)
+    int per_warp;      // floats of a warp's shared area
+};
+
+// ------------------------------------------------------ row geometry --
+// DEM index of view cell (a, j) of direction d and the index step from view
+// row a to view row a + 1 (the four D4 views of section 4.1 / Alg. 6).
+__device__ __forceinline__ long long view_index(const DirDev& d, int cols, int a, int j, int* step)
+{
+    switch (d.frame) {
+    case 0:  *step = cols;  return (long long)a * cols + j;
+    case 1:  *step = 1;     return (long long)j * cols + a;
+    case 2:  *step = 1;     return (long long)(d.W - 1 - j) * cols + a;
+    default: *step = -cols; return (long long)(d.H - 1 - a) * cols + j;
+    }
+}
+
+// ------------------------------------------------ double-float helpers --
+// Error-free transformations in round-to-nearest single precision.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// a + b = s + e exactly when a == 0 or exponent(a) >= exponent(b).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)
+{
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ bool df_gt(float ah, float al, float bh, float bl)
+{
+    return ah > bh || (ah == bh && al > bl);
+}
+
+// Height of the sample blending va (row a) and vb (row a + 1) with weights
+// 1 - r and r, r = fr * 2^-32 (Alg. 6), as hi + lo: the difference vb - va
+// and r are split exactly (TwoSum; r into its top 24 and low 8 bits), the main
+// product exactly (FMA), the rest rounds at about 2^-46 of max(|va|, |vb|):
+// |hi + lo - exact| <= 2^-43 max(|va|, |vb|), |lo| <= ulp(hi) / 2.
+__device__ __forceinline__ void df_blend(float va, float vb, unsigned fr, float& zh, float& zl)
+{
+    if (fr == 0u) { zh = va; zl = 0.f; return; }
+    float dh, dl;
+    two_sum(vb, -va, dh, dl);
+    const float rh = __fmul_rn(__uint2float_rn(fr & 0xFFFFFF00u), 0x1p-32f);
+    const float rl = __fmul_rn(__uint2float_rn(fr & 0xFFu), 0x1p-32f);
+    const float ph = __fmul_rn(rh, dh);
+    const float pe = __fmaf_rn(rh, dh, -ph);
+    const float t = __fmaf_rn(rh, dl, __fmaf_rn(rl, dh, __fmul_rn(rl, dl)));
+    float sh, se;
+    two_sum(va, ph, sh, se);
+    const float lo = __fadd_rn(se, __fadd_rn(pe, t));
+    two_sum(sh, lo, zh, zl);
+}
+
+// The paper's single-precision blend of Kernel-1: r = float(fr) 2^-32,
+// (1 - r) a + r b with every operation rounded.
+__device__ __forceinline__ float blend32(float va, float vb, unsigned fr)
+{
+    if (fr == 0u) return va;
+    const float r = __fmul_rn(__uint2float_rn(fr), 0x1p-32f);
+    const float wa = __fsub_rn(1.0f, r);
+    return __fadd_rn(__fmul_rn(wa, va), __fmul_rn(r, vb));
+}
+
+// A sweep work item: (direction, skewed row, walk direction).
+struct ItemRow {
+    long long rowbase;   // slab offset of the row's first usable sample
+    int dir, p, jlo;
+    int L, K, pov;
+    float h0;
+    bool rev;
+};
+
+// Decodes item into its row; false when the row is empty.
+__device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* istart, int item, ItemRow* it)
+{
+    int lo = 0, hi = sp.ndir - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (istart[mid] <= item) lo = mid; else hi = mid - 1;
+    }
+    const DirDev& d = sp.dirs[lo];
+    const int rem = item - istart[lo];
+    const int p = rem >> 1;
+    it->rev = (rem & 1) != 0;
+    const int jlo = sp.rowlo[d.row_off + p], jhi = sp.rowhi[d.row_off + p];
+    it->dir = lo;
+    it->p = p;
+    it->jlo = jlo;
+    it->L = jhi - jlo + 1;
+    it->K = d.K;
+    it->h0 = d.h0;
+    it->pov = row_pov(it->L, d.K, d.pov, d.p4_pct);
+    it->rowbase = d.slab + (long long)p * d.Wp + jlo;
+    return it->L > 0;
+}
+
+// Stages the item's row (reversed for backward items) from the DEM: FP32
+// heights into Fh, or with CERT hi parts into Fh and lo parts into Fl.  The
+// last sample and ROW_PADR samples after it hold -inf (lo 0): the last target
+// of a walk never adds area, so it may be a sentinel that is never visible.
+// Returns (CERT) the row's largest |elevation| read, for the blend's error
+// bound.
+template <bool CERT>
+__device__ __forceinline__ float stage_row(const SweepParams& sp, const ItemRow& it, float* Fh, float* Fl, int lane)
+{
+    const DirDev& d = sp.dirs[it.dir];
+    const float* __restrict__ dem = sp.jobs[d.job].dem;
+    const int cols = sp.jobs[d.job].cols;
+    const long long cells = (long long)sp.jobs[d.job].rows * cols;
+    const int b = it.p - d.D;
+    const unsigned long long t_fx = d.t_fx;
+    const float NEG = neg_inf();
+    float zmax = 0.f;
+    constexpr int B = 4;
+    for (int x0 = lane; x0 < it.L; x0 += 32 * B) {
+        float va[B], vb[B];
+        unsigned fr[B];
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int x = x0 + 32 * k;
+            va[k] = 0.f; vb[k] = 0.f; fr[k] = 0u;
+            if (x < it.L) {
+                const int j = it.jlo + (it.rev ? it.L - 1 - x : x);
+                const unsigned long long y = (unsigned long long)j * t_fx;
+                const int a = b + (int)(y >> 32);
+                fr[k] = (unsigned)y;
+                int st;
+                const long long idx = view_index(d, cols, a, j, &st);
+                va[k] = in_range(idx, cells, 1) ? dem[idx] : 0.f;
+                vb[k] = fr[k] != 0u ? (in_range(idx + st, cells, 2) ? dem[idx + st] : 0.f) : va[k];
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < B; ++k) {
+            const int x = x0 + 32 * k;
+            if (x >= it.L || !in_range(ROW_PADL + x, sp.half, 3)) continue;
+            if (CERT) {
+                float zh, zl;
+                df_blend(va[k], vb[k], fr[k], zh, zl);
+                Fh[ROW_PADL + x] = x == it.L - 1 ? NEG : zh;
+                Fl[ROW_PADL + x] = x == it.L - 1 ? 0.f : zl;
+                zmax = fmaxf(zmax, fmaxf(fabsf(va[k]), fabsf(vb[k])));
+            } else {
+                Fh[ROW_PADL + x] = x == it.L - 1 ? NEG : blend32(va[k], vb[k], fr[k]);
+            }
+        }
+    }
+    for (int m = lane; m < ROW_PADR; m += 32) {
+        if (!in_range(ROW_PADL + it.L + m, sp.half, 4)) continue;
+        Fh[ROW_PADL + it.L + m] = NEG;
+        if (CERT) Fl[ROW_PADL + it.L + m] = 0.f;
+    }
+    if (CERT) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
+    }
+    return zmax;
+}
+
+// ------------------------------------------------ FP32-decision sweep --
+__device__ __forceinline__ float fset_gt(float a, float b)
+{
+    // 1.0f if a > b (strict; false for NaN), else 0.0f
+    float v;
+    asm("set.gt.f32.f32 %0, %1, %2;" : "=f"(v) : "f"(a), "f"(b));
+    return v;
+}
+
+// Distance entry (1/d, 1/d, 2d + 1, 2d + 1) as the table holds it.
+__device__ __forceinline__ float4 dist_entry(int d)
+{
+    const float r = __frcp_rn((float)d);
+    const float c = (float)(2 * d + 1);
+    return make_float4(r, r, c, c);
+}
+
+// U steps of one lane's P POVs.  POV q at step u (distance d = e + 1 + u)
+// sees target w[q + u + 1]; its slope is (target - h_q) * (1/d) in single
+// precision, it is visible iff that slope is strictly above the running
+// maximum M_q, and a visible target adds 2d + 1 to the POV's measure.  Two
+// POVs share one packed multiply and one packed accumulate; the comparison and
+// the maximum are scalar.  tab[u] holds (1/d, 1/d, 2d + 1, 2d + 1); a
+// range-limited walk's last block counts only its first `nvalid` steps.
+// With FAR the block's entries are computed (distances e + 1 .. e + U, past
+// the end of a capped table) instead of read from tab[0 .. U).
+template <int P, int U, bool MASKED, bool FAR>
+__device__ __forceinline__ void sweep_block(const float* w, const float4* __restrict__ tab, int e, const float* h,
+                                            float* M, float2* acc2, int nvalid)
+{
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const float4 t4 = FAR ? dist_entry(e + u + 1) : tab[u];
+        const float2 iv = make_float2(t4.x, t4.y);
+        float2 cpair = make_float2(t4.z, t4.w);
+        if (MASKED && u >= nvalid) cpair = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < P; q += 2) {
+            const float2 d = make_float2(__fsub_rn(w[q + u + 1], h[q]), __fsub_rn(w[q + u + 2], h[q + 1]));
+            const float2 t = __fmul2_rn(d, iv);
+            const float2 v = make_float2(fset_gt(t.x, M[q]), fset_gt(t.y, M[q + 1]));
+            acc2[q / 2] = __ffma2_rn(v, cpair, acc2[q / 2]);
+            M[q] = fmaxf(M[q], t.x);
+            M[q + 1] = fmaxf(M[q + 1], t.y);
+        }
+    }
+}
+
+// Walks of more than LONG_WALK steps (rows longer than the constant, with a
+// range beyond it) move their FP32 partial measures into integers every
+// FLUSH_STEPS steps: a measure is a sum of odd integers 2d + 1 and stays exact
+// in FP32 only below 2^24 (a walk of D steps sums to at most D^2 + 2D, and
+// FLUSH_STEPS steps at d < 16384 add at most 1.1e7).  Shorter walks never
+// flush (the LONG = false instantiation).
+constexpr int LONG_WALK = 4000;
+constexpr int FLUSH_STEPS = 336;   // a multiple of SMALL_UNROLL and LARGE_UNROLL
+// Suffix maxima of a staged row are kept at every ZS_STRIDE-th sample; pruning
+// checks every PRUNE_EVERY blocks.
+constexpr int ZS_STRIDE = 4;
+constexpr int PRUNE_EVERY = 1;
+
+// A warp item is one skewed row and one walk direction.  Its G groups of P
+// consecutive POVs are taken in order (longest walks first) from a warp-local
+// queue by whichever lane is free, so lanes stay busy whatever the walk
+// lengths (and wherever pruning ends a walk early).  F holds the row (or the
+// reversed row for backward walks) with -inf at its last sample and after it:
+// the last target of a walk never adds area (its segment closes there), so it
+// may be a sentinel that is never visible.  A walk's measure is
+// cv = 1 + sum_{d=1}^{n-1} v_d (2d + 1) for n >= 1 targets, which is Alg. 8's
+// sum of d^2 - open^2 over its closed segments plus the segment still open at
+// the end (closed at the last target).
+//
+// PRUNE (exact horizon pruning): every PRUNE_EVERY blocks a lane stops its
+// group's walks once min_q M_q >= B, B = fl(A * (1/d)) if A >= 0 else 0, where
+// d is the next target distance and A = fl(Zmax - min_q h_q) with Zmax an upper
+// bound of every remaining target (the suffix maximum ZS).  Rounding to nearest
+// is monotone, so every remaining slope fl(fl(z - h_q) * fl(1/d')) is at most
+// fl(A * fl(1/d)) when A >= 0 (d' >= d) and at most 0 when A < 0: no remaining
+// target can be strictly above its POV's running maximum, and the walk's
+// measure is already complete.  The result is bit for bit the same.
+//
+// With LONG, `spill` is the lane's column (stride 32) of P integers.
+template <int P, int U, bool LONG, bool PRUNE>
+__device__ __forceinline__ void sweep_row(const float* __restrict__ F, const float* __restrict__ ZS,
+                                          const float4* __restrict__ tab, int tabn, int* __restrict__ cvrow,
+                                          int* __restrict__ spill, int L, int K, float h0, bool rev, int lane)
+{
+    // the window is read as float4 from F + ROW_PADL + x0 + e (x0 = g P, e a
+    // multiple of U): both must keep it 16-byte aligned
+    static_assert(P % 4 == 0 && U % 4 == 0, "window loads must stay 16-byte aligned");
+    const unsigned FULL = 0xffffffffu;
+    const unsigned below = (1u << lane) - 1u;
+    const float NEG = neg_inf();
+    const int G = (L + P - 1) / P;
+    const int klim = K - 1;          // last target distance that still adds area
+    float h[P], M[P];
+    float2 acc2[P / 2];
+    float hmin = 0.f;
+    int g = lane, next = 32;         // the lane's group; the first group nobody has taken
+    int x0 = 0, e = 0, dlim = -1, seg = FLUSH_STEPS;
+    int pc = 1;                      // blocks until the next pruning check
+    bool klimited = false;
+
+    auto start = [&]() {
+        x0 = g * P;
+        const int rowlim = L - 2 - x0;   // last target adding area, POV q = 0
+        dlim = min(klim, rowlim);
+        klimited = klim < rowlim;
+        e = 0;
+        seg = FLUSH_STEPS;
+        pc = 1;
+#pragma unroll
+        for (int q = 0; q < P; ++q) { h[q] = __fadd_rn(F[ROW_PADL + x0 + q], h0); M[q] = NEG; }
+#pragma unroll
+        for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+        if (PRUNE) {
+            hmin = h[0];
+#pragma unroll
+            for (int q = 1; q < P; ++q) hmin = fminf(hmin, h[q]);
+        }
+        if (LONG) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) spill[32 * q] = 0;
+        }
+    };
+    if (g < G) start();
+    for (;;) {
+        const bool fin = g < G && e >= dlim;
+        const unsigned need = __ballot_sync(FULL, fin);
+        if (need) {
+            if (fin) {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int x = x0 + q;
+                    if (x < L) {
+                        const int n = min(L - 1 - x, K);
+                        const float s = q % 2 ? acc2[q / 2].y : acc2[q / 2].x;
+                        cvrow[rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)s + (LONG ? spill[32 * q] : 0) : 0;
+                    }
+                }
+            }
+            if (fin) {
+                g = next + __popc(need & below);
+                if (g < G) start(); else g = G;
+            }
+            next += __popc(need);
+            if (!__any_sync(FULL, g < G)) break;
+            continue;
+        }
+        if (g < G) {
+            if (LONG && e >= seg) {
+                seg += FLUSH_STEPS;
+#pragma unroll
+                for (int q = 0; q < P; q += 2) {
+                    spill[32 * q] += __float2int_rz(acc2[q / 2].x);
+                    spill[32 * (q + 1)] += __float2int_rz(acc2[q / 2].y);
+                    acc2[q / 2] = make_float2(0.f, 0.f);
+                }
+            }
+            if (PRUNE && --pc < 0) {
+                pc = PRUNE_EVERY - 1;
+                const float A = __fsub_rn(ZS[(x0 + e + 1) / ZS_STRIDE], hmin);
+                const float rd = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tab[e].x;
+                const float B = A >= 0.f ? __fmul_rn(A, rd) : 0.f;
+                float m = M[0];
+#pragma unroll
+                for (int q = 1; q < P; ++q) m = fminf(m, M[q]);
+                if (m >= B) { e = dlim; continue; }
+            }
+            const float* base = F + ROW_PADL + x0 + e;
+            float w[P + U];
+#pragma unroll
+            for (int m = 0; m < P + U; m += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(base + m);
+                w[m] = v.x; w[m + 1] = v.y; w[m + 2] = v.z; w[m + 3] = v.w;
+            }
+            // long walks may run past a capped distance table (LONG only)
+            const bool far = LONG && e + U > tabn;
+            if (klimited && e + U > dlim) {
+                if (far) sweep_block<P, U, true, true>(w, tab, e, h, M, acc2, dlim - e);
+                else sweep_block<P, U, true, false>(w, tab + e, e, h, M, acc2, dlim - e);
+            } else {
+                if (far) sweep_block<P, U, false, true>(w, tab, e, h, M, acc2, U);
+                else sweep_block<P, U, false, false>(w, tab + e, e, h, M, acc2, U);
+            }
+            e += U;
+        }
+    }
+}
+
+// Suffix maxima of the staged row F (L samples, -inf from L - 1 on) at every
+// ZS_STRIDE-th sample: ZS[j] = max F[x] over x >= ZS_STRIDE * j, for
+// j <= (L - 1) / ZS_STRIDE.  Lane l scans its own segment, a warp scan joins
+// the segments.
+__device__ __forceinline__ void suffix_max(const float* __restrict__ F, float* __restrict__ ZS, int L, int lane)
+{
+    const float NEG = neg_inf();
+    const int seglen = ((L + 31) / 32 + ZS_STRIDE - 1) / ZS_STRIDE * ZS_STRIDE;
+    const int a = lane * seglen, b = min(a + seglen, L);
+    float m = NEG;
+    for (int x = b - 1; x >= a; --x) m = fmaxf(m, F[ROW_PADL + x]);
+    // inclusive suffix scan of the segment maxima over the lanes
+    float s = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_down_sync(0xffffffffu, s, o);
+        if (lane + o < 32) s = fmaxf(s, t);
+    }
+    float after = __shfl_down_sync(0xffffffffu, s, 1);   // maximum of the following segments
+    if (lane == 31) after = NEG;
+    float run = after;
+    for (int x = b - 1; x >= a; --x) {
+        run = fmaxf(run, F[ROW_PADL + x]);
+        if (x % ZS_STRIDE == 0) ZS[x / ZS_STRIDE] = run;   // x / ZS_STRIDE <= (L - 1) / ZS_STRIDE < zs_len
+    }
+}
+
+// ------------------------------------------------ certified decisions --
+//
+// The fast path of a group of P POVs x0 .. x0 + P - 1 works on differences
+// against the group's reference R = z(x0) (a double-float): per block it
+// forms, for every target t of its window, y_t = fl(fl(zh_t - Rh) + fl(zl_t -
+// Rl)), and per POV q once g_q = fl(fl(fl(zh_q - Rh) + fl(zl_q - Rl)) + h0).
+// Then, for POV q and target t at distance d,
+//     diff = fl(y_t - g_q),  x = fl(diff * fl(1/d)),  s = fl(x - M_q),
+// visible iff s > 0 (the sign of s is exact), M_q = max(M_q, x).
+//
+// Error bound (u = 2^-24; D = z_t - h_q exact, theta = D / d, G = h_q - R):
+//   |y_t - (z_t - R)| <= 2u |z_t - R| + 2 eta,  |g_q - G| <= 3.01u |G| +
+//   2.01u |h0| + |h0 - float(h0)| + 2 eta  (eta: the staged heights' error),
+//   so |diff - D| <= 3.01u |D| + Eg with Eg = 5.02u |G| + 2.01u |h0| +
+//   |h0 - float(h0)| + 4 eta, and |x - theta| <= 5.04u |theta| + 1.01 Eg / d.
+// M_q is the x of the last visible target a (the maximum is exact), so with
+// every earlier decision right, comparing x_t with M_q errs by at most
+//   5.04u (|theta_t| + |theta_a|) + 1.01 Eg (1/d_t + 1/d_a).
+// When |s| >= delta the decision is right as soon as
+//   delta (1 - u)(1 - 5.05u) >= 10.1u |M| + 1.02 Eg (1/d_t + 1/d_a)
+// (|theta| <= |x| (1 + 5.1u) + Eg / d, |x_t| <= |M| + |x_t - M|).  Per block
+// and POV the kernel takes
+//   delta = CERT_REL * Mb + CERT_ABS * Eg' * (1/(e+1) + ia) + CERT_FLOOR,
+// with Mb >= |M| over the whole block (|M| at its start, or the block
+// window's largest possible slope Bw when M can rise that far), 1/(e+1) >=
+// 1/d_t, ia >= 1/d_a (1/(e'+1) of the last block e' in which M rose; 1 at
+// first), Eg' >= Eg from the group's largest |g_q|.  Induction over the
+// targets then makes every unflagged decision the exact one.  A POV with a
+// step inside its margin is flagged: its fast-path measure is discarded and
+// it is walked again exactly.
+constexpr float CERT_REL = 10.2f * 0x1p-24f * 1.01f;
+constexpr float CERT_ABS = 1.03f * 1.01f;
+constexpr float CERT_FLOOR = 0x1p-99f;
+// Window maxima WM[k] = max Fh over [4k, 4k + WM_SPAN): a block window starts
+// at a multiple of 4 and reaches at most P + U - 1 <= WM_SPAN - 1 samples on.
+constexpr int WM_SPAN = 40;
+static_assert(LARGE_POV + LARGE_UNROLL <= WM_SPAN && SMALL_POV + SMALL_UNROLL <= WM_SPAN, "window span");
+static_assert(WM_SPAN + 4 <= ROW_PADR, "window maxima read into the right pad");
+// Entries of a warp's flagged-POV list (at least 32 lanes x LARGE_POV).
+constexpr int FLAG_CAP = 256;
+// Targets per lane per chunk of an exact walk.
+constexpr int XW_KPL = 8;
+
+// 1.0f if s >= 2^-100 (s > 0 and outside every margin, which is at least
+// CERT_FLOOR), 0.0f if s <= 0, a fraction only inside the margin.
+__device__ __forceinline__ float sat_pos(float s)
+{
+    float v;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(v) : "f"(s), "f"(0x1p100f), "f"(0.0f));
+    return v;
+}
+
+__device__ __forceinline__ void window_max(const float* __restrict__ H, float* __restrict__ WM, int L, int half,
+                                           int wm_len, int lane)
+{
+    const float NEG = neg_inf();
+    const int nk = (L + 3) / 4;
+    for (int k = lane; k < nk; k += 32) {
+        float m = NEG;
+#pragma unroll
+        for (int i = 0; i < WM_SPAN; i += 4) {
+            if (!in_range(ROW_PADL + 4 * k + i + 3, half, 5)) continue;
+            const float4 v = *reinterpret_cast<const float4*>(H + 4 * k + i);
+            m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
+        }
+        if (in_range(k, wm_len, 6)) WM[k] = m;
+    }
+}
+
+// What the exact walks of a row need.
+struct ExactCtx {
+    const float* H;      // staged hi parts (index 0 = first sample)
+    const float* Lo;     // staged lo parts
+    int L, K;
+    float h0h, h0l;      // h0 = h0h + h0l (to 2^-48)
+    float eta;           // bound of the staged heights' error, plus h0's split
+    int* cvrow;
+    bool rev;
+    const DirDev* dir;
+    const JobDev* job;
+    int p, jlo;
+    int half;            // floats of a staged row array (index bound, with ROW_PADL)
+    int zs_len, wm_len;  // entries of the suffix and window maxima
+};
+
+// Double-float slope (z - h) / d of a staged target against the observer h.
+__device__ __forceinline__ void df_slope(float zh, float zl, float hh, float hl, int d, float& qh, float& ql)
+{
+    float s, e;
+    two_sum(zh, -hh, s, e);
+    e = __fadd_rn(e, __fsub_rn(zl, hl));
+    float Dh, Dl;
+    two_sum(s, e, Dh, Dl);
+    const float fd = (float)d;
+    const float iv = __frcp_rn(fd);
+    const float q1 = __fmul_rn(Dh, iv);
+    const float ph = __fmul_rn(q1, fd);
+    const float pl = __fmaf_rn(q1, fd, -ph);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(Dh, ph), pl), Dl);
+    fast_two_sum(q1, __fmul_rn(r, iv), qh, ql);
+}
+
+// FP64 height of staged sample xs exactly as the FP64 definition forms it:
+// (1 - r) * a + r * b with r = fr / 2^32, every operation rounded.
+__device__ __forceinline__ double z64_at(const ExactCtx& c, int xs)
+{
+    const DirDev& d = *c.dir;
+    const int j = c.jlo + (c.rev ? c.L - 1 - xs : xs);
+    const unsigned long long y = (unsigned long long)j * d.t_fx;
+    const int a = c.p - d.D + (int)(y >> 32);
+    const unsigned fr = (unsigned)y;
+    int st;
+    const long long idx = view_index(d, c.job->cols, a, j, &st);
+    const long long cells = (long long)c.job->rows * c.job->cols;
+    if (!in_range(idx, cells, 16) || (fr != 0u && !in_range(idx + st, cells, 17))) return 0.0;
+    const double lo = (double)c.job->dem[idx];
+    if (fr == 0u) return lo;
+    const double hi = (double)c.job->dem[idx + st];
+    const double r = __dmul_rn((double)fr, 0x1p-32);
+    return __dadd_rn(__dmul_rn(__dsub_rn(1.0, r), lo), __dmul_rn(r, hi));
+}
+
+__device__ __forceinline__ int warp_sum(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The FP64 walk of POV x (Alg. 8 in double precision: theta = (z - h) / d
+// rounded once, strict comparison with the running maximum): sum of 2d + 1
+// over the visible targets d = 1 .. last.  Warp-cooperative: 32 x XW_KPL
+// targets per chunk, a warp max-scan gives each lane the running maximum
+// before its first target.
+__device__ __noinline__ int fp64_walk(const ExactCtx& c, int x, int last, int lane)
+{
+    const double h = __dadd_rn(z64_at(c, x), c.job->h0);
+    double run = -__longlong_as_double(0x7ff0000000000000LL);
+    int acc = 0;
+    for (int base = 1; base <= last; base += 32 * XW_KPL) {
+        double th[XW_KPL];
+        double m = run;
+        const int d0 = base + lane * XW_KPL;
+#pragma unroll
+        for (int k = 0; k < XW_KPL; ++k) {
+            const int d = d0 + k;
+            th[k] = d <= last ? __ddiv_rn(__dsub_rn(z64_at(c, x + d), h), (double)d) : run;
+            m = fmax(m, th[k]);
+        }
+        double incl = m;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl = fmax(incl, t);
+        }
+        double cur = __shfl_up_sync(0xffffffffu, incl, 1);
+        if (lane == 0) cur = run;
+        cur = fmax(cur, run);
+#pragma unroll
+        for (int k = 0; k < XW_KPL; ++k) {
+            const int d = d0 + k;
+            if (d > last) break;
+            if (th[k] > cur) { acc += 2 * d + 1; cur = th[k]; }
+        }
+        run = fmax(run, __shfl_sync(0xffffffffu, incl, 31));
+    }
+    return warp_sum(acc);
+}
+
+// The double-float walk of POV x: the same sum, with every decision proved by
+// a margin (slope error <= 2^-45 |theta| + eta / d each); a decision inside
+// its margin sets *esc and the FP64 walk decides instead.
+__device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane, bool* esc_out)
+{
+    const float NEG = neg_inf();
+    float hh, hl;
+    {
+        float s, e;
+        two_sum(c.H[x], c.h0h, s, e);
+        e = __fadd_rn(e, __fadd_rn(c.Lo[x], c.h0l));
+        two_sum(s, e, hh, hl);
+    }
+    float rh = NEG, rl = 0.f;
+    int rd = 1;
+    int acc = 0;
+    bool esc = false;
+    for (int base = 1; base <= last; base += 32 * XW_KPL) {
+        float th[XW_KPL], tl[XW_KPL];
+        float mh = NEG, ml = 0.f;
+        int md = 1;
+        const int d0 = base + lane * XW_KPL;
+#pragma unroll
+        for (int k = 0; k < XW_KPL; ++k) {
+            const int d = d0 + k;
+            th[k] = NEG; tl[k] = 0.f;
+            if (d <= last && in_range(ROW_PADL + x + d, c.half, 15)) {
+                df_slope(c.H[x + d], c.Lo[x + d], hh, hl, d, th[k], tl[k]);
+                if (df_gt(th[k], tl[k], mh, ml)) { mh = th[k]; ml = tl[k]; md = d; }
+            }
+        }
+        // inclusive max-scan over the lanes
+        float ph = mh, pl = ml;
+        int pd = md;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float qh = __shfl_up_sync(0xffffffffu, ph, o);
+            const float ql = __shfl_up_sync(0xffffffffu, pl, o);
+            const int qd = __shfl_up_sync(0xffffffffu, pd, o);
+            if (lane >= o && df_gt(qh, ql, ph, pl)) { ph = qh; pl = ql; pd = qd; }
+        }
+        float ch = __shfl_up_sync(0xffffffffu, ph, 1);
+        float cl = __shfl_up_sync(0xffffffffu, pl, 1);
+        int cd = __shfl_up_sync(0xffffffffu, pd, 1);
+        if (lane == 0 || df_gt(rh, rl, ch, cl)) { ch = rh; cl = rl; cd = rd; }
+#pragma unroll
+        for (int k = 0; k < XW_KPL; ++k) {
+            const int d = d0 + k;
+            if (d > last) break;
+            bool v = true;                           // the first target (no earlier one) is visible
+            if (ch > NEG) {
+                float s, e;
+                two_sum(th[k], -ch, s, e);
+                const float dh = __fadd_rn(s, __fadd_rn(e, __fsub_rn(tl[k], cl)));
+                const float marg = __fmaf_rn(0x1p-40f, fabsf(th[k]) + fabsf(ch),
+                                             4.04f * c.eta * (__frcp_rn((float)d) + __frcp_rn((float)cd))) +
+                                   0x1p-120f;
+                if (!(fabsf(dh) > marg)) esc = true;
+                v = dh > 0.f;
+            }
+            if (v) acc += 2 * d + 1;
+            if (df_gt(th[k], tl[k], ch, cl)) { ch = th[k]; cl = tl[k]; cd = d; }
+        }
+        const float lh = __shfl_sync(0xffffffffu, ph, 31);
+        const float ll = __shfl_sync(0xffffffffu, pl, 31);
+        const int ld = __shfl_sync(0xffffffffu, pd, 31);
+        if (df_gt(lh, ll, rh, rl)) { rh = lh; rl = ll; rd = ld; }
+    }
+    *esc_out = __any_sync(0xffffffffu, esc);
+    return warp_sum(acc);
+}
+
+// Exact measure of POV x of the staged row, written by lane 0.
+__device__ __noinline__ void exact_walk(const ExactCtx& c, int x, int lane)
+{
+    const int n = min(c.L - 1 - x, c.K);
+    int cv;
+    if (n < 2) {
+        cv = n < 1 ? 0 : 1;
+    } else {
+        bool esc = false;
+        const int s = df_walk(c, x, n - 1, lane, &esc);
+        cv = 1 + (esc ? fp64_walk(c, x, n - 1, lane) : s);
+    }
+    if (lane == 0 && in_range(x, c.L, 14)) c.cvrow[c.rev ? c.L - 1 - x : x] = cv;
+}
+
+// The warp's list of flagged POVs (positions in the staged row).
+struct FlagList {
+    int* list;
+    int count;
+};
+
+__device__ __noinline__ void drain_flags(FlagList& fl, const ExactCtx& c, int lane)
+{
+    __syncwarp();
+    for (int i = 0; i < fl.count; ++i) exact_walk(c, fl.list[i], lane);
+    fl.count = 0;
+    __syncwarp();
+}
+
+// Warp-collective: appends every lane's flagged POVs (bits of fm, positions
+// x0 + q), first walking the list exactly when it would overflow.
+__device__ __forceinline__ void flag_push(FlagList& fl, const ExactCtx& c, unsigned fm, int x0, int lane)
+{
+    const int cnt = __popc(fm);
+    int incl = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (fl.count + total > FLAG_CAP) drain_flags(fl, c, lane);
+    int pos = fl.count + incl - cnt;
+    for (unsigned m = fm; m; m &= m - 1, ++pos)
+        if (in_range(pos, FLAG_CAP, 13)) fl.list[pos] = x0 + __ffs(m) - 1;
+    fl.count += total;
+    __syncwarp();
+}
+
+// U certified steps of one lane's P POVs (see the derivation above).  y[m] is
+// the window's target x0 + e + m relative to R, g[q] the POV's height relative
+// to R, dl[q] its margin for this block.
+template <int P, int U, bool MASKED, bool FAR>
+__device__ __forceinline__ void cert_block(const float* y, const float4* __restrict__ tab, int e, const float* g,
+                                           float* M, float2* acc2, const float* dl, bool& tie, int nvalid)
+{
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+        const float4 t4 = FAR ? dist_entry(e + u + 1) : tab[u];
+        const float2 iv = make_float2(t4.x, t4.y);
+        float2 cp = make_float2(t4.z, t4.w);
+        if (MASKED && u >= nvalid) cp = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < P; q += 2) {
+            const float2 d = make_float2(__fsub_rn(y[q + u + 1], g[q]), __fsub_rn(y[q + u + 2], g[q + 1]));
+            const float2 x = __fmul2_rn(d, iv);
+            const float2 s = __ffma2_rn(make_float2(-1.f, -1.f), make_float2(M[q], M[q + 1]), x);
+            const float2 v = make_float2(sat_pos(s.x), sat_pos(s.y));
+            acc2[q / 2] = __ffma2_rn(v, cp, acc2[q / 2]);
+            M[q] = fmaxf(M[q], x.x);
+            M[q + 1] = fmaxf(M[q + 1], x.y);
+            tie |= fabsf(s.x) < dl[q];
+            tie |= fabsf(s.y) < dl[q + 1];
+        }
+    }
+}
+
+// Replays one block POV by POV (the same arithmetic) to find which POVs had a
+// step inside their margin.  Rare: only after a block whose lane-level flag
+// was raised.
+template <int P>
+__device__ __noinline__ unsigned cert_recheck(const float* __restrict__ H, const float* __restrict__ Lo, int xe,
+                                              int e, int nsteps, const float4* __restrict__ tab, int tabn,
+                                              float Rh, float Rl, const float* g, const float* Ms, const float* dl,
+                                              int half)
+{
+    unsigned mask = 0u;
+    for (int q = 0; q < P; ++q) {
+        float M = Ms[q];
+        for (int u = 0; u < nsteps; ++u) {
+            const int t = xe + q + u + 1;
+            if (!in_range(ROW_PADL + t, half, 18)) continue;
+            const float yv = __fadd_rn(__fsub_rn(H[t], Rh), __fsub_rn(Lo[t], Rl));
+            const float dv = __fsub_rn(yv, g[q]);
+            const int dd = e + u + 1;
+            const float iv = dd <= tabn ? tab[dd - 1].x : __frcp_rn((float)dd);
+            const float x = __fmul_rn(dv, iv);
+            const float s = __fmaf_rn(-1.f, M, x);
+            if (fabsf(s) < dl[q]) mask |= 1u << q;
+            M = fmaxf(M, x);
+        }
+    }
+    return mask;
+}
+
+// Certified sweep of one staged row (the lane queue of sweep_row).  eg0 =
+// 2.01u |h0| + |h0 - float(h0)| + 4 eta (the parts of Eg that do not depend
+// on the group).  With PRUNE a group stops once, for every POV q, the
+// remaining targets' largest possible exact slope (from the suffix maxima)
+// is at most M_q - 2 delta_q: they are then not above theta_a exactly.
+template <int P, int U, bool LONG, bool PRUNE>
+__device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* __restrict__ ZS,
+                                               const float* __restrict__ WM, const float4* __restrict__ tab,
+                                               int tabn, int* __restrict__ spill, float eg0, FlagList& fl, int lane)
+{
+    static_assert(P % 4 == 0 && U % 4 == 0, "window loads must stay 16-byte aligned");
+    const unsigned FULL = 0xffffffffu;
+    const unsigned below = (1u << lane) - 1u;
+    const float NEG = neg_inf();
+    const float* __restrict__ H = xc.H;
+    const float* __restrict__ Lo = xc.Lo;
+    const int L = xc.L, K = xc.K;
+    const int G = (L + P - 1) / P;
+    const int klim = K - 1;
+    float g[P], M[P], ia[P];
+    float2 acc2[P / 2];
+    float Rh = 0.f, Rl = 0.f, gmin = 0.f, c2e = 0.f;
+    unsigned mask = 0u;
+    int gi = lane, next = 32;
+    int x0 = 0, e = 0, dlim = -1, seg = FLUSH_STEPS;
+    bool klimited = false;
+
+    auto start = [&]() {
+        x0 = gi * P;
+        const int rowlim = L - 2 - x0;
+        dlim = min(klim, rowlim);
+        klimited = klim < rowlim;
+        e = 0;
+        seg = FLUSH_STEPS;
+        mask = 0u;
+#pragma unroll
+        for (int q = 0; q < P / 2; ++q) acc2[q] = make_float2(0.f, 0.f);
+        if (LONG) {
+#pragma unroll
+            for (int q = 0; q < P; ++q) spill[32 * q] = 0;
+        }
+        if (dlim < 1) return;                 // no block runs (x0 <= L - 3 below)
+        if (!in_range(ROW_PADL + x0 + P + 1, xc.half, 19)) {
+            dlim = 0;
+            mask = L - x0 >= P ? (1u << P) - 1u : (1u << (L - x0)) - 1u;   // walked exactly instead
+            return;
+        }
+        Rh = H[x0];
+        Rl = Lo[x0];
+        float gmax = 0.f;
+        gmin = pos_inf();
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            const int x = x0 + q;
+            float gq = 0.f;
+            if (x <= L - 2) {
+                gq = __fadd_rn(__fadd_rn(__fsub_rn(H[x], Rh), __fsub_rn(Lo[x], Rl)), xc.h0h);
+                gmin = fminf(gmin, gq);
+            }
+            g[q] = gq;
+            gmax = fmaxf(gmax, fabsf(gq));
+        }
+        c2e = CERT_ABS * __fmaf_rn(5.1f * 0x1p-24f, gmax, eg0);
+#pragma unroll
+        for (int q = 0; q < P; ++q) {
+            // target 1 (a sentinel, -inf, when the POV has no target adding
+            // area): M starts just below its slope, so that target is visible
+            // and outside its margin, and the maximum then is its slope exactly
+            const int x = x0 + q;
+            const float y1 = __fadd_rn(__fsub_rn(H[x + 1], Rh), __fsub_rn(Lo[x + 1], Rl));
+            const float x1 = __fsub_rn(y1, g[q]);
+            const float C = __fmaf_rn(0x1p-6f, fabsf(x1), __fmaf_rn(4.f, c2e, 0x1p-16f));
+            M[q] = __fsub_rn(x1, C);
+            ia[q] = 1.f;
+        }
+    };
+    if (gi < G) start();
+    for (;;) {
+        const bool fin = gi < G && e >= dlim;
+        const unsigned need = __ballot_sync(FULL, fin);
+        if (need) {
+            if (fin) {
+#pragma unroll
+                for (int q = 0; q < P; ++q) {
+                    const int x = x0 + q;
+                    if (x < L && !((mask >> q) & 1u)) {
+                        const int n = min(L - 1 - x, K);
+                        const float s = q % 2 ? acc2[q / 2].y : acc2[q / 2].x;
+                        xc.cvrow[xc.rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)s + (LONG ? spill[32 * q] : 0) : 0;
+                    }
+                }
+            }
+            const unsigned fm = fin ? mask : 0u;
+            if (__any_sync(FULL, fm != 0u)) flag_push(fl, xc, fm, x0, lane);
+            if (fin) {
+                gi = next + __popc(need & below);
+                if (gi < G) start(); else gi = G;
+            }
+            next += __popc(need);
+            if (!__any_sync(FULL, gi < G)) break;
+            continue;
+        }
+        if (gi < G) {
+            if (LONG && e >= seg) {
+                seg += FLUSH_STEPS;
+#pragma unroll
+                for (int q = 0; q < P; q += 2) {
+                    spill[32 * q] += __float2int_rz(acc2[q / 2].x);
+                    spill[32 * (q + 1)] += __float2int_rz(acc2[q / 2].y);
+                    acc2[q / 2] = make_float2(0.f, 0.f);
+                }
+            }
+            // margins of this block (indices checked: the window's end, the
+            // window and suffix maxima, the distance table when it is read)
+            const bool far = LONG && e + U > tabn;
+            if (!in_range(ROW_PADL + x0 + e + P + U - 1, xc.half, 10) || !in_range((x0 + e) >> 2, xc.wm_len, 8) ||
+                (PRUNE && !in_range((x0 + e + 1) / ZS_STRIDE, xc.zs_len, 9)) ||
+                (!far && !in_range(e + U - 1, tabn, 11))) {
+                e = dlim;
+                mask = L - x0 >= P ? (1u << P) - 1u : (1u << (L - x0)) - 1u;   // walked exactly instead
+                continue;
+            }
+            const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tab[e].x;
+            float Bw = 0.f;
+            {
+                const float wz = WM[(x0 + e) >> 2];
+                if (wz > NEG) {
+                    const float A = __fsub_rn(__fsub_rn(wz, Rh), gmin);
+                    const float sl = 0x1p-20f * (fabsf(wz) + fabsf(Rh) + fabsf(gmin)) + c2e;
+                    Bw = __fmul_rn(fmaxf(__fadd_rn(A, sl), 0.f), ive) * 1.0000039f;
+                }
+            }
+            const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
+            float dl[P], Ms[P];
+#pragma unroll
+            for (int q = 0; q < P; ++q) {
+                Ms[q] = M[q];
+                dl[q] = __fmaf_rn(CERT_REL, fmaxf(fabsf(M[q]), Bw), __fmaf_rn(c2e, ia[q], ce));
+            }
+            if (PRUNE) {
+                const float zs = ZS[(x0 + e + 1) / ZS_STRIDE];
+                float Bp = 0.f;
+                if (zs > NEG) {
+                    const float A = __fsub_rn(__fsub_rn(zs, Rh), gmin);
+                    const float sl = 0x1p-20f * (fabsf(zs) + fabsf(Rh) + fabsf(gmin)) + 2.f * c2e;
+                    Bp = __fmul_rn(fmaxf(__fadd_rn(A, sl), 0.f), ive) * 1.0000039f;
+                }
+                float m = pos_inf();
+#pragma unroll
+                for (int q = 0; q < P; ++q)
+                    if (x0 + q <= L - 2) m = fminf(m, __fmaf_rn(-2.f, dl[q], M[q]));
+                if (m >= Bp) { e = dlim; continue; }
+            }
+            // the window, relative to R
+            float y[P + U];
+            {
+                const float2 nRh = make_float2(-Rh, -Rh), nRl = make_float2(-Rl, -Rl);
+                const float* bh = H + x0 + e;
+                const float* bl = Lo + x0 + e;
+#pragma unroll
+                for (int m = 0; m < P + U; m += 4) {
+                    const float4 a = *reinterpret_cast<const float4*>(bh + m);
+                    const float4 b = *reinterpret_cast<const float4*>(bl + m);
+                    const float2 y0 = __fadd2_rn(__fadd2_rn(make_float2(a.x, a.y), nRh),
+                                                 __fadd2_rn(make_float2(b.x, b.y), nRl));
+                    const float2 y1 = __fadd2_rn(__fadd2_rn(make_float2(a.z, a.w), nRh),
+                                                 __fadd2_rn(make_float2(b.z, b.w), nRl));
+                    y[m] = y0.x; y[m + 1] = y0.y; y[m + 2] = y1.x; y[m + 3] = y1.y;
+                }
+            }
+            bool tie = false;
+            const bool masked = klimited && e + U > dlim;
+            if (masked) {
+                if (far) cert_block<P, U, true, true>(y, tab, e, g, M, acc2, dl, tie, dlim - e);
+                else cert_block<P, U, true, false>(y, tab + e, e, g, M, acc2, dl, tie, dlim - e);
+            } else {
+                if (far) cert_block<P, U, false, true>(y, tab, e, g, M, acc2, dl, tie, U);
+                else cert_block<P, U, false, false>(y, tab + e, e, g, M, acc2, dl, tie, U);
+            }
+            if (tie) {
+                float tg[P], tm[P], td[P];
+#pragma unroll
+                for (int q = 0; q < P; ++q) { tg[q] = g[q]; tm[q] = Ms[q]; td[q] = dl[q]; }
+                mask |= cert_recheck<P>(H, Lo, x0 + e, e, masked ? dlim - e : U, tab, tabn, Rh, Rl, tg, tm, td,
+                                        xc.half);
+            }
+#pragma unroll
+            for (int q = 0; q < P; ++q) ia[q] = M[q] > Ms[q] ? ive : ia[q];
+            e += U;
+        }
+    }
+    if (fl.count > 0) drain_flags(fl, xc, lane);
+}
+
+template <bool LONG, bool PRUNE>
+__device__ __forceinline__ void sweep_item(const ItemRow& it, const float* F, const float* ZS, const float4* tab,
+                                           int tabn, int* cvrow, int* spill, int lane)
+{
+    if (it.pov == SMALL_POV)
+        sweep_row<SMALL_POV, SMALL_UNROLL, LONG, PRUNE>(F, ZS, tab, tabn, cvrow, spill, it.L, it.K, it.h0, it.rev,
+                                                       lane);
+    else
+        sweep_row<LARGE_POV, LARGE_UNROLL, LONG, PRUNE>(F, ZS, tab, tabn, cvrow, spill, it.L, it.K, it.h0, it.rev,
+                                                       lane);
+}
+
+template <bool LONG, bool PRUNE>
+__device__ __forceinline__ void sweep_item_cert(const ItemRow& it, const ExactCtx& xc, const float* ZS,
+                                                const float* WM, const float4* tab, int tabn, int* spill, float eg0,
+                                                FlagList& fl, int lane)
+{
+    if (it.pov == SMALL_POV)
+        sweep_row_cert<SMALL_POV, SMALL_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
+    else
+        sweep_row_cert<LARGE_POV, LARGE_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
+}
+
+// PRUNE: exact horizon pruning; LONG: the launch holds rows with walks of
+// more than LONG_WALK steps (every row then takes the flushing walk); CERT:
+// certified decisions.  Per warp, shared memory holds the staged row (hi
+// parts; CERT: lo parts after them), the suffix maxima (PRUNE), the window
+// maxima and the flagged-POV list (CERT), and the long-walk spill (LONG).
+template <bool PRUNE, bool LONG, bool CERT>
+__global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepParams sp)
+{
+    extern __shared__ __align__(16) float smem[];
+    float4* tab = reinterpret_cast<float4*>(smem);
+    int* istart = reinterpret_cast<int*>(smem + 4 * sp.inv_len);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* Fh = smem + 4 * sp.inv_len + sp.istart_len + warp * sp.per_warp;
+    float* Fl = Fh + sp.half;
+    float* ZS = Fh + (CERT ? 2 : 1) * sp.half;
+    float* WM = ZS + sp.zs_len;
+    int* flist = reinterpret_cast<int*>(WM + sp.wm_len);
+    int* spill = reinterpret_cast<int*>(WM + sp.wm_len) + sp.fl_cap + lane;
+    // per distance d = m + 1: (1/d, 1/d, 2d + 1, 2d + 1); 1/d correctly rounded
+    for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
+        const float r = __frcp_rn((float)(m + 1));
+        const float c = (float)(2 * m + 3);
+        tab[m] = make_float4(r, r, c, c);
+    }
+    for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
+    __syncthreads();
+    FlagList fl{flist, 0};
+
+    int next = 0;
+    if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    for (;;) {
+        const int item = next;
+        if (item >= sp.total_items) break;
+        ItemRow it;
+        const bool nonempty = decode_item(sp, istart, item, &it);
+        if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
+        next = __shfl_sync(0xffffffffu, next, 0);
+        if (!nonempty) continue;
+        __syncwarp();
+        const float zmax = stage_row<CERT>(sp, it, Fh, Fl, lane);
+        __syncwarp();   // the staged row is visible to every lane
+        if (PRUNE) suffix_max(Fh, ZS, it.L, lane);
+        if (CERT) window_max(Fh + ROW_PADL, WM, it.L, sp.half, sp.wm_len, lane);
+        if (PRUNE || CERT) __syncwarp();
+        int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
+        if (CERT) {
+            const DirDev* d = sp.dirs + it.dir;
+            ExactCtx xc;
+            xc.H = Fh + ROW_PADL;
+            xc.Lo = Fl + ROW_PADL;
+            xc.L = it.L;
+            xc.K = it.K;
+            xc.h0h = it.h0;
+            xc.h0l = d->h0_lo;
+            xc.eta = 0x1p-42f * (zmax + fabsf(it.h0)) + 0x1p-126f;
+            xc.cvrow = cvrow;
+            xc.rev = it.rev;
+            xc.dir = d;
+            xc.job = sp.jobs + d->job;
+            xc.p = it.p;
+            xc.jlo = it.jlo;
+            xc.half = sp.half;
+            xc.zs_len = sp.zs_len;
+            xc.wm_len = sp.wm_len;
+            const float u = 0x1p-24f;
+            const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
+            sweep_item_cert<LONG, PRUNE>(it, xc, ZS, WM, tab, sp.inv_len, spill, eg0, fl, lane);
+        } else {
+            sweep_item<LONG, PRUNE>(it, Fh, ZS, tab, sp.inv_len, cvrow, spill, lane);
+        }
+    }
+}
+
+}  // namespace
+
+// A long-walk launch keeps at least this many warps per CTA, shrinking the
+// distance table (to no fewer than MIN_TABLE entries) when both do not fit.
+constexpr int LONG_MIN_WARPS = 2;
+constexpr int MIN_TABLE = 1024;
+
+cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* d_item_start, int ndir,
+                         int total_items, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd, int wmax,
+                         int dmax, int prune, int cert, unsigned* counter, int num_sms, int smem_optin,
+                         int max_warps, cudaStream_t stream)
+{
+    if (ndir <= 0 || total_items <= 0) return cudaSuccess;
+    constexpr int U = LARGE_UNROLL;
+    SweepParams sp;
+    sp.dirs = d_dirs; sp.jobs = d_jobs; sp.item_start = d_item_start; sp.rowlo = rowlo;
+    sp.rowhi = rowhi; sp.cv_fwd = cv_fwd; sp.cv_bwd = cv_bwd; sp.counter = counter; sp.ndir = ndir;
+    sp.total_items = total_items;
+    // the distance table is read up to d = dmax + U (a walk of at most
+    // min(K, W) - 1 steps, rounded up to U); dmax <= wmax
+    sp.inv_len = (std::min(dmax, wmax) + 2 * U + 8 + 1) & ~1;
+    sp.istart_len = (ndir + 1 + 3) & ~3;
+    sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
+    const bool longw = wmax - 2 > LONG_WALK && dmax - 1 > LONG_WALK;
+    sp.zs_len = prune ? ((wmax + ZS_STRIDE - 1) / ZS_STRIDE + 4) & ~3 : 0;
+    sp.wm_len = cert ? ((wmax + 3) / 4 + 4) & ~3 : 0;
+    sp.fl_cap = cert ? FLAG_CAP : 0;
+    sp.per_warp = (cert ? 2 : 1) * sp.half + sp.zs_len + sp.wm_len + sp.fl_cap + (longw ? 32 * LARGE_POV : 0);
+    void (*kern)(SweepParams);
+    if (cert)
+        kern = prune ? (longw ? sweep_kernel<true, true, true> : sweep_kernel<true, false, true>)
+                     : (longw ? sweep_kernel<false, true, true> : sweep_kernel<false, false, true>);
+    else
+        kern = prune ? (longw ? sweep_kernel<true, true, false> : sweep_kernel<true, false, false>)
+                     : (longw ? sweep_kernel<false, true, false> : sweep_kernel<false, false, false>);
+    const size_t per_warp = (size_t)sp.per_warp * 4;
+    size_t fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
+    if (longw && fixed + (size_t)LONG_MIN_WARPS * per_warp > (size_t)smem_optin) {
+        // Rows of more than about 10^4 samples: the whole table and several
+        // staged rows do not fit together.  Keep LONG_MIN_WARPS warps (or as
+        // many as fit) and a table of what is left (at least MIN_TABLE
+        // entries); the long-walk sweep computes the entries past its end.
+        const size_t base = (size_t)sp.istart_len * 4;
+        int w = LONG_MIN_WARPS;
+        while (w > 1 && base + (size_t)MIN_TABLE * 16 + (size_t)w * per_warp > (size_t)smem_optin) --w;
+        if (base + (size_t)w * per_warp >= (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+        const size_t room = ((size_t)smem_optin - base - (size_t)w * per_warp) / 16;
+        sp.inv_len = (int)std::min<size_t>((size_t)sp.inv_len, room) & ~1;
+        fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
+    }
+    if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+    // As many resident warps as shared memory and registers allow, in one CTA per SM
+    // (each warp stages its own row; the 1/d table is shared by the CTA).
+    const int cap = max_warps > 0 ? std::min(max_warps, SWEEP_MAX_WARPS) : SWEEP_MAX_WARPS;
+    int warps = (int)std::min<size_t>((smem_optin - fixed) / per_warp, (size_t)cap);
+    const size_t smem = fixed + (size_t)warps * per_warp;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    int per_sm = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
+    if (err != cudaSuccess) return err;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    kern<<<per_sm * num_sms, warps * 32, smem, stream>>>(sp);
+    return cudaGetLastError();
+}
+
+}  // namespace tvs
+
+extern "C" int tvs_debug_sweep_check(int32_t* out, int clear)
+{
+    if (!out) return TVS_ERR_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, tvs::g_sweep_check, sizeof(int) * 4);
+    if (e == cudaSuccess && clear) {
+        const int zero[4] = {0, 0, 0, 0};
+        e = cudaMemcpyToSymbol(tvs::g_sweep_check, zero, sizeof(zero));
+    }
+    return e == cudaSuccess ? TVS_OK : TVS_ERR_CUDA;
+}

@@ -1,6 +1,7 @@
 """Seeded random cases across shapes, direction counts, ranges, observer
-heights and terrains: the CUDA path against the FP32-decision oracle, and
-pruning on/off and batched/single bit for bit."""
+heights and terrains: certified decisions against the FP64 oracle, FP32
+decisions against the oracle's FP32-decision mode, and pruning on/off and
+batched/single bit for bit."""
 import numpy as np
 import pytest
 
@@ -41,15 +42,18 @@ def ctx():
 
 
 @pytest.mark.parametrize("seed", range(24))
-def test_fuzz_against_fp32_oracle_and_modes(ctx, orc, seed):
+def test_fuzz_against_the_oracle_and_modes(ctx, orc, seed):
     import torch
     dem, step, h0, n, rng_m = _case(seed)
     got = ctx.total_viewshed(dem, step, h0, n, rng_m)
+    o64 = orc.total_viewshed(dem, step, h0, n, rng_m, prec=64)
+    np.testing.assert_allclose(got, o64, rtol=FP32_RTOL, atol=0)
     o32 = orc.total_viewshed(dem, step, h0, n, rng_m, prec=32)
-    np.testing.assert_allclose(got, o32, rtol=FP32_RTOL, atol=0)
     with tvs.Context(0) as c2:
         c2.set_tuning(prune=0)
         assert np.array_equal(c2.total_viewshed(dem, step, h0, n, rng_m), got)
+        c2.set_tuning(fp32_decisions=1)
+        np.testing.assert_allclose(c2.total_viewshed(dem, step, h0, n, rng_m), o32, rtol=FP32_RTOL, atol=0)
     d = torch.from_numpy(dem).cuda()
     other = torch.from_numpy(np.ascontiguousarray(dem[::-1, ::-1])).cuda()
     jobs = [dict(dem=d, out=torch.empty_like(d), step_m=step, obs_height_m=h0, n_sectors=n, max_range_m=rng_m),

@@ -1,20 +1,22 @@
 """GPU parity: the CUDA path (through the C ABI) against the oracle.
 
-Two bars:
-* against the oracle's FP32-decision mode (visibility decided in single
-  precision with the same slope formula, as the paper's kernels declare it:
-  float heights and slopes in Alg. 6-8): integer offsets, row maps and every
-  per-sample cv must be bit-identical, and the per-cell area may differ only
-  by FP32 summation (rtol FP32_RTOL).  Both sides take every visibility
-  decision in the same precision, so this is the parity gate;
-* against the FP64 oracle: the share of cells within 1e-4 (denominator
-  max(|oracle|, step^2)) is reported and bounded below by FP64_SHARE_FLOOR, and
-  every cell within FP64_MAX_REL.  A near-tie between a target's slope and the
-  running maximum decides differently in FP32 and FP64; each such flip moves a
-  half-line's measure by 2d+1, and on paper-scale fractal terrain a few percent
-  of cells (those with small viewsheds) see one that exceeds 1e-4.  With few
-  directions and a short range one flip can move a small viewshed by a few
-  percent, hence FP64_MAX_REL.
+The library takes every visibility decision (Alg. 8's strict comparison of a
+target's elevation angle with the running maximum) one of two ways:
+
+* certified (the default): as exact arithmetic on the blended heights takes
+  it, which is what the FP64 definition decides.  Every per-sample measure cv
+  must equal the FP64 oracle's bit for bit, and every cell's area may differ
+  from the FP64 oracle's only by the single-precision blend and sums of the
+  unskew (rtol FP32_RTOL).  The benchmark spec's tolerance (per-POV relative error
+  <= 1e-4 on 99.9 % of POVs and <= 1e-2 on every POV, denominator
+  max(|oracle|, step^2)) is checked beside it;
+* FP32 decisions (tuning fp32_decisions = 1), as the paper's kernels declare
+  heights and slopes (float in Alg. 6-8): cv bit for bit equal to the
+  oracle's FP32-decision mode (prec = 32), areas within FP32_RTOL of it.  A
+  near-tie between a target's slope and the running maximum decides
+  differently in FP32 and FP64; each such flip moves a half-line's measure by
+  2d + 1, so this mode misses the benchmark spec's tolerance on a few percent of
+  paper-scale cells (reported, not gated).
 """
 import math
 
@@ -29,15 +31,23 @@ pytestmark = pytest.mark.gpu
 # FP32 per-direction blend + FP32 sums over groups of 8 directions: each cell's
 # value carries at most ~10 single-precision roundings relative to the FP64 sum.
 FP32_RTOL = 4e-6
-# Measured lower bound of the share of cells within 1e-4 of the FP64 oracle for
-# FP32 decisions (99.7 % at 100^2, about 97 % at 2000^2).
-FP64_SHARE_FLOOR = 0.95
-FP64_MAX_REL = 5e-2
+# The benchmark spec's bar against the FP64 oracle.
+FP64_SHARE_FLOOR = 0.999
+FP64_MAX_REL = 1e-2
 
 
 @pytest.fixture(scope="module")
 def ctx():
     c = tvs.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx32():
+    """A handle taking FP32 visibility decisions."""
+    c = tvs.Context(0)
+    c.set_tuning(fp32_decisions=1)
     yield c
     c.close()
 
@@ -53,6 +63,13 @@ def assert_fp64_tolerance(got, want, step, floor=FP64_SHARE_FLOOR):
     print(f"vs FP64 oracle: {frac_ok:.5f} of cells within 1e-4, max rel err {e.max():.3g}")
     assert frac_ok >= floor, f"only {frac_ok:.5f} of cells within 1e-4 (max {e.max():.3g})"
     assert e.max() <= FP64_MAX_REL, f"max relative error {e.max():.3g}"
+
+
+def assert_certified(got, o64, step):
+    """Certified decisions: areas equal the FP64 oracle's up to FP32 sums, and
+    therefore meet the benchmark spec's tolerance."""
+    np.testing.assert_allclose(got, o64, rtol=FP32_RTOL, atol=0)
+    assert_fp64_tolerance(got, o64, step)
 
 
 def rand_dem(rows, cols, seed, scale=50.0):
@@ -83,48 +100,70 @@ def test_rowmap_bit_exact(ctx, orc, rows, cols, n, ks):
 
 # ------------------------------------------------- per-sample cv, bit-exact --
 
-def oracle_cv_slab(orc, dem, step, h0, n, rng, k):
+def oracle_cv_slab(orc, dem, step, h0, n, rng, k, prec=64):
     rows, cols = dem.shape
     d = orc.direction(n, k, rows, cols)
     R = d["H"] + d["D"]
-    return np.stack([orc.line_cv(dem, step, h0, n, rng, 32, k, p - d["D"]) for p in range(R)])
+    return np.stack([orc.line_cv(dem, step, h0, n, rng, prec, k, p - d["D"]) for p in range(R)])
+
+
+def both_modes(ctx, ctx32, orc, dem, step, h0, n, rng, k):
+    """Per-sample cv of both decision modes against the matching oracle mode."""
+    for c, prec in ((ctx, 64), (ctx32, 32)):
+        got = c.debug_direction_cv(dem, step, h0, n, rng, k)
+        want = oracle_cv_slab(orc, dem, step, h0, n, rng, k, prec)
+        assert got.shape == want.shape
+        bad = np.argwhere(got != want)
+        assert bad.size == 0, f"prec {prec}: {len(bad)} samples differ, first {bad[:5].tolist()}"
 
 
 @pytest.mark.parametrize("k", [0, 1, 17, 44, 45, 46, 71, 89, 90, 91, 112, 134, 135, 136, 160, 179])
-def test_direction_cv_bit_exact_fp32_oracle(ctx, orc, k):
+def test_direction_cv_bit_exact(ctx, ctx32, orc, k):
     w = terrain.WORKLOADS["tvs100"]
     dem = terrain.workload_dem("tvs100")
-    got = ctx.debug_direction_cv(dem, w["step"], w["h0"], w["n"], 0.0, k)
-    want = oracle_cv_slab(orc, dem, w["step"], w["h0"], w["n"], 0.0, k)
-    assert got.shape == want.shape
-    bad = np.argwhere(got != want)
-    assert bad.size == 0, f"{len(bad)} samples differ, first {bad[:5].tolist()}"
+    both_modes(ctx, ctx32, orc, dem, w["step"], w["h0"], w["n"], 0.0, k)
 
 
 @pytest.mark.parametrize("rows,cols,n,k,rng,h0", [
     (7, 700, 12, 0, 0.0, 1.5), (700, 7, 12, 5, 0.0, 1.5), (40, 600, 24, 3, 37.0, 4.0),
     (600, 40, 24, 20, 90.0, 0.0), (300, 300, 8, 1, 0.0, 2.0), (3, 257, 4, 0, 0.0, 1.0),
 ])
-def test_direction_cv_long_rows_and_range(ctx, orc, rows, cols, n, k, rng, h0):
+def test_direction_cv_long_rows_and_range(ctx, ctx32, orc, rows, cols, n, k, rng, h0):
     """Rows longer than one warp item (256 samples), several items per row,
     and walks cut by the max range (the masked last block)."""
     dem = rand_dem(rows, cols, seed=rows + cols + k)
-    got = ctx.debug_direction_cv(dem, 10.0, h0, n, rng, k)
-    want = oracle_cv_slab(orc, dem, 10.0, h0, n, rng, k)
-    assert np.array_equal(got, want)
+    both_modes(ctx, ctx32, orc, dem, 10.0, h0, n, rng, k)
+
+
+@pytest.mark.parametrize("kind", ["zero", "steps", "ramp"])
+def test_direction_cv_exact_ties(ctx, ctx32, orc, kind):
+    """Terrains built of exact ties (level ground seen from h0 = 0, integer
+    steps, a constant slope): slopes equal to the running maximum are hidden
+    (strict comparison); certified decisions take them exactly, through the
+    double-float and FP64 walks, since no FP32 margin can settle a tie."""
+    rows, cols = 60, 90
+    if kind == "zero":
+        dem, h0 = np.zeros((rows, cols), np.float32), 0.0
+    elif kind == "steps":
+        dem, h0 = (np.random.default_rng(3).integers(0, 4, (rows, cols)) * 2.0).astype(np.float32), 2.0
+    else:
+        dem, h0 = (np.arange(cols, dtype=np.float32)[None, :] * 0.5).repeat(rows, 0), 0.0
+    for k in (0, 3, 9, 12):
+        both_modes(ctx, ctx32, orc, dem, 10.0, h0, 24, 0.0, k)
 
 
 @pytest.mark.parametrize("cols,rng", [(9000, 0.0), (6100, 52000.0)])
-def test_direction_cv_long_walks_stay_exact(ctx, orc, cols, rng):
+def test_direction_cv_long_walks_stay_exact(ctx, ctx32, orc, cols, rng):
     """Walks of several thousand steps on flat ground see every target, so
     their measures reach L^2 (above 2^24, where FP32 sums of odd integers stop
     being exact): the sweep moves its FP32 partial measures into integers
     before that."""
     dem = np.zeros((2, cols), np.float32)
-    got = ctx.debug_direction_cv(dem, 10.0, 1.5, 4, rng, 0)
-    want = oracle_cv_slab(orc, dem, 10.0, 1.5, 4, rng, 0)
-    assert want.max() > 1 << 24
-    assert np.array_equal(got, want)
+    for c, prec in ((ctx, 64), (ctx32, 32)):
+        got = c.debug_direction_cv(dem, 10.0, 1.5, 4, rng, 0)
+        want = oracle_cv_slab(orc, dem, 10.0, 1.5, 4, rng, 0, prec)
+        assert want.max() > 1 << 24
+        assert np.array_equal(got, want)
 
 
 @pytest.mark.parametrize("kind,h0,rng", [("fractal", 1.5, 0.0), ("fractal", 30.0, 900.0), ("spiky", 10.0, 0.0),
@@ -132,7 +171,7 @@ def test_direction_cv_long_walks_stay_exact(ctx, orc, cols, rng):
 def test_pruning_changes_no_bit(ctx, kind, h0, rng):
     """Exact horizon pruning stops walks whose remaining targets cannot rise
     above the running maximum: every per-sample measure and every area is
-    the same with and without it."""
+    the same with and without it, in both decision modes."""
     rows, cols = 230, 170
     if kind == "flat":
         dem = np.zeros((rows, cols), np.float32)
@@ -140,29 +179,32 @@ def test_pruning_changes_no_bit(ctx, kind, h0, rng):
         dem = (np.arange(cols, dtype=np.float32)[None, :] * 3.0).repeat(rows, 0)
     else:
         dem = terrain.fractal_dem(rows, cols, 0.8, 900.0, seed=77, spike_frac=0.05 if kind == "spiky" else 0.0)
-    with tvs.Context(0) as c:
-        c.set_tuning(prune=0)
-        cv0 = [c.debug_direction_cv(dem, 10.0, h0, 36, rng, k) for k in (0, 5, 9, 13, 22, 31)]
-        a0 = c.total_viewshed(dem, 10.0, h0, 36, rng)
-        c.set_tuning(prune=1)
-        cv1 = [c.debug_direction_cv(dem, 10.0, h0, 36, rng, k) for k in (0, 5, 9, 13, 22, 31)]
-        a1 = c.total_viewshed(dem, 10.0, h0, 36, rng)
-    for x, y in zip(cv0, cv1):
-        assert np.array_equal(x, y)
-    assert np.array_equal(a0, a1)
+    for fp32 in (0, 1):
+        with tvs.Context(0) as c:
+            c.set_tuning(prune=0, fp32_decisions=fp32)
+            cv0 = [c.debug_direction_cv(dem, 10.0, h0, 36, rng, k) for k in (0, 5, 9, 13, 22, 31)]
+            a0 = c.total_viewshed(dem, 10.0, h0, 36, rng)
+            c.set_tuning(prune=1)
+            cv1 = [c.debug_direction_cv(dem, 10.0, h0, 36, rng, k) for k in (0, 5, 9, 13, 22, 31)]
+            a1 = c.total_viewshed(dem, 10.0, h0, 36, rng)
+        for x, y in zip(cv0, cv1):
+            assert np.array_equal(x, y)
+        assert np.array_equal(a0, a1)
 
 
 # ---------------------------------------------------------- total viewshed --
 
-def test_tvs100_matches_fp32_oracle_and_fp64_tolerance(ctx, orc):
+def test_tvs100_every_cell(ctx, ctx32, orc):
     """The 100 x 100, 180-direction workload, every cell."""
     w = terrain.WORKLOADS["tvs100"]
     dem = terrain.workload_dem("tvs100")
-    got = ctx.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0)
-    o32 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=32)
-    np.testing.assert_allclose(got, o32, rtol=FP32_RTOL, atol=0)
     o64 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=64)
-    assert_fp64_tolerance(got, o64, w["step"])
+    assert_certified(ctx.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0), o64, w["step"])
+    got32 = ctx32.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0)
+    o32 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=32)
+    np.testing.assert_allclose(got32, o32, rtol=FP32_RTOL, atol=0)
+    e = rel_err(got32, o64, w["step"])
+    print(f"FP32 decisions vs FP64 oracle: {np.mean(e <= 1e-4):.5f} within 1e-4, max {e.max():.3g}")
 
 
 CASES = [
@@ -190,13 +232,12 @@ def make_dem(rows, cols, kind, seed):
 
 
 @pytest.mark.parametrize("rows,cols,n,rng,h0,kind", CASES)
-def test_shapes_edges_and_ranges(ctx, orc, rows, cols, n, rng, h0, kind):
+def test_shapes_edges_and_ranges(ctx, ctx32, orc, rows, cols, n, rng, h0, kind):
     dem = make_dem(rows, cols, kind, seed=rows * 31 + cols)
-    got = ctx.total_viewshed(dem, 10.0, h0, n, rng)
-    o32 = orc.total_viewshed(dem, 10.0, h0, n, rng, prec=32)
-    np.testing.assert_allclose(got, o32, rtol=FP32_RTOL, atol=0)
     o64 = orc.total_viewshed(dem, 10.0, h0, n, rng, prec=64)
-    assert_fp64_tolerance(got, o64, 10.0)
+    assert_certified(ctx.total_viewshed(dem, 10.0, h0, n, rng), o64, 10.0)
+    o32 = orc.total_viewshed(dem, 10.0, h0, n, rng, prec=32)
+    np.testing.assert_allclose(ctx32.total_viewshed(dem, 10.0, h0, n, rng), o32, rtol=FP32_RTOL, atol=0)
 
 
 def test_max_range_below_one_step_gives_zero(ctx):
@@ -276,7 +317,7 @@ def test_profiling_counts_the_work(ctx):
     ctx.profile(False)
     assert st["sweep"]["launches"] == 1 and st["sweep"]["total_ms"] > 0
     assert st["sweep"]["units"] == tvs.count_evals(120, 90, 32, 10.0, 0.0)
-    assert st["skew"]["launches"] == 1 and st["unskew"]["launches"] == 1
+    assert st["unskew"]["launches"] == 1 and "skew" not in st
 
 
 # ------------------------------------------- full-size workloads, sampled --
@@ -287,21 +328,26 @@ def sample_cells(rows, cols, count, seed):
     return np.unique(np.concatenate([edge, rng.choice(rows * cols, size=count, replace=False)]))
 
 
-def test_tvs2000_sampled_parity(ctx, orc):
+def test_tvs2000_sampled_parity(ctx, ctx32, orc):
     """The 2000 x 2000, 180-direction workload on the device path (the launch
-    configuration the benchmark times); 1000 sampled cells against the oracle."""
+    configuration the benchmark times); 1000 sampled cells against the FP64
+    oracle, 300 against the FP32-decision mode."""
     import torch
     w = terrain.WORKLOADS["tvs2000"]
     dem = terrain.workload_dem("tvs2000")
     d = torch.from_numpy(dem).cuda()
     out = ctx.total_viewshed_device(d, w["step"], w["h0"], w["n"], 0.0)
+    out32 = ctx32.total_viewshed_device(d, w["step"], w["h0"], w["n"], 0.0)
     torch.cuda.synchronize()
     got = out.cpu().numpy().reshape(-1)
+    got32 = out32.cpu().numpy().reshape(-1)
     cells = sample_cells(2000, 2000, 1000, seed=11)
     o64 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=64, cells=cells)
-    assert_fp64_tolerance(got[cells], o64, w["step"])
+    assert_certified(got[cells], o64, w["step"])
     o32 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], 0.0, prec=32, cells=cells[:300])
-    np.testing.assert_allclose(got[cells[:300]], o32, rtol=FP32_RTOL, atol=0)
+    np.testing.assert_allclose(got32[cells[:300]], o32, rtol=FP32_RTOL, atol=0)
+    e = rel_err(got32[cells], o64, w["step"])
+    print(f"FP32 decisions vs FP64 oracle: {np.mean(e <= 1e-4):.5f} within 1e-4, max {e.max():.3g}")
     assert np.all(np.isfinite(got)) and got.min() > 0
 
 
@@ -316,25 +362,29 @@ def test_tvs4000_range_limited_sampled_parity(ctx, orc):
     torch.cuda.synchronize()
     got = out.cpu().numpy().reshape(-1)
     cells = sample_cells(4000, 4000, 200, seed=12)
-    o32 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], w["max_range"], prec=32, cells=cells)
-    np.testing.assert_allclose(got[cells], o32, rtol=FP32_RTOL, atol=0)
     o64 = orc.total_viewshed(dem, w["step"], w["h0"], w["n"], w["max_range"], prec=64, cells=cells)
-    assert_fp64_tolerance(got[cells], o64, w["step"])
+    assert_certified(got[cells], o64, w["step"])
     # nothing farther than the range: bounded by the full disc of 10 km radius
     assert got.max() <= math.pi * w["max_range"] ** 2 * 1.01
 
 
 @pytest.mark.parametrize("rows,cols,n", [(3, 16384, 8), (16384, 3, 8)])
-def test_longest_rows_sampled_parity(ctx, orc, rows, cols, n):
+def test_longest_rows_sampled_parity(ctx, ctx32, orc, rows, cols, n):
     """Rows of the longest supported length (16384 samples): walks beyond
     LONG_WALK, measures beyond 2^24, and a distance table too large to stay
     whole beside the staged rows (the sweep computes the entries past it) —
     in a row-major and a transposed view."""
     dem = make_dem(rows, cols, "frac", seed=rows + cols)
-    got = ctx.total_viewshed(dem, 10.0, 1.5, n, 0.0)
     cells = sample_cells(rows, cols, 60, seed=5)
-    o32 = orc.total_viewshed(dem, 10.0, 1.5, n, 0.0, prec=32, cells=cells)
-    np.testing.assert_allclose(got.ravel()[cells], o32, rtol=FP32_RTOL, atol=0)
     o64 = orc.total_viewshed(dem, 10.0, 1.5, n, 0.0, prec=64, cells=cells)
-    rel = np.abs(got.ravel()[cells] - o64) / np.maximum(np.abs(o64), 100.0)
-    assert rel.max() <= FP64_MAX_REL
+    assert_certified(ctx.total_viewshed(dem, 10.0, 1.5, n, 0.0).ravel()[cells], o64, 10.0)
+    o32 = orc.total_viewshed(dem, 10.0, 1.5, n, 0.0, prec=32, cells=cells)
+    np.testing.assert_allclose(ctx32.total_viewshed(dem, 10.0, 1.5, n, 0.0).ravel()[cells], o32,
+                               rtol=FP32_RTOL, atol=0)
+
+
+def test_zz_sweep_index_checks_never_fired():
+    """The sweep checks its staging, margin, list and exact-walk indices
+    against their buffers and records the first violation (skipping the
+    access): after every test above, none may have fired."""
+    assert tvs.sweep_check() == [0, 0, 0, 0]

@@ -16,7 +16,10 @@ FP32_RTOL = 4e-6
 
 @pytest.fixture(scope="module")
 def ctx():
+    # the points walk decides in FP32: its sDEM mode equals the map taken with
+    # FP32 decisions
     c = tvs.Context(0)
+    c.set_tuning(fp32_decisions=1)
     yield c
     c.close()
 
