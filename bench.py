@@ -1,8 +1,9 @@
 #!/usr/bin/env python3
 """Benchmark of the GB300 total viewshed (sDEM method, arXiv 2003.02200).
 
-One step = one whole total viewshed (every direction: skew, sweep, unskew) of
-the 2000 x 2000, 180-direction workload (the paper's DEM10m-2k scale: 10 m
+One step = one whole total viewshed (every direction: row map, sweep with the
+relocation fused into its row staging, unskew) of the 2000 x 2000,
+180-direction workload (the paper's DEM10m-2k scale: 10 m
 step, observers 1.5 m above ground), on a seeded fractal DEM that stands in for
 the paper's dataset.  The metric is G (POV x direction x target) evaluations
 per second, counted exactly from the row maps by the library; DEMs/s is
@@ -37,7 +38,7 @@ from paper_2003_02200_gb300 import terrain  # noqa: E402
 
 METRIC = "G POV*sector*target evals/s"
 UNIT = "Geval/s"
-KERNEL_SRC = os.path.join(ROOT, "paper_2003_02200_gb300", "csrc", "tvs_kernels.cu")
+KERNEL_SRC = os.path.join(ROOT, "paper_2003_02200_gb300", "csrc", "tvs_sweep.cu")
 PROFILES = os.path.join(ROOT, "profiles")
 # FP32 operations one evaluation needs (slope: subtract, multiply; compare; max)
 OPS_PER_EVAL = 4
@@ -54,6 +55,10 @@ def parse_args(argv=None):
                     choices=sorted(terrain.WORKLOADS) + ["batch64", "serve", "points"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="budget of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true", help="skip the oracle baseline (profiling runs)")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="tvs2000: skip the tvs4000 / batch / serve sub-records (profiling runs)")
+    ap.add_argument("--serve-requests", type=int, default=120,
+                    help="default run: requests of the serve sub-record (mean 20 req/s)")
     ap.add_argument("--e2e-steps", type=int, default=None, help="steps of the host-buffer end-to-end run")
     ap.add_argument("--hbm-budget-mb", type=int, default=0,
                     help="device scratch budget of the library handle (0 = library default)")
@@ -178,12 +183,21 @@ def config_of(name: str, w: dict, E: int, world: int) -> dict:
 
 
 def cpu_model() -> str:
-    """The host CPU's model name (first /proc/cpuinfo entry that has one)."""
+    """The host CPU's model name: lscpu's 'Model name' (Arm hosts have no
+    'model name' line in /proc/cpuinfo), else /proc/cpuinfo's."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            key, _, val = line.partition(":")
+            if key.strip() == "Model name" and val.strip() and val.strip() != "-":
+                return val.strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
                 key, _, val = line.partition(":")
-                if key.strip() in ("model name", "Model", "CPU part", "Hardware") and val.strip():
+                if key.strip() in ("model name", "Model") and val.strip():
                     return val.strip()
     except OSError:
         pass
@@ -330,6 +344,32 @@ def run_ours(args) -> int:
     p_evals, p_max = aggregate(float(E) * args.steps, sum(p_ms) / 1e3, dist, device)
     ctx.set_tuning(prune=0)
 
+    # the same unpruned steps with FP32 visibility decisions (the paper's
+    # kernel precision): its rate, its sweep's rate, and how many cells move
+    ctx.set_tuning(fp32_decisions=1)
+    flush.zero_()
+    step()
+    torch.cuda.synchronize(device)
+    diff = (out.double() - ref_out.double()).abs() / ref_out.double().abs().clamp(min=w["step"] ** 2)
+    f32_cells = {"cells_differing": int((out != ref_out).sum().item()),
+                 "cells_over_1e-4": int((diff > 1e-4).sum().item()), "max_rel_diff": float(diff.max().item())}
+    ctx.profile(True)
+    f_ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        step()
+        b.record(stream)
+        b.synchronize()
+        f_ms.append(a.elapsed_time(b))
+    f_stats = ctx.profile_read()
+    ctx.profile(False)
+    ctx.set_tuning(fp32_decisions=0)
+    f_evals, f_max = aggregate(float(E) * args.steps, sum(f_ms) / 1e3, dist, device)
+    f_sweep = f_stats.get("sweep", {})
+    f_sweep_rate = f_sweep["units"] / (f_sweep["total_ms"] / 1e3) if f_sweep.get("total_ms") else 0.0
+
     sweep = stats.get("sweep", {})
     peaks = measured_peaks()
     sm_max_mhz = peaks.get("sm_max_mhz") or (getattr(props, "clock_rate", 0) / 1e3) or 2070.0
@@ -374,7 +414,32 @@ def run_ours(args) -> int:
                    "identical_output": same_pruned,
                    "note": "exact horizon pruning on (the library default): walks stop once no remaining target "
                            "can rise above the running maximum; evaluations counted unpruned, output bit-identical"},
+        "fp32_decisions": {"value": f_evals / f_max / 1e9, "unit": UNIT, "dems_per_s": args.steps * world / f_max,
+                           "ms_per_step": statistics.mean(f_ms), "sweep_geval_per_s": f_sweep_rate / 1e9,
+                           "sweep_frac_of_roofline": f_sweep_rate / peak_evals, **f32_cells,
+                           "note": "the same unpruned steps with FP32 visibility decisions (the paper's kernel "
+                                   "precision, tuning fp32_decisions = 1): near-ties flip against the FP64 "
+                                   "definition; the headline takes certified (exact) decisions"},
     }
+    if world == 1 and not args.no_extras:
+        ctx.close()
+        ctx = None
+        del dem, out, ref_out, flush
+        torch.cuda.empty_cache()
+        line["tvs4000"] = measure_tvs4000(tvs, torch, device, stream, args, peak_evals)
+        line["batch"] = measure_batch(tvs, torch, device, stream, args, autotune=False)
+        sv = measure_serve(tvs, torch, device, args, requests=args.serve_requests, factors=(1.0, 1.25, 1.5),
+                           policies=("deadline",), sweep_plain=False)
+        at = sv["latency_by_rate_hz"][f"{args.rate:g}"]
+        tgt = sv["at_equal_p99"]["targets"][0]
+        sv["summary"] = {
+            "rate_hz": args.rate, "plain": at["plain"], "served": at["served_deadline"],
+            "plain_p99_target_ms": tgt["p99_target_ms"],
+            "served_rate_hz_at_plain_p99": tgt.get("served_deadline_rate_hz"),
+            "saturation_dems_per_s": {k: v["dems_per_s"] for k, v in sv["saturation"].items()},
+            "note": "served = continuous-batching server (deadline policy), plain = one request at a time "
+                    "through tvs_total_viewshed, same page-locked buffers, library defaults on both"}
+        line["serve"] = sv
     if world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(w, dem_np, args.cpu_seconds)
         full_s = s["sec_per_cell"] * w["rows"] * w["cols"]
@@ -383,7 +448,8 @@ def run_ours(args) -> int:
                                 "sample": f"{s['cells']} random cells of the workload (all {w['n']} directions "
                                           f"each, FP64), {s['seconds']:.1f} s, extrapolated by cell count"}
     print(json.dumps(line), flush=True)
-    ctx.close()
+    if ctx is not None:
+        ctx.close()
     return 0
 
 
@@ -420,14 +486,17 @@ def run_reference(args) -> int:
     value = E / full_s / 1e9
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": full_s * 1e3, "higher_is_better": True,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(times) * 1e3,
+        "extrapolated": True, "extrapolated_ms_per_dem": full_s * 1e3, "cells_per_step": n_cells,
+        "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic: seeded spectral-fractal DEM standing in for the paper's DEM10m datasets",
         "config": config_of(args.workload, w, E, world), "dems_per_s": 1.0 / full_s,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": info.get("threads", 1), "kind": "oracle",
                          "cpu_model": cpu_model(),
                          "sample": f"each step: {n_cells} random cells (all {w['n']} directions each, FP64), "
-                                   "extrapolated to the whole DEM by cell count"},
+                                   "timed (ms_per_step) and extrapolated to the whole DEM by cell count "
+                                   "(extrapolated_ms_per_dem, value)"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -436,18 +505,50 @@ def run_reference(args) -> int:
 
 # ------------------------------------------------------------------ batch --
 
-def run_batch_bench(args) -> int:
+def measure_tvs4000(tvs, torch, device, stream, args, peak_evals) -> dict:
+    """The large single-DEM configuration (4000 x 4000 with spikes, 360
+    directions, 10 km range): steps with the library defaults (certified
+    decisions, exact pruning) and one unpruned step for the sweep's rate."""
+    w = workload("tvs4000")
+    dem = torch.from_numpy(terrain.workload_dem("tvs4000")).to(device)
+    out = torch.empty_like(dem)
+    E = tvs.count_evals(w["rows"], w["cols"], w["n"], w["step"], w["max_range"])
+    ctx = tvs.Context(device.index, hbm_budget_bytes=args.hbm_budget_mb << 20)
+
+    def step():
+        ctx.total_viewshed_device(dem, w["step"], w["h0"], w["n"], w["max_range"], out=out, stream=stream)
+
+    def timed(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            step()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / 1e3 / reps
+
+    step()
+    pruned_s = timed(2)
+    ctx.set_tuning(prune=0)
+    ctx.profile(True)
+    unpruned_s = timed(1)
+    st = ctx.profile_read()
+    ctx.close()
+    sw = st.get("sweep", {})
+    rate = sw["units"] / (sw["total_ms"] / 1e3) if sw.get("total_ms") else 0.0
+    return {"config": config_of("tvs4000", w, E, 1)["workload"], "evals_per_dem": E,
+            "dems_per_s": 1.0 / pruned_s, "value": E / pruned_s / 1e9, "unit": UNIT, "ms_per_dem": pruned_s * 1e3,
+            "unpruned": {"dems_per_s": 1.0 / unpruned_s, "value": E / unpruned_s / 1e9,
+                         "sweep_geval_per_s": rate / 1e9, "sweep_frac_of_roofline": rate / peak_evals},
+            "note": "library defaults (certified decisions, exact pruning, 16 GiB scratch budget: chunked); "
+                    "2 timed steps after one warm-up, and one unpruned step"}
+
+
+def measure_batch(tvs, torch, device, stream, args, autotune: bool) -> dict:
     """64 uneven fractal tiles, all directions of all tiles per step, as one
     prepared batch (plan, tables and launch sequence captured once in a CUDA
-    graph, replayed per step), against the same tiles one at a time."""
-    import torch
-
-    import paper_2003_02200_gb300 as tvs
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    dist = dist_init("nccl")
+    graph, replayed per step), against the same tiles one at a time; and 256
+    small tiles the same way."""
     tiles = terrain.batch_tiles(64)
     jobs = []
     E = 0
@@ -456,21 +557,15 @@ def run_batch_bench(args) -> int:
         jobs.append(dict(dem=d, out=torch.empty_like(d), step_m=t["step"], obs_height_m=t["h0"], n_sectors=t["n"],
                          max_range_m=t["max_range"]))
         E += tvs.count_evals(t["rows"], t["cols"], t["n"], t["step"], t["max_range"])
-    ctx = tvs.Context(local, hbm_budget_bytes=args.hbm_budget_mb << 20)
-    tuning, tune_ms = ctx.autotune(jobs)
+    ctx = tvs.Context(device.index, hbm_budget_bytes=args.hbm_budget_mb << 20)
+    tuning = ctx.autotune(jobs)[0] if autotune else ctx.get_tuning()
     batch = ctx.prepare_batch(jobs)
     info = batch.info()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
-    stream = torch.cuda.current_stream(device)
     for _ in range(args.warmup):
         flush.zero_()
         batch.launch(stream)
     torch.cuda.synchronize(device)
-    props = torch.cuda.get_device_properties(device)
-    uuid = getattr(props, "uuid", None)
-    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
-    barrier(dist, device)
-    sampler.start()
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for k in range(args.steps):
@@ -479,51 +574,78 @@ def run_batch_bench(args) -> int:
         batch.launch(stream)
         ends[k].record(stream)
     torch.cuda.synchronize(device)
-    barrier(dist, device)
-    clocks = sampler.stop()
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_evals, max_s = aggregate(float(E) * args.steps, sum(step_ms) / 1e3, dist, device)
     # the same tiles one at a time through the single-DEM entry point
-    single = tvs.Context(local, hbm_budget_bytes=args.hbm_budget_mb << 20)
+    single = tvs.Context(device.index, hbm_budget_bytes=args.hbm_budget_mb << 20)
     single.set_tuning(**tuning)
-    for j in jobs:
-        single.total_viewshed_device(j["dem"], j["step_m"], j["obs_height_m"], j["n_sectors"], j["max_range_m"],
-                                     out=j["out"], stream=stream)
+
+    def one_pass():
+        for j in jobs:
+            single.total_viewshed_device(j["dem"], j["step_m"], j["obs_height_m"], j["n_sectors"],
+                                         j["max_range_m"], out=j["out"], stream=stream)
+
+    one_pass()
     torch.cuda.synchronize(device)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     a.record(stream)
-    for j in jobs:
-        single.total_viewshed_device(j["dem"], j["step_m"], j["obs_height_m"], j["n_sectors"], j["max_range_m"],
-                                     out=j["out"], stream=stream)
+    one_pass()
     b.record(stream)
     torch.cuda.synchronize(device)
     one_s = a.elapsed_time(b) / 1e3
+    mean_s = statistics.mean(step_ms) / 1e3
     small = _small_tiles_batch(tvs, torch, device, stream, args)
+    batch.close()
+    single.close()
+    ctx.close()
+    return {"tiles": len(jobs), "evals_per_step": E, "ms_per_step": statistics.mean(step_ms),
+            "dems_per_s": len(jobs) / mean_s, "value": E / mean_s / 1e9, "unit": UNIT,
+            "one_at_a_time": {"dems_per_s": len(jobs) / one_s, "value": E / one_s / 1e9,
+                              "api": "tvs_total_viewshed_device per tile, same tuning"},
+            "speedup": one_s / mean_s, "chunks": info["chunks"], "kernels_per_step": info["kernels_per_launch"],
+            "scratch_gb": info["scratch_bytes"] / 1e9, "tuning": tuning, "autotuned": autotune,
+            "small_tiles": small}
+
+
+def run_batch_bench(args) -> int:
+    """The batched workload as its own bench line (autotuned)."""
+    import torch
+
+    import paper_2003_02200_gb300 as tvs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    stream = torch.cuda.current_stream(device)
+    props = torch.cuda.get_device_properties(device)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    barrier(dist, device)
+    sampler.start()
+    rec = measure_batch(tvs, torch, device, stream, args, autotune=True)
+    clocks = sampler.stop()
+    total_evals, max_s = aggregate(float(rec["evals_per_step"]) * args.steps, rec["ms_per_step"] * args.steps / 1e3,
+                                   dist, device)
     if rank != 0:
         return 0
-    mean_s = max_s / args.steps
     line = {
         "metric": METRIC, "value": total_evals / max_s / 1e9, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": statistics.mean(step_ms), "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": rec["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32",
         "data": "synthetic: 64 seeded spectral-fractal tiles (side log-uniform 256-1500, Hurst U(0.6,0.9), "
                 "step from {5,10,30} m, observer U(1.5,30) m)",
         "config": {"workload": "batch64: 64 uneven DEM tiles x 180 directions per step, one prepared batch "
-                               "replayed from a CUDA graph", "tiles": len(jobs), "evals_per_step": E,
-                   "chunks": info["chunks"], "kernels_per_step": info["kernels_per_launch"],
-                   "scratch_gb": info["scratch_bytes"] / 1e9, "tuning": tuning,
-                   "l2": "flushed between steps (256 MiB write, outside the step events)"},
-        "dems_per_s": len(jobs) * world / mean_s,
-        "one_at_a_time": {"dems_per_s": len(jobs) / one_s, "value": E / one_s / 1e9, "unit": UNIT,
-                          "api": "tvs_total_viewshed_device per tile, same tuning"},
-        "small_tiles": small,
-        "gpu_launches": info["kernels_per_launch"] * args.steps,
+                               "replayed from a CUDA graph", "tiles": rec["tiles"],
+                   "evals_per_step": rec["evals_per_step"], "chunks": rec["chunks"],
+                   "kernels_per_step": rec["kernels_per_step"], "scratch_gb": rec["scratch_gb"],
+                   "tuning": rec["tuning"], "l2": "flushed between steps (256 MiB write, outside the step events)"},
+        "dems_per_s": rec["tiles"] * world / (max_s / args.steps),
+        "one_at_a_time": rec["one_at_a_time"],
+        "small_tiles": rec["small_tiles"],
+        "gpu_launches": rec["kernels_per_step"] * args.steps,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
-    batch.close()
-    single.close()
-    ctx.close()
     return 0
 
 
@@ -588,25 +710,19 @@ def _rate_at(points, slo):
     return best
 
 
-def run_serve_bench(args) -> int:
+def measure_serve(tvs, torch, device, args, requests: int, factors, policies, sweep_plain: bool = True,
+                  step_evals=(0.0,)) -> dict:
     """A seeded Poisson stream of total-viewshed requests (sides log-uniform
     128-2048, 90/180/360 directions, observer 1.5-30 m, unlimited or 5 km range)
     served on the same GPU from the same page-locked host buffers by the
     request server (continuous batching under an 80 GB budget; each policy of
-    --policies) and by the plain path (one worker calling tvs_total_viewshed
-    per request in arrival order).  Each offered rate of the sweep replays the
-    stream with its arrival times scaled; latency = completion - scheduled
-    arrival.  Saturation throughput replays it with every request arriving at
-    once.  The library defaults hold on both arms (exact horizon pruning on)."""
-    import torch
-
-    import paper_2003_02200_gb300 as tvs
-
-    world, rank, local = dist_env()
-    torch.cuda.set_device(local)
-    device = torch.device("cuda", local)
-    dist = dist_init("nccl")
-    reqs = terrain.request_stream(args.requests, rate_hz=args.rate)
+    `policies`) and by the plain path (one worker calling tvs_total_viewshed
+    per request in arrival order).  Each offered rate (args.rate x factor)
+    replays the stream with its arrival times scaled (the plain path at every
+    factor with sweep_plain, else at the first only); latency = completion -
+    scheduled arrival.  Saturation throughput replays it with every request
+    arriving at once.  The library defaults hold on both arms."""
+    reqs = terrain.request_stream(requests, rate_hz=args.rate)
     dems, outs = [], []
     for r in reqs:
         d = torch.from_numpy(terrain.fractal_dem(r["rows"], r["cols"], r["hurst"], r["relief"], r["seed"]))
@@ -614,18 +730,16 @@ def run_serve_bench(args) -> int:
         outs.append(torch.empty_like(d).pin_memory().numpy())
     evals = [tvs.count_evals(r["rows"], r["cols"], r["n"], r["step"], r["max_range"]) for r in reqs]
     arrivals = [r["arrival"] for r in reqs]
-    policies = [p.strip() for p in args.policies.split(",") if p.strip()]
-    steps_list = [float(x) for x in str(args.step_evals).split(",") if x.strip()]
     # one server holds the 80 GB budget of the workload; several arms split 60 % of free memory
-    narms = len(policies) * len(steps_list)
+    narms = len(policies) * len(step_evals)
     free = torch.cuda.mem_get_info(device)[0]
     budget = (80 << 30) if narms == 1 else int(0.6 * free / narms) & ~((1 << 20) - 1)
     servers = {}
     for p in policies:
-        for se in steps_list:
-            key = p if len(steps_list) == 1 else f"{p}_{se:.0e}".replace("+", "")
-            servers[key] = tvs.Server(local, hbm_budget_bytes=budget, step_evals=se, policy=p)
-    ctx = tvs.Context(local, hbm_budget_bytes=args.hbm_budget_mb << 20)
+        for se in step_evals:
+            key = p if len(step_evals) == 1 else f"{p}_{se:.0e}".replace("+", "")
+            servers[key] = tvs.Server(device.index, hbm_budget_bytes=budget, step_evals=se, policy=p)
+    ctx = tvs.Context(device.index, hbm_budget_bytes=args.hbm_budget_mb << 20)
 
     def served(srv, scale):
         t0 = time.perf_counter()
@@ -667,18 +781,14 @@ def run_serve_bench(args) -> int:
         ctx.total_viewshed(dems[i], r["step"], r["h0"], r["n"], r["max_range"], out=outs[i])
         for srv in servers.values():
             srv.wait(srv.submit(dems[i], r["step"], r["h0"], r["n"], r["max_range"], out=outs[i]))
-    props = torch.cuda.get_device_properties(device)
-    uuid = getattr(props, "uuid", None)
-    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
-    barrier(dist, device)
-    sampler.start()
     st0 = {p: srv.stats() for p, srv in servers.items()}
     ctx.profile(True)
-    factors = [float(x) for x in args.rate_factors.split(",") if x.strip()]
     sweep = {}
-    for f in factors:
+    for k, f in enumerate(factors):
         row = {}
         for name, fn in arms.items():
+            if name == "plain" and not sweep_plain and k > 0:
+                continue
             lat, span = fn(1.0 / f)
             row[name] = {"p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99), "dems_per_s": len(reqs) / span}
         sweep[f"{args.rate * f:g}"] = row
@@ -687,52 +797,82 @@ def run_serve_bench(args) -> int:
         lat, span = fn(0.0)
         sat[name] = {"dems_per_s": len(reqs) / span, "evals_per_s": sum(evals) / span, "makespan_s": span,
                      "p50_ms": 1e3 * _pct(lat, 50), "p99_ms": 1e3 * _pct(lat, 99)}
-    clocks = sampler.stop()
     st1 = {p: srv.stats() for p, srv in servers.items()}
     plain_launches = sum(v["launches"] for v in ctx.profile_read().values())
-    barrier(dist, device)
+    # for each rate the plain path was swept at, its p99 there as the latency
+    # target and the offered rate every server arm sustains within it
+    equal_p99 = {"basis": "target = the plain path's p99 at a swept rate; for each server arm the highest offered "
+                          "rate whose p99 stays within the target, interpolated linearly between swept rates",
+                 "targets": []}
+    curves = {name: sorted((float(k), v[name]["p99_ms"]) for k, v in sweep.items() if name in v) for name in arms}
+    for rate, row in sorted(sweep.items(), key=lambda kv: float(kv[0])):
+        if "plain" not in row:
+            continue
+        slo = row["plain"]["p99_ms"]
+        equal_p99["targets"].append({"plain_rate_hz": float(rate), "p99_target_ms": slo,
+                                     **{f"{name}_rate_hz": _rate_at(curves[name], slo) for name in arms
+                                        if name != "plain"}})
     best_served = max((k for k in sat if k.startswith("served")), key=lambda k: sat[k]["dems_per_s"])
-    tot_e, max_s = aggregate(float(sum(evals)), sat[best_served]["makespan_s"], dist, device)
-    if rank == 0:
-        # for each swept rate, the plain path's p99 there as the latency target and
-        # the offered rate every arm sustains within it
-        equal_p99 = {"basis": "target = the plain path's p99 at a swept rate; for each arm the highest offered "
-                              "rate whose p99 stays within the target, interpolated linearly between swept rates",
-                     "targets": []}
-        curves = {name: sorted((float(k), v[name]["p99_ms"]) for k, v in sweep.items()) for name in arms}
-        for rate, row in sorted(sweep.items(), key=lambda kv: float(kv[0])):
-            slo = row["plain"]["p99_ms"]
-            equal_p99["targets"].append({"plain_rate_hz": float(rate), "p99_target_ms": slo,
-                                         **{f"{name}_rate_hz": _rate_at(curves[name], slo) for name in arms
-                                            if name != "plain"}})
-        line = {
-            "metric": METRIC, "value": tot_e / max_s / 1e9, "unit": UNIT, "n_gpus": world,
-            "steps": len(factors) * len(arms) + len(arms), "warmup": len(order), "ms_per_step": None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": f"synthetic: {len(reqs)} seeded Poisson requests (mean {args.rate:g}/s) on spectral-fractal "
-                    "DEMs, side log-uniform 128-2048, n from {90,180,360}, observer U(1.5,30) m, range "
-                    "{unlimited, 5 km}, step {5,10,30} m",
-            "config": {"workload": "serve: request stream through the continuous-batching server vs the "
-                                   "plain one-at-a-time path", "requests": len(reqs),
-                       "evals_total": sum(evals), "server_arms": list(servers), "headline_arm": best_served,
-                       "step_evals": steps_list,
-                       "server_budget_gb": budget / 1e9,
-                       "server_arena_gb": next(iter(st1.values()))["arena_bytes"] / 1e9,
-                       "lanes": next(iter(st1.values()))["lanes"],
-                       "host_buffers": "page-locked", "pruning": "on (library default) on every arm"},
-            "dems_per_s": len(reqs) * world / max_s,
-            "saturation": sat,
-            "latency_by_rate_hz": sweep,
-            "at_equal_p99": equal_p99,
-            "server": {p: {"steps": st1[p]["steps"] - st0[p]["steps"], "max_step_jobs": st1[p]["max_step_jobs"],
-                           "arena_peak_gb": st1[p]["arena_peak_bytes"] / 1e9} for p in servers},
-            "gpu_launches": sum(st1[p]["kernels"] - st0[p]["kernels"] for p in servers) + plain_launches,
-            "clocks": clocks,
-        }
-        print(json.dumps(line), flush=True)
+    rec = {"requests": len(reqs), "rate_hz": args.rate, "evals_total": sum(evals), "server_arms": list(servers),
+           "headline_arm": best_served, "step_evals": list(step_evals), "server_budget_gb": budget / 1e9,
+           "server_arena_gb": next(iter(st1.values()))["arena_bytes"] / 1e9,
+           "lanes": next(iter(st1.values()))["lanes"], "host_buffers": "page-locked",
+           "saturation": sat, "latency_by_rate_hz": sweep, "at_equal_p99": equal_p99,
+           "server": {p: {"steps": st1[p]["steps"] - st0[p]["steps"], "max_step_jobs": st1[p]["max_step_jobs"],
+                          "arena_peak_gb": st1[p]["arena_peak_bytes"] / 1e9} for p in servers},
+           "gpu_launches": sum(st1[p]["kernels"] - st0[p]["kernels"] for p in servers) + plain_launches}
     for srv in servers.values():
         srv.close()
     ctx.close()
+    return rec
+
+
+def run_serve_bench(args) -> int:
+    """The serving workload as its own bench line (a sweep of offered rates)."""
+    import torch
+
+    import paper_2003_02200_gb300 as tvs
+
+    world, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    dist = dist_init("nccl")
+    props = torch.cuda.get_device_properties(device)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid else None)
+    barrier(dist, device)
+    sampler.start()
+    factors = [float(x) for x in args.rate_factors.split(",") if x.strip()]
+    policies = [p.strip() for p in args.policies.split(",") if p.strip()]
+    steps_list = [float(x) for x in str(args.step_evals).split(",") if x.strip()]
+    rec = measure_serve(tvs, torch, device, args, args.requests, factors, policies, True, steps_list)
+    clocks = sampler.stop()
+    barrier(dist, device)
+    sat = rec["saturation"][rec["headline_arm"]]
+    tot_e, max_s = aggregate(float(rec["evals_total"]), sat["makespan_s"], dist, device)
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": tot_e / max_s / 1e9, "unit": UNIT, "n_gpus": world,
+            "steps": (len(factors) + 1) * (len(rec["server_arms"]) + 1), "warmup": max(args.warmup, 1),
+            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": f"synthetic: {rec['requests']} seeded Poisson requests (mean {args.rate:g}/s) on spectral-fractal "
+                    "DEMs, side log-uniform 128-2048, n from {90,180,360}, observer U(1.5,30) m, range "
+                    "{unlimited, 5 km}, step {5,10,30} m",
+            "config": {"workload": "serve: request stream through the continuous-batching server vs the "
+                                   "plain one-at-a-time path",
+                       **{k: rec[k] for k in ("requests", "evals_total", "server_arms", "headline_arm", "step_evals",
+                                              "server_budget_gb", "server_arena_gb", "lanes", "host_buffers")},
+                       "decisions": "certified (library default) on every arm",
+                       "pruning": "on (library default) on every arm"},
+            "dems_per_s": rec["requests"] * world / max_s,
+            "saturation": rec["saturation"],
+            "latency_by_rate_hz": rec["latency_by_rate_hz"],
+            "at_equal_p99": rec["at_equal_p99"],
+            "server": rec["server"],
+            "gpu_launches": rec["gpu_launches"],
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
     return 0
 
 

@@ -270,6 +270,13 @@ int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, d
  * skipped instead of faulting.  Errors: TVS_ERR_ARG, TVS_ERR_CUDA. */
 int tvs_debug_sweep_check(int32_t* out, int clear);
 
+/* Test and profiling hook: event counts of the certified sweep on the current
+ * device since the last clear, after a device synchronisation: out[0] exact
+ * walks (POVs with a decision inside its FP32 margin), out[1] of them walked
+ * in FP64 (a decision inside the double-float margin too).  Errors:
+ * TVS_ERR_ARG, TVS_ERR_CUDA. */
+int tvs_debug_sweep_stats(uint64_t* out, int clear);
+
 /* Turn per-kernel timing on (1) or off (0); turning it on clears the counters.
  * While on, each launch is bracketed by CUDA events on its stream. */
 int tvs_profile_enable(tvs_handle h, int on);

@@ -134,6 +134,7 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             "tvs_debug_direction_cv": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
             "tvs_debug_sweep_check": ([i32p, C.c_int], C.c_int),
+            "tvs_debug_sweep_stats": ([C.POINTER(C.c_uint64), C.c_int], C.c_int),
             "tvs_viewshed_points": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
                                      C.c_int, C.c_int, vp, vp], C.c_int),
             "tvs_visibility_map": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int, C.c_double, vp,
@@ -183,6 +184,14 @@ def sweep_check(clear: bool = True) -> list[int]:
     out = (C.c_int32 * 4)()
     _check(load().tvs_debug_sweep_check(out, int(clear)))
     return list(out)
+
+
+def sweep_stats(clear: bool = True) -> dict:
+    """tvs_debug_sweep_stats: event counts of the certified sweep on the
+    current device (exact walks, FP64 walks)."""
+    out = (C.c_uint64 * 2)()
+    _check(load().tvs_debug_sweep_stats(out, int(clear)))
+    return {"exact_walks": int(out[0]), "fp64_walks": int(out[1])}
 
 
 def count_evals(rows: int, cols: int, n_sectors: int, step_m: float = 1.0, max_range_m: float = 0.0) -> int:

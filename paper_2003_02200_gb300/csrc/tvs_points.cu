@@ -18,8 +18,9 @@
 // One warp per (POV, group of FP32_GROUP directions): lane = 4 kk + 2 v + s
 // walks direction 8 g + kk, virtual POV v (hi / lo; DIRECT uses v = 0 only),
 // forward (s = 0) or backward (s = 1).  The walk is the sweep's: targets
-// d = 1 .. n (n = min(usable samples, K)), visible iff the FP32 slope
-// (z - h) * rcp(d) is strictly above the running maximum, and
+// d = 1 .. n (n = min(usable samples, K)), visible iff the target's slope is
+// strictly above the running maximum -- the exact decision (certified walks,
+// the default) or the FP32 one, (z - h) * rcp(d) (fp32_decisions) -- and
 // cv = 1 + sum_{d < n} v_d (2d + 1) for n >= 1 (the last target only closes a
 // segment).  Lane 0 adds the group's terms g * blend(cv) in direction order in
 // FP32 and stores the group sum as an exact partial; a finalize kernel adds
@@ -27,6 +28,7 @@
 #include "tvs.h"
 #include "tvs_host.h"
 #include "tvs_internal.h"
+#include "tvs_df.cuh"
 
 #include <cuda_runtime.h>
 
@@ -50,6 +52,9 @@ struct PointsParams {
     double scale;           // (pi / (2n)) step^2
     int rows, cols, n, ngroups, npov, mode;
     float h0;
+    float h0_lo;            // h0 - (double)h0 above, rounded
+    double h0d;             // h0 (the FP64 walks)
+    int cert;               // certified (exact) visibility decisions
 };
 
 // View value V[i][j] of the direction's D4 view, read from the row-major DEM.
@@ -272,6 +277,224 @@ __device__ __forceinline__ int walk_half_line(const float* __restrict__ dem, int
     return n >= 1 ? 1 + sum - (lastvis ? 2 * n + 1 : 0) : 0;
 }
 
+// ----------------------------------------------------- certified walks --
+// With certified decisions (the library default) a half-line is walked with
+// double-float heights (the blend of Alg. 6 to about 2^-43 of the heights) and
+// double-float slopes, warp-cooperatively as walk_half_line does; each
+// decision is proved by a margin (slope errors <= 2^-45 |theta| + 2 eta / d),
+// and when one is not, the warp walks the half-line again in FP64 exactly as
+// the FP64 definition does ((1 - r) a + r b, h = z + h0, (z - h) / d, strict
+// comparison with the running maximum).  Either way every decision is the one
+// exact arithmetic takes (up to FP64 rounding, which the FP64 walk shares with
+// the definition), so an sDEM point's area is the certified map's value.
+
+// A half-line: direction, observer's view cell (i0 = base row for DIRECT),
+// line base, walk direction.
+struct LineRef {
+    const float* dem;
+    int cols;
+    DirDev d;
+    long long base;
+    int j0, dir;
+    bool direct;
+};
+
+// Position of the target at distance dd: false when it is not part of the walk.
+__device__ __forceinline__ bool line_target(const LineRef& L, int dd, long long* a, unsigned* fr, int* j)
+{
+    *j = L.j0 + L.dir * dd;
+    line_pos(L.d, L.direct, L.base, L.j0, *j, a, fr);
+    return dd <= L.d.K && usable(L.d, *a, *fr, *j);
+}
+
+__device__ __forceinline__ double z64_of(const LineRef& L, long long a, unsigned fr, int j)
+{
+    const double lo = (double)view_at(L.dem, L.cols, L.d, a, j);
+    if (fr == 0u) return lo;
+    const double hi = (double)view_at(L.dem, L.cols, L.d, a + 1, j);
+    const double r = __dmul_rn((double)fr, 0x1p-32);
+    return __dadd_rn(__dmul_rn(__dsub_rn(1.0, r), lo), __dmul_rn(r, hi));
+}
+
+// The FP64 walk: the measure cv (0 for no target) on every lane, flags as
+// walk_half_line stores them.
+__device__ __noinline__ int walk_fp64(const LineRef& L, double h, unsigned char* flags, int cap, int lane)
+{
+    const unsigned FULL = 0xffffffffu;
+    const double NEG = -__longlong_as_double(0x7ff0000000000000LL);
+    double M = NEG;
+    int sum = 0, n = 0, lastvis = 0;
+    for (int c = 0;; c += WALK_CHUNK) {
+        double t[WALK_TPL];
+        int firstbad = WALK_TPL;
+        const int d0 = c + WALK_TPL * lane + 1;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m) {
+            long long a;
+            unsigned fr;
+            int j;
+            const bool ok = line_target(L, d0 + m, &a, &fr, &j);
+            t[m] = NEG;
+            if (ok) t[m] = __ddiv_rn(__dsub_rn(z64_of(L, a, fr, j), h), (double)(d0 + m));
+            if (!ok && firstbad == WALK_TPL) firstbad = m;
+        }
+        const unsigned bad = __ballot_sync(FULL, firstbad < WALK_TPL);
+        const int badlane = bad ? __ffs(bad) - 1 : 32;
+        const int cnt = badlane == 32 ? WALK_CHUNK : WALK_TPL * badlane + __shfl_sync(FULL, firstbad, badlane);
+        const int mine = min(max(cnt - WALK_TPL * lane, 0), WALK_TPL);
+        double lm = NEG;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m)
+            if (m < mine) lm = fmax(lm, t[m]);
+        double pm = lm;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const double y = __shfl_up_sync(FULL, pm, o);
+            if (lane >= o) pm = fmax(pm, y);
+        }
+        const double before = __shfl_up_sync(FULL, pm, 1);
+        double run = lane == 0 ? M : fmax(M, before);
+        unsigned vbits = 0u;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m) {
+            if (m < mine) {
+                const int dd = d0 + m;
+                const bool vis = t[m] > run;
+                run = fmax(run, t[m]);
+                if (vis) { sum += 2 * dd + 1; vbits |= 1u << m; }
+                if (flags && dd < cap) flags[dd] = vis ? 1 : 0;
+            }
+        }
+        if (cnt > 0) {
+            const int last = cnt - 1;
+            lastvis = (__shfl_sync(FULL, vbits, last / WALK_TPL) >> (last % WALK_TPL)) & 1u;
+            n = c + cnt;
+        }
+        M = fmax(M, __shfl_sync(FULL, pm, 31));
+        if (cnt < WALK_CHUNK) break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+    return n >= 1 ? 1 + sum - (lastvis ? 2 * n + 1 : 0) : 0;
+}
+
+// The double-float walk with its margins; *esc (warp-uniform) when a
+// decision fell inside its margin (the measure and flags are then the FP64
+// walk's to write).  hh + hl is the observer, zobs the |elevations| it blends.
+__device__ __noinline__ int walk_df(const LineRef& L, float hh, float hl, float zobs, float h0abs,
+                                    unsigned char* flags, int cap, int lane, bool* esc_out)
+{
+    const unsigned FULL = 0xffffffffu;
+    const float NEG = __int_as_float(0xff800000);
+    float rh = NEG, rl = 0.f;
+    int rd = 1;
+    float zmax = zobs;
+    int sum = 0, n = 0, lastvis = 0;
+    bool esc = false;
+    for (int c = 0;; c += WALK_CHUNK) {
+        float th[WALK_TPL], tl[WALK_TPL];
+        int firstbad = WALK_TPL;
+        const int d0 = c + WALK_TPL * lane + 1;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m) {
+            long long a;
+            unsigned fr;
+            int j;
+            const bool ok = line_target(L, d0 + m, &a, &fr, &j);
+            th[m] = NEG; tl[m] = 0.f;
+            if (ok) {
+                const float va = view_at(L.dem, L.cols, L.d, a, j);
+                const float vb = fr ? view_at(L.dem, L.cols, L.d, a + 1, j) : va;
+                float zh, zl;
+                df::df_blend(va, vb, fr, zh, zl);
+                zmax = fmaxf(zmax, fmaxf(fabsf(va), fabsf(vb)));
+                df::df_slope(zh, zl, hh, hl, d0 + m, th[m], tl[m]);
+            }
+            if (!ok && firstbad == WALK_TPL) firstbad = m;
+        }
+        const unsigned bad = __ballot_sync(FULL, firstbad < WALK_TPL);
+        const int badlane = bad ? __ffs(bad) - 1 : 32;
+        const int cnt = badlane == 32 ? WALK_CHUNK : WALK_TPL * badlane + __shfl_sync(FULL, firstbad, badlane);
+        const int mine = min(max(cnt - WALK_TPL * lane, 0), WALK_TPL);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(FULL, zmax, o));
+        const float eta = 0x1p-42f * (zmax + h0abs) + 0x1p-126f;
+        float mh = NEG, ml = 0.f;
+        int md = 1;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m)
+            if (m < mine && df::df_gt(th[m], tl[m], mh, ml)) { mh = th[m]; ml = tl[m]; md = d0 + m; }
+        float ph = mh, pl = ml;
+        int pd = md;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float qh = __shfl_up_sync(FULL, ph, o);
+            const float ql = __shfl_up_sync(FULL, pl, o);
+            const int qd = __shfl_up_sync(FULL, pd, o);
+            if (lane >= o && df::df_gt(qh, ql, ph, pl)) { ph = qh; pl = ql; pd = qd; }
+        }
+        float ch = __shfl_up_sync(FULL, ph, 1);
+        float cl = __shfl_up_sync(FULL, pl, 1);
+        int cd = __shfl_up_sync(FULL, pd, 1);
+        if (lane == 0 || df::df_gt(rh, rl, ch, cl)) { ch = rh; cl = rl; cd = rd; }
+        unsigned vbits = 0u;
+#pragma unroll
+        for (int m = 0; m < WALK_TPL; ++m) {
+            if (m < mine) {
+                const int dd = d0 + m;
+                bool vis = true;                   // the first target (no earlier one) is visible
+                if (ch > NEG) {
+                    float s, e;
+                    df::two_sum(th[m], -ch, s, e);
+                    const float dh = __fadd_rn(s, __fadd_rn(e, __fsub_rn(tl[m], cl)));
+                    const float marg = __fmaf_rn(0x1p-40f, fabsf(th[m]) + fabsf(ch),
+                                                 4.04f * eta * (__frcp_rn((float)dd) + __frcp_rn((float)cd))) +
+                                       0x1p-120f;
+                    if (!(fabsf(dh) > marg)) esc = true;
+                    vis = dh > 0.f;
+                }
+                if (df::df_gt(th[m], tl[m], ch, cl)) { ch = th[m]; cl = tl[m]; cd = dd; }
+                if (vis) { sum += 2 * dd + 1; vbits |= 1u << m; }
+                if (flags && dd < cap) flags[dd] = vis ? 1 : 0;
+            }
+        }
+        if (cnt > 0) {
+            const int last = cnt - 1;
+            lastvis = (__shfl_sync(FULL, vbits, last / WALK_TPL) >> (last % WALK_TPL)) & 1u;
+            n = c + cnt;
+        }
+        const float lh = __shfl_sync(FULL, ph, 31), ll = __shfl_sync(FULL, pl, 31);
+        const int ld = __shfl_sync(FULL, pd, 31);
+        if (df::df_gt(lh, ll, rh, rl)) { rh = lh; rl = ll; rd = ld; }
+        if (cnt < WALK_CHUNK) break;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(FULL, sum, o);
+    *esc_out = __any_sync(FULL, esc);
+    return n >= 1 ? 1 + sum - (lastvis ? 2 * n + 1 : 0) : 0;
+}
+
+// Certified measure of a half-line whose observer stands on the sample
+// (a0, fr0) of view column j0 (DIRECT: the cell itself, fr0 = 0).
+__device__ __forceinline__ int walk_exact(const LineRef& L, long long a0, unsigned fr0, float h0, float h0_lo,
+                                          double h0d, unsigned char* flags, int cap, int lane)
+{
+    const float va = view_at(L.dem, L.cols, L.d, a0, L.j0);
+    const float vb = fr0 ? view_at(L.dem, L.cols, L.d, a0 + 1, L.j0) : va;
+    float zh, zl, hh, hl;
+    df::df_blend(va, vb, fr0, zh, zl);
+    {
+        float s, e;
+        df::two_sum(zh, h0, s, e);
+        e = __fadd_rn(e, __fadd_rn(zl, h0_lo));
+        df::two_sum(s, e, hh, hl);
+    }
+    bool esc = false;
+    const int cv = walk_df(L, hh, hl, fmaxf(fabsf(va), fabsf(vb)), fabsf(h0), flags, cap, lane, &esc);
+    if (!esc) return cv;
+    return walk_fp64(L, __dadd_rn(z64_of(L, a0, fr0, L.j0), h0d), flags, cap, lane);
+}
+
 // Directions per CTA of the points kernel (4 warps each: 2 lines x 2 sides).
 constexpr int POINTS_DIRS = 2;
 
@@ -299,9 +522,15 @@ __global__ void __launch_bounds__(128 * POINTS_DIRS) points_kernel(PointsParams 
             long long a;
             unsigned fr;
             line_pos(L.d, direct, L.base, L.j0, L.j0, &a, &fr);
-            const float h = __fadd_rn(direct ? view_at(pp.dem, pp.cols, L.d, L.i, L.j0)
-                                             : sample_at(pp.dem, pp.cols, L.d, a, fr, L.j0), pp.h0);
-            cv = walk_half_line(pp.dem, pp.cols, L.d, rtab, L.base, L.j0, direct, s ? -1 : 1, h, nullptr, 0, lane);
+            if (pp.cert) {
+                const LineRef R{pp.dem, pp.cols, L.d, L.base, L.j0, s ? -1 : 1, direct};
+                cv = walk_exact(R, a, fr, pp.h0, pp.h0_lo, pp.h0d, nullptr, 0, lane);
+            } else {
+                const float h = __fadd_rn(direct ? view_at(pp.dem, pp.cols, L.d, L.i, L.j0)
+                                                 : sample_at(pp.dem, pp.cols, L.d, a, fr, L.j0), pp.h0);
+                cv = walk_half_line(pp.dem, pp.cols, L.d, rtab, L.base, L.j0, direct, s ? -1 : 1, h, nullptr, 0,
+                                    lane);
+            }
         }
         if (lane == 0) cvs[w] = cv;
     }
@@ -356,6 +585,9 @@ struct MapParams {
     int* count;
     int rows, cols, n, npov, cap;
     float h0;
+    float h0_lo;
+    double h0d;
+    int cert;
 };
 
 // One warp per (POV, slot), walking the half-line as the points kernel does.
@@ -377,6 +609,11 @@ __global__ void __launch_bounds__(256) map_flags_kernel(MapParams mp)
     case 1:  i = jD; j0 = iD; break;
     case 2:  i = jD; j0 = d.W - 1 - iD; break;
     default: i = d.H - 1 - iD; j0 = jD; break;
+    }
+    if (mp.cert) {
+        const LineRef R{mp.dem, mp.cols, d, i, j0, dir, true};
+        walk_exact(R, i, 0u, mp.h0, mp.h0_lo, mp.h0d, mp.flags + t * mp.cap, mp.cap, lane);
+        return;
     }
     const float h = __fadd_rn(view_at(mp.dem, mp.cols, d, i, j0), mp.h0);
     walk_half_line(mp.dem, mp.cols, d, rtab, i, j0, true, dir, h, mp.flags + t * mp.cap, mp.cap, lane);
@@ -538,6 +775,9 @@ extern "C" int tvs_visibility_map(tvs_handle h, const float* d_dem, int rows, in
     mp.count = d_count;
     mp.rows = rows; mp.cols = cols; mp.n = n_sectors; mp.npov = npov; mp.cap = cap;
     mp.h0 = (float)obs_height_m;
+    mp.h0_lo = (float)(obs_height_m - (double)mp.h0);
+    mp.h0d = obs_height_m;
+    mp.cert = !h->tuning.fp32_decisions;
     const long long walks = (long long)npov * 2 * n_sectors;
     const size_t rtab_bytes = ((size_t)std::max(rows, cols) + 1) * sizeof(float);
     TVS_CUDA(cudaFuncSetAttribute(map_flags_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rtab_bytes),
@@ -608,6 +848,9 @@ extern "C" int tvs_viewshed_points(tvs_handle h, const float* d_dem, int rows, i
     pp.scale = (M_PI / (2.0 * (double)n_sectors)) * (step_m * step_m);
     pp.rows = rows; pp.cols = cols; pp.n = n_sectors; pp.ngroups = ngroups; pp.npov = npov; pp.mode = mode;
     pp.h0 = (float)obs_height_m;
+    pp.h0_lo = (float)(obs_height_m - (double)pp.h0);
+    pp.h0d = obs_height_m;
+    pp.cert = !h->tuning.fp32_decisions;
     const size_t rtab_bytes = ((size_t)std::max(rows, cols) + 1) * sizeof(float);
     TVS_CUDA(cudaFuncSetAttribute(points_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)rtab_bytes),
              "points shared memory");

@@ -25,6 +25,7 @@
 //    FP64 definition itself for what that margin cannot settle).
 #include "tvs.h"
 #include "tvs_internal.h"
+#include "tvs_df.cuh"
 
 #include <cuda_runtime.h>
 
@@ -39,6 +40,9 @@ namespace tvs {
 // bound, CTA) and skips the access instead of faulting.  Read and cleared by
 // tvs_debug_sweep_check.
 __device__ int g_sweep_check[4];
+// Event counts of the certified sweep: exact walks (flagged POVs), of them
+// FP64 walks.
+__device__ unsigned long long g_sweep_stats[2];
 
 __device__ __forceinline__ bool in_range(long long idx, long long bound, int code)
 {
@@ -87,48 +91,6 @@ __device__ __forceinline__ long long view_index(const DirDev& d, int cols, int a
     case 2:  *step = 1;     return (long long)(d.W - 1 - j) * cols + a;
     default: *step = -cols; return (long long)(d.H - 1 - a) * cols + j;
     }
-}
-
-// ------------------------------------------------ double-float helpers --
-// Error-free transformations in round-to-nearest single precision.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e)
-{
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-// a + b = s + e exactly when a == 0 or exponent(a) >= exponent(b).
-__device__ __forceinline__ void fast_two_sum(float a, float b, float& s, float& e)
-{
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-__device__ __forceinline__ bool df_gt(float ah, float al, float bh, float bl)
-{
-    return ah > bh || (ah == bh && al > bl);
-}
-
-// Height of the sample blending va (row a) and vb (row a + 1) with weights
-// 1 - r and r, r = fr * 2^-32 (Alg. 6), as hi + lo: the difference vb - va
-// and r are split exactly (TwoSum; r into its top 24 and low 8 bits), the main
-// product exactly (FMA), the rest rounds at about 2^-46 of max(|va|, |vb|):
-// |hi + lo - exact| <= 2^-43 max(|va|, |vb|), |lo| <= ulp(hi) / 2.
-__device__ __forceinline__ void df_blend(float va, float vb, unsigned fr, float& zh, float& zl)
-{
-    if (fr == 0u) { zh = va; zl = 0.f; return; }
-    float dh, dl;
-    two_sum(vb, -va, dh, dl);
-    const float rh = __fmul_rn(__uint2float_rn(fr & 0xFFFFFF00u), 0x1p-32f);
-    const float rl = __fmul_rn(__uint2float_rn(fr & 0xFFu), 0x1p-32f);
-    const float ph = __fmul_rn(rh, dh);
-    const float pe = __fmaf_rn(rh, dh, -ph);
-    const float t = __fmaf_rn(rh, dl, __fmaf_rn(rl, dh, __fmul_rn(rl, dl)));
-    float sh, se;
-    two_sum(va, ph, sh, se);
-    const float lo = __fadd_rn(se, __fadd_rn(pe, t));
-    two_sum(sh, lo, zh, zl);
 }
 
 // The paper's single-precision blend of Kernel-1: r = float(fr) 2^-32,
@@ -216,7 +178,7 @@ __device__ __forceinline__ float stage_row(const SweepParams& sp, const ItemRow&
             if (x >= it.L || !in_range(ROW_PADL + x, sp.half, 3)) continue;
             if (CERT) {
                 float zh, zl;
-                df_blend(va[k], vb[k], fr[k], zh, zl);
+                df::df_blend(va[k], vb[k], fr[k], zh, zl);
                 Fh[ROW_PADL + x] = x == it.L - 1 ? NEG : zh;
                 Fl[ROW_PADL + x] = x == it.L - 1 ? 0.f : zl;
                 zmax = fmaxf(zmax, fmaxf(fabsf(va[k]), fabsf(vb[k])));
@@ -492,6 +454,18 @@ constexpr float CERT_FLOOR = 0x1p-99f;
 constexpr int WM_SPAN = 40;
 static_assert(LARGE_POV + LARGE_UNROLL <= WM_SPAN && SMALL_POV + SMALL_UNROLL <= WM_SPAN, "window span");
 static_assert(WM_SPAN + 4 <= ROW_PADR, "window maxima read into the right pad");
+// Steps per unrolled block of the certified walk with LARGE_POV groups: its
+// step is about 40 % longer than the FP32 one, and a 28-step block of it no
+// longer stays in the instruction cache.
+#ifndef TVS_CERT_UNROLL
+#define TVS_CERT_UNROLL 16
+#endif
+constexpr int CERT_UNROLL = TVS_CERT_UNROLL;
+#ifndef TVS_CERT_POV
+#define TVS_CERT_POV SMALL_POV
+#endif
+constexpr int CERT_POV = TVS_CERT_POV;
+static_assert(FLUSH_STEPS % CERT_UNROLL == 0, "long walks flush on block boundaries");
 // Entries of a warp's flagged-POV list (at least 32 lanes x LARGE_POV).
 constexpr int FLAG_CAP = 256;
 // Targets per lane per chunk of an exact walk.
@@ -538,23 +512,6 @@ struct ExactCtx {
     int half;            // floats of a staged row array (index bound, with ROW_PADL)
     int zs_len, wm_len;  // entries of the suffix and window maxima
 };
-
-// Double-float slope (z - h) / d of a staged target against the observer h.
-__device__ __forceinline__ void df_slope(float zh, float zl, float hh, float hl, int d, float& qh, float& ql)
-{
-    float s, e;
-    two_sum(zh, -hh, s, e);
-    e = __fadd_rn(e, __fsub_rn(zl, hl));
-    float Dh, Dl;
-    two_sum(s, e, Dh, Dl);
-    const float fd = (float)d;
-    const float iv = __frcp_rn(fd);
-    const float q1 = __fmul_rn(Dh, iv);
-    const float ph = __fmul_rn(q1, fd);
-    const float pl = __fmaf_rn(q1, fd, -ph);
-    const float r = __fadd_rn(__fsub_rn(__fsub_rn(Dh, ph), pl), Dl);
-    fast_two_sum(q1, __fmul_rn(r, iv), qh, ql);
-}
 
 // FP64 height of staged sample xs exactly as the FP64 definition forms it:
 // (1 - r) * a + r * b with r = fr / 2^32, every operation rounded.
@@ -632,9 +589,9 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
     float hh, hl;
     {
         float s, e;
-        two_sum(c.H[x], c.h0h, s, e);
+        df::two_sum(c.H[x], c.h0h, s, e);
         e = __fadd_rn(e, __fadd_rn(c.Lo[x], c.h0l));
-        two_sum(s, e, hh, hl);
+        df::two_sum(s, e, hh, hl);
     }
     float rh = NEG, rl = 0.f;
     int rd = 1;
@@ -650,8 +607,8 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
             const int d = d0 + k;
             th[k] = NEG; tl[k] = 0.f;
             if (d <= last && in_range(ROW_PADL + x + d, c.half, 15)) {
-                df_slope(c.H[x + d], c.Lo[x + d], hh, hl, d, th[k], tl[k]);
-                if (df_gt(th[k], tl[k], mh, ml)) { mh = th[k]; ml = tl[k]; md = d; }
+                df::df_slope(c.H[x + d], c.Lo[x + d], hh, hl, d, th[k], tl[k]);
+                if (df::df_gt(th[k], tl[k], mh, ml)) { mh = th[k]; ml = tl[k]; md = d; }
             }
         }
         // inclusive max-scan over the lanes
@@ -662,12 +619,12 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
             const float qh = __shfl_up_sync(0xffffffffu, ph, o);
             const float ql = __shfl_up_sync(0xffffffffu, pl, o);
             const int qd = __shfl_up_sync(0xffffffffu, pd, o);
-            if (lane >= o && df_gt(qh, ql, ph, pl)) { ph = qh; pl = ql; pd = qd; }
+            if (lane >= o && df::df_gt(qh, ql, ph, pl)) { ph = qh; pl = ql; pd = qd; }
         }
         float ch = __shfl_up_sync(0xffffffffu, ph, 1);
         float cl = __shfl_up_sync(0xffffffffu, pl, 1);
         int cd = __shfl_up_sync(0xffffffffu, pd, 1);
-        if (lane == 0 || df_gt(rh, rl, ch, cl)) { ch = rh; cl = rl; cd = rd; }
+        if (lane == 0 || df::df_gt(rh, rl, ch, cl)) { ch = rh; cl = rl; cd = rd; }
 #pragma unroll
         for (int k = 0; k < XW_KPL; ++k) {
             const int d = d0 + k;
@@ -675,7 +632,7 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
             bool v = true;                           // the first target (no earlier one) is visible
             if (ch > NEG) {
                 float s, e;
-                two_sum(th[k], -ch, s, e);
+                df::two_sum(th[k], -ch, s, e);
                 const float dh = __fadd_rn(s, __fadd_rn(e, __fsub_rn(tl[k], cl)));
                 const float marg = __fmaf_rn(0x1p-40f, fabsf(th[k]) + fabsf(ch),
                                              4.04f * c.eta * (__frcp_rn((float)d) + __frcp_rn((float)cd))) +
@@ -684,12 +641,12 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
                 v = dh > 0.f;
             }
             if (v) acc += 2 * d + 1;
-            if (df_gt(th[k], tl[k], ch, cl)) { ch = th[k]; cl = tl[k]; cd = d; }
+            if (df::df_gt(th[k], tl[k], ch, cl)) { ch = th[k]; cl = tl[k]; cd = d; }
         }
         const float lh = __shfl_sync(0xffffffffu, ph, 31);
         const float ll = __shfl_sync(0xffffffffu, pl, 31);
         const int ld = __shfl_sync(0xffffffffu, pd, 31);
-        if (df_gt(lh, ll, rh, rl)) { rh = lh; rl = ll; rd = ld; }
+        if (df::df_gt(lh, ll, rh, rl)) { rh = lh; rl = ll; rd = ld; }
     }
     *esc_out = __any_sync(0xffffffffu, esc);
     return warp_sum(acc);
@@ -706,6 +663,10 @@ __device__ __noinline__ void exact_walk(const ExactCtx& c, int x, int lane)
         bool esc = false;
         const int s = df_walk(c, x, n - 1, lane, &esc);
         cv = 1 + (esc ? fp64_walk(c, x, n - 1, lane) : s);
+        if (lane == 0) {
+            atomicAdd(&g_sweep_stats[0], 1ull);
+            if (esc) atomicAdd(&g_sweep_stats[1], 1ull);
+        }
     }
     if (lane == 0 && in_range(x, c.L, 14)) c.cvrow[c.rev ? c.L - 1 - x : x] = cv;
 }
@@ -746,10 +707,11 @@ __device__ __forceinline__ void flag_push(FlagList& fl, const ExactCtx& c, unsig
 
 // U certified steps of one lane's P POVs (see the derivation above).  y[m] is
 // the window's target x0 + e + m relative to R, g[q] the POV's height relative
-// to R, dl[q] its margin for this block.
+// to R.  mn[q] keeps the smallest |s| of the POV's steps: the block's margin
+// test (mn < delta) runs once at its end.
 template <int P, int U, bool MASKED, bool FAR>
 __device__ __forceinline__ void cert_block(const float* y, const float4* __restrict__ tab, int e, const float* g,
-                                           float* M, float2* acc2, const float* dl, bool& tie, int nvalid)
+                                           float2* M2, float2* acc2, float* mn, int nvalid)
 {
 #pragma unroll
     for (int u = 0; u < U; ++u) {
@@ -761,43 +723,29 @@ __device__ __forceinline__ void cert_block(const float* y, const float4* __restr
         for (int q = 0; q < P; q += 2) {
             const float2 d = make_float2(__fsub_rn(y[q + u + 1], g[q]), __fsub_rn(y[q + u + 2], g[q + 1]));
             const float2 x = __fmul2_rn(d, iv);
-            const float2 s = __ffma2_rn(make_float2(-1.f, -1.f), make_float2(M[q], M[q + 1]), x);
+            const float2 s = __ffma2_rn(make_float2(-1.f, -1.f), M2[q / 2], x);
             const float2 v = make_float2(sat_pos(s.x), sat_pos(s.y));
             acc2[q / 2] = __ffma2_rn(v, cp, acc2[q / 2]);
-            M[q] = fmaxf(M[q], x.x);
-            M[q + 1] = fmaxf(M[q + 1], x.y);
-            tie |= fabsf(s.x) < dl[q];
-            tie |= fabsf(s.y) < dl[q + 1];
+            M2[q / 2].x = fmaxf(M2[q / 2].x, x.x);
+            M2[q / 2].y = fmaxf(M2[q / 2].y, x.y);
+            if (!MASKED || u < nvalid) {
+                mn[q] = fminf(mn[q], fabsf(s.x));
+                mn[q + 1] = fminf(mn[q + 1], fabsf(s.y));
+            }
         }
     }
 }
 
-// Replays one block POV by POV (the same arithmetic) to find which POVs had a
-// step inside their margin.  Rare: only after a block whose lane-level flag
-// was raised.
-template <int P>
-__device__ __noinline__ unsigned cert_recheck(const float* __restrict__ H, const float* __restrict__ Lo, int xe,
-                                              int e, int nsteps, const float4* __restrict__ tab, int tabn,
-                                              float Rh, float Rl, const float* g, const float* Ms, const float* dl,
-                                              int half)
+// Upper bound of the slopes a POV of the group can meet among targets whose
+// hi heights are at most z (a window or suffix maximum): max(0, z + slack -
+// Rh - gmin) / (e + 1), with slack covering the hi / lo split, the rounding of
+// the differences and of g (2^-20 relative, plus eg).  z = -inf (sentinels
+// only) gives 0.
+__device__ __forceinline__ float bound_slope(float z, float Rh, float gmin, float eg, float ive)
 {
-    unsigned mask = 0u;
-    for (int q = 0; q < P; ++q) {
-        float M = Ms[q];
-        for (int u = 0; u < nsteps; ++u) {
-            const int t = xe + q + u + 1;
-            if (!in_range(ROW_PADL + t, half, 18)) continue;
-            const float yv = __fadd_rn(__fsub_rn(H[t], Rh), __fsub_rn(Lo[t], Rl));
-            const float dv = __fsub_rn(yv, g[q]);
-            const int dd = e + u + 1;
-            const float iv = dd <= tabn ? tab[dd - 1].x : __frcp_rn((float)dd);
-            const float x = __fmul_rn(dv, iv);
-            const float s = __fmaf_rn(-1.f, M, x);
-            if (fabsf(s) < dl[q]) mask |= 1u << q;
-            M = fmaxf(M, x);
-        }
-    }
-    return mask;
+    const float A = __fsub_rn(__fsub_rn(z, Rh), gmin);
+    const float sl = 0x1p-20f * (fminf(fabsf(z), 0x1p100f) + fabsf(Rh) + fabsf(gmin)) + eg;
+    return __fmul_rn(fmaxf(__fadd_rn(A, sl), 0.f), ive) * 1.0000039f;
 }
 
 // Certified sweep of one staged row (the lane queue of sweep_row).  eg0 =
@@ -819,8 +767,9 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
     const int L = xc.L, K = xc.K;
     const int G = (L + P - 1) / P;
     const int klim = K - 1;
-    float g[P], M[P], ia[P];
-    float2 acc2[P / 2];
+    float g[P], ia[P];
+    float2 M2[P / 2], acc2[P / 2];   // running maxima of POV pairs (packed x - M)
+#define CERT_M(q) ((q) % 2 ? M2[(q) / 2].y : M2[(q) / 2].x)
     float Rh = 0.f, Rl = 0.f, gmin = 0.f, c2e = 0.f;
     unsigned mask = 0u;
     int gi = lane, next = 32;
@@ -842,7 +791,13 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             for (int q = 0; q < P; ++q) spill[32 * q] = 0;
         }
         if (dlim < 1) return;                 // no block runs (x0 <= L - 3 below)
-        if (!in_range(ROW_PADL + x0 + P + 1, xc.half, 19)) {
+        // every index the group's blocks use, checked once: the last block
+        // starts below dlim
+        const int elast = (dlim - 1) / U * U;
+        if (!in_range(ROW_PADL + x0 + elast + P + U - 1, xc.half, 19) ||
+            !in_range((x0 + elast) >> 2, xc.wm_len, 8) ||
+            (PRUNE && !in_range((x0 + elast + 1) / ZS_STRIDE, xc.zs_len, 9)) ||
+            (!(LONG && elast + U > tabn) && !in_range(elast + U - 1, tabn, 11))) {
             dlim = 0;
             mask = L - x0 >= P ? (1u << P) - 1u : (1u << (L - x0)) - 1u;   // walked exactly instead
             return;
@@ -872,7 +827,10 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             const float y1 = __fadd_rn(__fsub_rn(H[x + 1], Rh), __fsub_rn(Lo[x + 1], Rl));
             const float x1 = __fsub_rn(y1, g[q]);
             const float C = __fmaf_rn(0x1p-6f, fabsf(x1), __fmaf_rn(4.f, c2e, 0x1p-16f));
-            M[q] = __fsub_rn(x1, C);
+            // a POV with no target that adds area (x >= L - 2) starts at +inf:
+            // nothing is visible to it, no step is inside its margin, and it
+            // never holds back pruning
+            CERT_M(q) = x <= L - 3 ? __fsub_rn(x1, C) : pos_inf();
             ia[q] = 1.f;
         }
     };
@@ -912,45 +870,24 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                     acc2[q / 2] = make_float2(0.f, 0.f);
                 }
             }
-            // margins of this block (indices checked: the window's end, the
-            // window and suffix maxima, the distance table when it is read)
+            // margins of this block.  The bounds are formed branch-free: a
+            // window or suffix of sentinels only (-inf) gives 0.
             const bool far = LONG && e + U > tabn;
-            if (!in_range(ROW_PADL + x0 + e + P + U - 1, xc.half, 10) || !in_range((x0 + e) >> 2, xc.wm_len, 8) ||
-                (PRUNE && !in_range((x0 + e + 1) / ZS_STRIDE, xc.zs_len, 9)) ||
-                (!far && !in_range(e + U - 1, tabn, 11))) {
-                e = dlim;
-                mask = L - x0 >= P ? (1u << P) - 1u : (1u << (L - x0)) - 1u;   // walked exactly instead
-                continue;
-            }
             const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tab[e].x;
-            float Bw = 0.f;
-            {
-                const float wz = WM[(x0 + e) >> 2];
-                if (wz > NEG) {
-                    const float A = __fsub_rn(__fsub_rn(wz, Rh), gmin);
-                    const float sl = 0x1p-20f * (fabsf(wz) + fabsf(Rh) + fabsf(gmin)) + c2e;
-                    Bw = __fmul_rn(fmaxf(__fadd_rn(A, sl), 0.f), ive) * 1.0000039f;
-                }
-            }
+            const float Bw = bound_slope(WM[(x0 + e) >> 2], Rh, gmin, c2e, ive);
             const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
-            float dl[P], Ms[P];
+            float dl[P], Ms[P], mn[P];
 #pragma unroll
             for (int q = 0; q < P; ++q) {
-                Ms[q] = M[q];
-                dl[q] = __fmaf_rn(CERT_REL, fmaxf(fabsf(M[q]), Bw), __fmaf_rn(c2e, ia[q], ce));
+                Ms[q] = CERT_M(q);
+                dl[q] = __fmaf_rn(CERT_REL, fmaxf(fabsf(CERT_M(q)), Bw), __fmaf_rn(c2e, ia[q], ce));
+                mn[q] = pos_inf();
             }
             if (PRUNE) {
-                const float zs = ZS[(x0 + e + 1) / ZS_STRIDE];
-                float Bp = 0.f;
-                if (zs > NEG) {
-                    const float A = __fsub_rn(__fsub_rn(zs, Rh), gmin);
-                    const float sl = 0x1p-20f * (fabsf(zs) + fabsf(Rh) + fabsf(gmin)) + 2.f * c2e;
-                    Bp = __fmul_rn(fmaxf(__fadd_rn(A, sl), 0.f), ive) * 1.0000039f;
-                }
+                const float Bp = bound_slope(ZS[(x0 + e + 1) / ZS_STRIDE], Rh, gmin, 2.f * c2e, ive);
                 float m = pos_inf();
 #pragma unroll
-                for (int q = 0; q < P; ++q)
-                    if (x0 + q <= L - 2) m = fminf(m, __fmaf_rn(-2.f, dl[q], M[q]));
+                for (int q = 0; q < P; ++q) m = fminf(m, __fmaf_rn(-2.f, dl[q], CERT_M(q)));
                 if (m >= Bp) { e = dlim; continue; }
             }
             // the window, relative to R
@@ -970,28 +907,23 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                     y[m] = y0.x; y[m + 1] = y0.y; y[m + 2] = y1.x; y[m + 3] = y1.y;
                 }
             }
-            bool tie = false;
             const bool masked = klimited && e + U > dlim;
             if (masked) {
-                if (far) cert_block<P, U, true, true>(y, tab, e, g, M, acc2, dl, tie, dlim - e);
-                else cert_block<P, U, true, false>(y, tab + e, e, g, M, acc2, dl, tie, dlim - e);
+                if (far) cert_block<P, U, true, true>(y, tab, e, g, M2, acc2, mn, dlim - e);
+                else cert_block<P, U, true, false>(y, tab + e, e, g, M2, acc2, mn, dlim - e);
             } else {
-                if (far) cert_block<P, U, false, true>(y, tab, e, g, M, acc2, dl, tie, U);
-                else cert_block<P, U, false, false>(y, tab + e, e, g, M, acc2, dl, tie, U);
-            }
-            if (tie) {
-                float tg[P], tm[P], td[P];
-#pragma unroll
-                for (int q = 0; q < P; ++q) { tg[q] = g[q]; tm[q] = Ms[q]; td[q] = dl[q]; }
-                mask |= cert_recheck<P>(H, Lo, x0 + e, e, masked ? dlim - e : U, tab, tabn, Rh, Rl, tg, tm, td,
-                                        xc.half);
+                if (far) cert_block<P, U, false, true>(y, tab, e, g, M2, acc2, mn, U);
+                else cert_block<P, U, false, false>(y, tab + e, e, g, M2, acc2, mn, U);
             }
 #pragma unroll
-            for (int q = 0; q < P; ++q) ia[q] = M[q] > Ms[q] ? ive : ia[q];
+            for (int q = 0; q < P; ++q) mask |= mn[q] < dl[q] ? 1u << q : 0u;
+#pragma unroll
+            for (int q = 0; q < P; ++q) ia[q] = CERT_M(q) > Ms[q] ? ive : ia[q];
             e += U;
         }
     }
     if (fl.count > 0) drain_flags(fl, xc, lane);
+#undef CERT_M
 }
 
 template <bool LONG, bool PRUNE>
@@ -1014,7 +946,7 @@ __device__ __forceinline__ void sweep_item_cert(const ItemRow& it, const ExactCt
     if (it.pov == SMALL_POV)
         sweep_row_cert<SMALL_POV, SMALL_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
     else
-        sweep_row_cert<LARGE_POV, LARGE_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
+        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
 }
 
 // PRUNE: exact horizon pruning; LONG: the launch holds rows with walks of
@@ -1022,8 +954,17 @@ __device__ __forceinline__ void sweep_item_cert(const ItemRow& it, const ExactCt
 // certified decisions.  Per warp, shared memory holds the staged row (hi
 // parts; CERT: lo parts after them), the suffix maxima (PRUNE), the window
 // maxima and the flagged-POV list (CERT), and the long-walk spill (LONG).
+// Warps per CTA of the certified kernels: their per-lane state (8 POVs'
+// maxima, heights, margins and last-visible bounds, the window relative to
+// the group) needs more than 128 registers, and at 2000-sample rows the two
+// staged arrays already limit a CTA to about 8 warps of shared memory.
+#ifndef TVS_CERT_MAX_WARPS
+#define TVS_CERT_MAX_WARPS 8
+#endif
+constexpr int CERT_MAX_WARPS = TVS_CERT_MAX_WARPS;
+
 template <bool PRUNE, bool LONG, bool CERT>
-__global__ void __launch_bounds__(SWEEP_MAX_WARPS * 32, 1) sweep_kernel(SweepParams sp)
+__global__ void __launch_bounds__((CERT ? CERT_MAX_WARPS : SWEEP_MAX_WARPS) * 32, 1) sweep_kernel(SweepParams sp)
 {
     extern __shared__ __align__(16) float smem[];
     float4* tab = reinterpret_cast<float4*>(smem);
@@ -1144,7 +1085,8 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
     // As many resident warps as shared memory and registers allow, in one CTA per SM
     // (each warp stages its own row; the 1/d table is shared by the CTA).
-    const int cap = max_warps > 0 ? std::min(max_warps, SWEEP_MAX_WARPS) : SWEEP_MAX_WARPS;
+    const int most = cert ? CERT_MAX_WARPS : SWEEP_MAX_WARPS;
+    const int cap = max_warps > 0 ? std::min(max_warps, most) : most;
     int warps = (int)std::min<size_t>((smem_optin - fixed) / per_warp, (size_t)cap);
     const size_t smem = fixed + (size_t)warps * per_warp;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -1158,6 +1100,18 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
 }
 
 }  // namespace tvs
+
+extern "C" int tvs_debug_sweep_stats(uint64_t* out, int clear)
+{
+    if (!out) return TVS_ERR_ARG;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, tvs::g_sweep_stats, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess && clear) {
+        const unsigned long long zero[2] = {0, 0};
+        e = cudaMemcpyToSymbol(tvs::g_sweep_stats, zero, sizeof(zero));
+    }
+    return e == cudaSuccess ? TVS_OK : TVS_ERR_CUDA;
+}
 
 extern "C" int tvs_debug_sweep_check(int32_t* out, int clear)
 {

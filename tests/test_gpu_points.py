@@ -1,7 +1,8 @@
 """Singular and multiple viewsheds of a list of POVs (tvs_viewshed_points):
 the sDEM mode gives the total viewshed map's value at each cell bit for bit,
 the direct mode (Alg. 1-3, lines through the cell itself) matches the
-oracle's definition."""
+oracle's definition -- with certified decisions (the default) the FP64
+definition, with FP32 decisions the oracle's FP32-decision mode."""
 import numpy as np
 import pytest
 
@@ -16,8 +17,15 @@ FP32_RTOL = 4e-6
 
 @pytest.fixture(scope="module")
 def ctx():
-    # the points walk decides in FP32: its sDEM mode equals the map taken with
-    # FP32 decisions
+    """Certified decisions (the library default)."""
+    c = tvs.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(scope="module")
+def ctx32():
+    """FP32 decisions."""
     c = tvs.Context(0)
     c.set_tuning(fp32_decisions=1)
     yield c
@@ -38,32 +46,33 @@ def _povs(rows, cols, count, seed):
                                                 (3, 257, 16, 0.0, 1.0), (150, 150, 45, 0.0, 0.0),
                                                 (2, 65, 1, 0.0, 1.5), (33, 64, 4, 320.0, 2.0),
                                                 (97, 33, 8, 0.0, 3.0), (3, 16384, 4, 0.0, 1.5)])
-def test_sdem_points_equal_the_total_map(ctx, rows, cols, n, rng, h0):
+def test_sdem_points_equal_the_total_map(ctx, ctx32, rows, cols, n, rng, h0):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.8, 600.0, seed=rows + cols)
     d = torch.from_numpy(dem).cuda()
-    full = ctx.total_viewshed_device(d, 10.0, h0, n, rng)
     povs = _povs(rows, cols, 40, seed=n)
-    got = ctx.viewshed_points(d, 10.0, h0, n, rng, povs, mode="sdem")
-    torch.cuda.synchronize()
-    want = full.cpu().numpy()[povs[:, 0], povs[:, 1]]
-    assert np.array_equal(got.cpu().numpy(), want)
+    for c in (ctx, ctx32):
+        full = c.total_viewshed_device(d, 10.0, h0, n, rng)
+        got = c.viewshed_points(d, 10.0, h0, n, rng, povs, mode="sdem")
+        torch.cuda.synchronize()
+        want = full.cpu().numpy()[povs[:, 0], povs[:, 1]]
+        assert np.array_equal(got.cpu().numpy(), want)
 
 
 @pytest.mark.parametrize("rows,cols,n,rng,h0", [(90, 70, 180, 0.0, 1.5), (60, 130, 24, 700.0, 8.0),
                                                 (33, 64, 4, 320.0, 2.0), (2, 65, 1, 0.0, 1.5)])
-def test_direct_points_match_the_oracle_definition(ctx, orc, rows, cols, n, rng, h0):
+def test_direct_points_match_the_oracle_definition(ctx, ctx32, orc, rows, cols, n, rng, h0):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.75, 500.0, seed=rows * cols)
     d = torch.from_numpy(dem).cuda()
     povs = _povs(rows, cols, 30, seed=rows)
-    got = ctx.viewshed_points(d, 10.0, h0, n, rng, povs, mode="direct").cpu().numpy()
     cells = povs[:, 0].astype(np.int64) * cols + povs[:, 1]
-    o32 = orc.direct_viewshed(dem, 10.0, h0, n, rng, prec=32, cells=cells)
-    np.testing.assert_allclose(got, o32, rtol=FP32_RTOL, atol=0)
+    got = ctx.viewshed_points(d, 10.0, h0, n, rng, povs, mode="direct").cpu().numpy()
     o64 = orc.direct_viewshed(dem, 10.0, h0, n, rng, prec=64, cells=cells)
-    rel = np.abs(got - o64) / o64
-    assert np.mean(rel <= 1e-4) >= 0.9 and rel.max() <= 5e-2
+    np.testing.assert_allclose(got, o64, rtol=FP32_RTOL, atol=0)
+    got32 = ctx32.viewshed_points(d, 10.0, h0, n, rng, povs, mode="direct").cpu().numpy()
+    o32 = orc.direct_viewshed(dem, 10.0, h0, n, rng, prec=32, cells=cells)
+    np.testing.assert_allclose(got32, o32, rtol=FP32_RTOL, atol=0)
 
 
 def test_direct_equals_sdem_when_lines_hit_cell_centres(ctx):
@@ -118,17 +127,18 @@ def _ambiguous(rows, cols, n, povs, eps=1e-9):
                                                      (2000, 2000, 180, 0.0, 1.5, 2), (33, 64, 4, 320.0, 2.0, 4),
                                                      (150, 170, 1000, 0.0, 5.0, 3), (41, 37, 12, 0.0, 1.5, 6),
                                                      (3, 16384, 4, 0.0, 1.5, 3)])
-def test_visibility_map_matches_the_oracle(ctx, orc, rows, cols, n, rng, h0, npov):
+def test_visibility_map_matches_the_oracle(ctx, ctx32, orc, rows, cols, n, rng, h0, npov):
     import torch
     dem = terrain.fractal_dem(rows, cols, 0.8, 900.0 if rows < 1000 else 1500.0, seed=rows + n)
     d = torch.from_numpy(dem).cuda()
     povs = _povs(rows, cols, npov, seed=rows + 1)[:npov]
-    got = ctx.visibility_map(d, 10.0, h0, n, rng, povs).cpu().numpy()
-    want = orc.visibility_map(dem, 10.0, h0, n, rng, prec=32, povs=povs)
     amb = _ambiguous(rows, cols, n, povs)
     assert amb.mean() < 1e-3
-    assert np.array_equal(got[~amb], want[~amb])
-    assert got.max() <= npov and all(got[p[0], p[1]] >= 1 for p in povs)
+    for c, prec in ((ctx, 64), (ctx32, 32)):
+        got = c.visibility_map(d, 10.0, h0, n, rng, povs).cpu().numpy()
+        want = orc.visibility_map(dem, 10.0, h0, n, rng, prec=prec, povs=povs)
+        assert np.array_equal(got[~amb], want[~amb]), prec
+        assert got.max() <= npov and all(got[p[0], p[1]] >= 1 for p in povs)
 
 
 def test_visibility_map_refuses_bad_arguments(ctx):

@@ -63,6 +63,31 @@ def test_results_are_the_same_alone_and_in_the_mix(alone, policy):
         assert 0.0 <= q["t_submit"] <= q["t_admit"] <= q["t_first"] <= q["t_done"]
 
 
+# FP32 blend and FP32 group sums of 8 directions against the FP64 sums
+FP32_RTOL = 4e-6
+
+
+def test_served_results_match_the_fp64_oracle(alone, orc):
+    """Every served result against the oracle itself (FP64 definition):
+    certified decisions make each per-sample measure the definition's, so a
+    served area differs from the oracle's only by single-precision sums --
+    every cell of the small requests, 400 sampled cells of the largest."""
+    dems, _ = alone
+    with tvs.Server(0, hbm_budget_bytes=2 * SLOT + (64 << 20), step_slot_bytes=SLOT, step_evals=3e8,
+                    policy="deadline") as srv:
+        tickets = _submit_all(srv, dems)
+        outs = {i: srv.wait(t, timeout=300) for i, t in tickets.items()}
+    for i, (r, c, n, step, h0, rng) in enumerate(REQS):
+        if r * c <= 40000:
+            want = orc.total_viewshed(dems[i], step, h0, n, rng, prec=64)
+            np.testing.assert_allclose(outs[i], want, rtol=FP32_RTOL, atol=0, err_msg=f"request {i}")
+        else:
+            cells = np.random.default_rng(i).choice(r * c, size=400, replace=False)
+            want = orc.total_viewshed(dems[i], step, h0, n, rng, prec=64, cells=cells)
+            np.testing.assert_allclose(outs[i].ravel()[cells], want, rtol=FP32_RTOL, atol=0,
+                                       err_msg=f"request {i}")
+
+
 def test_late_arrivals_join_and_finish_first(alone):
     """Small requests submitted while a large one runs join its next steps and,
     under the deadline policy, finish before it."""
