@@ -294,6 +294,7 @@ def run_ours(args) -> int:
     torch.cuda.synchronize(device)
     sampler.start()
     ctx.profile(True)
+    tvs.sweep_stats(clear=True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     for k in range(args.steps):
@@ -306,6 +307,15 @@ def run_ours(args) -> int:
     clocks = sampler.stop()
     stats = ctx.profile_read()
     ctx.profile(False)
+    cert = tvs.sweep_stats(clear=True)
+    walks = 2 * w["rows"] * w["cols"] * w["n"] * args.steps
+    certified = {"exact_walks_per_step": cert["exact_walks"] / args.steps,
+                 "fp64_walks_per_step": cert["fp64_walks"] / args.steps,
+                 "exact_walk_fraction": cert["exact_walks"] / walks,
+                 "exact_share_of_sweep_time": cert["exact_cycles"] / max(cert["sweep_cycles"], 1),
+                 "note": "walks (POV x direction x side) whose FP32 fast path had a decision inside its proven "
+                         "margin and were walked again exactly (double-float, FP64 past its margin); the share "
+                         "is of the warps' SM cycles in the sweep"}
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     local_s = sum(step_ms) / 1e3
     total_evals, max_s = aggregate(float(E) * args.steps, local_s, dist, device)
@@ -404,6 +414,7 @@ def run_ours(args) -> int:
                      f"{FP32_LANES_PER_SM} FP32 lanes x {sm_max_mhz:g} MHz / {OPS_PER_EVAL} ops per eval "
                      "(MEASURED_PEAKS sm_max_mhz)"},
         "kernels": kernels,
+        "certified": certified,
         "e2e": {"value": e2e_evals / e2e_max / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(dem_np.nbytes),
                 "d2h_bytes_per_step": int(dem_np.nbytes), "api": "tvs_total_viewshed (host buffers, pinned)",
                 "ms_per_step": e2e_local / e2e_steps * 1e3, "finite": ok_e2e},

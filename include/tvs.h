@@ -273,8 +273,10 @@ int tvs_debug_sweep_check(int32_t* out, int clear);
 /* Test and profiling hook: event counts of the certified sweep on the current
  * device since the last clear, after a device synchronisation: out[0] exact
  * walks (POVs with a decision inside its FP32 margin), out[1] of them walked
- * in FP64 (a decision inside the double-float margin too).  Errors:
- * TVS_ERR_ARG, TVS_ERR_CUDA. */
+ * in FP64 (a decision inside the double-float margin too), out[2] SM clock
+ * cycles warps spent walking flagged POVs exactly, out[3] cycles warps spent
+ * in the certified sweep in all (out[2] / out[3] is the share of the exact
+ * walks).  out holds 4 entries.  Errors: TVS_ERR_ARG, TVS_ERR_CUDA. */
 int tvs_debug_sweep_stats(uint64_t* out, int clear);
 
 /* Turn per-kernel timing on (1) or off (0); turning it on clears the counters.

@@ -188,10 +188,12 @@ def sweep_check(clear: bool = True) -> list[int]:
 
 def sweep_stats(clear: bool = True) -> dict:
     """tvs_debug_sweep_stats: event counts of the certified sweep on the
-    current device (exact walks, FP64 walks)."""
-    out = (C.c_uint64 * 2)()
+    current device (exact walks, FP64 walks, warp cycles in exact walks and
+    in the sweep)."""
+    out = (C.c_uint64 * 4)()
     _check(load().tvs_debug_sweep_stats(out, int(clear)))
-    return {"exact_walks": int(out[0]), "fp64_walks": int(out[1])}
+    return {"exact_walks": int(out[0]), "fp64_walks": int(out[1]), "exact_cycles": int(out[2]),
+            "sweep_cycles": int(out[3])}
 
 
 def count_evals(rows: int, cols: int, n_sectors: int, step_m: float = 1.0, max_range_m: float = 0.0) -> int:

@@ -50,8 +50,10 @@ __device__ __forceinline__ void df_blend(float va, float vb, unsigned fr, float&
     two_sum(sh, lo, zh, zl);
 }
 
-// Double-float slope (z - h) / d of a staged target against the observer h.
-__device__ __forceinline__ void df_slope(float zh, float zl, float hh, float hl, int d, float& qh, float& ql)
+// Double-float slope (z - h) / d of a staged target against the observer h,
+// given iv = fl(1/d) (correctly rounded, as __frcp_rn returns it).
+__device__ __forceinline__ void df_slope_iv(float zh, float zl, float hh, float hl, int d, float iv, float& qh,
+                                            float& ql)
 {
     float s, e;
     two_sum(zh, -hh, s, e);
@@ -59,12 +61,16 @@ __device__ __forceinline__ void df_slope(float zh, float zl, float hh, float hl,
     float Dh, Dl;
     two_sum(s, e, Dh, Dl);
     const float fd = (float)d;
-    const float iv = __frcp_rn(fd);
     const float q1 = __fmul_rn(Dh, iv);
     const float ph = __fmul_rn(q1, fd);
     const float pl = __fmaf_rn(q1, fd, -ph);
     const float r = __fadd_rn(__fsub_rn(__fsub_rn(Dh, ph), pl), Dl);
     fast_two_sum(q1, __fmul_rn(r, iv), qh, ql);
+}
+
+__device__ __forceinline__ void df_slope(float zh, float zl, float hh, float hl, int d, float& qh, float& ql)
+{
+    df_slope_iv(zh, zl, hh, hl, d, __frcp_rn((float)d), qh, ql);
 }
 
 }  // namespace df

@@ -41,8 +41,9 @@ namespace tvs {
 // tvs_debug_sweep_check.
 __device__ int g_sweep_check[4];
 // Event counts of the certified sweep: exact walks (flagged POVs), of them
-// FP64 walks.
-__device__ unsigned long long g_sweep_stats[2];
+// FP64 walks, SM clock cycles warps spent in exact walks, and cycles warps
+// spent in the certified sweep kernels in all.
+__device__ unsigned long long g_sweep_stats[4];
 
 __device__ __forceinline__ bool in_range(long long idx, long long bound, int code)
 {
@@ -72,6 +73,7 @@ struct SweepParams {
     int ndir;
     int total_items;
     int inv_len;       // entries of the per-distance table (float4 each)
+    int tab_slots;     // float4 slots the table takes (the certified kernels skew it)
     int istart_len;    // ints of the item-start table (multiple of 4)
     int half;          // floats of one staged row array (multiple of 4)
     int zs_len;        // floats of the row's suffix maxima (0 without pruning)
@@ -254,7 +256,7 @@ __device__ __forceinline__ void sweep_block(const float* w, const float4* __rest
 // FLUSH_STEPS steps at d < 16384 add at most 1.1e7).  Shorter walks never
 // flush (the LONG = false instantiation).
 constexpr int LONG_WALK = 4000;
-constexpr int FLUSH_STEPS = 336;   // a multiple of SMALL_UNROLL and LARGE_UNROLL
+constexpr int FLUSH_STEPS = 336;   // a multiple of SMALL_UNROLL, LARGE_UNROLL and 24
 // Suffix maxima of a staged row are kept at every ZS_STRIDE-th sample; pruning
 // checks every PRUNE_EVERY blocks.
 constexpr int ZS_STRIDE = 4;
@@ -419,18 +421,20 @@ __device__ __forceinline__ void suffix_max(const float* __restrict__ F, float* _
 // ------------------------------------------------ certified decisions --
 //
 // The fast path of a group of P POVs x0 .. x0 + P - 1 works on differences
-// against the group's reference R = z(x0) (a double-float): per block it
-// forms, for every target t of its window, y_t = fl(fl(zh_t - Rh) + fl(zl_t -
-// Rl)), and per POV q once g_q = fl(fl(fl(zh_q - Rh) + fl(zl_q - Rl)) + h0).
-// Then, for POV q and target t at distance d,
+// against the group's reference R = zh(x0) (the hi part of its first
+// sample, a float): per block it forms, for every target t of its window,
+// y_t = fl(fl(zh_t - R) + zl_t), and per POV q once g_q = fl(fl(fl(zh_q -
+// R) + zl_q) + h0).  Then, for POV q and target t at distance d,
 //     diff = fl(y_t - g_q),  x = fl(diff * fl(1/d)),  s = fl(x - M_q),
 // visible iff s > 0 (the sign of s is exact), M_q = max(M_q, x).
 //
 // Error bound (u = 2^-24; D = z_t - h_q exact, theta = D / d, G = h_q - R):
-//   |y_t - (z_t - R)| <= 2u |z_t - R| + 2 eta,  |g_q - G| <= 3.01u |G| +
-//   2.01u |h0| + |h0 - float(h0)| + 2 eta  (eta: the staged heights' error),
-//   so |diff - D| <= 3.01u |D| + Eg with Eg = 5.02u |G| + 2.01u |h0| +
-//   |h0 - float(h0)| + 4 eta, and |x - theta| <= 5.04u |theta| + 1.01 Eg / d.
+//   |y_t - (z_t - R)| <= 2u |z_t - R| + 2 eta (eta: the staged heights'
+//   error, which also covers the u |zl_t| <= 2^-48 |z_t| of adding zl_t
+//   after the subtraction), |g_q - G| <= 3.01u |G| + 2.01u |h0| + |h0 -
+//   float(h0)| + 2 eta, so |diff - D| <= 3.01u |D| + Eg with Eg = 5.02u |G|
+//   + 2.01u |h0| + |h0 - float(h0)| + 4 eta, and |x - theta| <= 5.04u
+//   |theta| + 1.01 Eg / d.
 // M_q is the x of the last visible target a (the maximum is exact), so with
 // every earlier decision right, comparing x_t with M_q errs by at most
 //   5.04u (|theta_t| + |theta_a|) + 1.01 Eg (1/d_t + 1/d_a).
@@ -454,9 +458,11 @@ constexpr float CERT_FLOOR = 0x1p-99f;
 constexpr int WM_SPAN = 40;
 static_assert(LARGE_POV + LARGE_UNROLL <= WM_SPAN && SMALL_POV + SMALL_UNROLL <= WM_SPAN, "window span");
 static_assert(WM_SPAN + 4 <= ROW_PADR, "window maxima read into the right pad");
-// Steps per unrolled block of the certified walk with LARGE_POV groups: its
-// step is about 40 % longer than the FP32 one, and a 28-step block of it no
-// longer stays in the instruction cache.
+// Group size and steps per unrolled block of every certified walk.  A
+// certified step takes about 40 % more instructions than an FP32 one and its
+// state per POV twice the registers: groups of 4 POVs, and blocks short
+// enough that the margin of a block (which grows with its window) stays
+// tight.
 #ifndef TVS_CERT_UNROLL
 #define TVS_CERT_UNROLL 16
 #endif
@@ -465,7 +471,19 @@ constexpr int CERT_UNROLL = TVS_CERT_UNROLL;
 #define TVS_CERT_POV SMALL_POV
 #endif
 constexpr int CERT_POV = TVS_CERT_POV;
+static_assert(CERT_POV + CERT_UNROLL <= WM_SPAN, "window span");
 static_assert(FLUSH_STEPS % CERT_UNROLL == 0, "long walks flush on block boundaries");
+// The certified kernels store distance entry m at slot m + m / TAB_SKEW.  A
+// lane reads entries e .. e + U - 1 of its own block start e (a multiple of
+// U = TAB_SKEW); groups of different lengths leave the lanes of a warp at
+// different e, and unskewed such reads would fall on a few of the eight
+// 16-byte bank groups.  Skewed, entry u of block k sits in bank group
+// ((U + 1) k + u) mod 8, which spreads blocks k over all eight.
+constexpr int TAB_SKEW = CERT_UNROLL;
+__host__ __device__ constexpr int tab_slots_for(int entries, bool skew)
+{
+    return skew ? ((entries + entries / TAB_SKEW + 1 + 1) & ~1) : entries;
+}
 // Entries of a warp's flagged-POV list (at least 32 lanes x LARGE_POV).
 constexpr int FLAG_CAP = 256;
 // Targets per lane per chunk of an exact walk.
@@ -511,7 +529,16 @@ struct ExactCtx {
     int p, jlo;
     int half;            // floats of a staged row array (index bound, with ROW_PADL)
     int zs_len, wm_len;  // entries of the suffix and window maxima
+    const float4* tab;   // the distance table (skewed: entry m at m + m / TAB_SKEW)
+    int tabn;            // its entries
 };
+
+// fl(1/d), correctly rounded: from the distance table while it reaches d.
+__device__ __forceinline__ float inv_d(const ExactCtx& c, int d)
+{
+    const int m = d - 1;
+    return m < c.tabn ? c.tab[m + m / TAB_SKEW].x : __frcp_rn((float)d);
+}
 
 // FP64 height of staged sample xs exactly as the FP64 definition forms it:
 // (1 - r) * a + r * b with r = fr / 2^32, every operation rounded.
@@ -598,16 +625,17 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
     int acc = 0;
     bool esc = false;
     for (int base = 1; base <= last; base += 32 * XW_KPL) {
-        float th[XW_KPL], tl[XW_KPL];
+        float th[XW_KPL], tl[XW_KPL], iv[XW_KPL];
         float mh = NEG, ml = 0.f;
         int md = 1;
         const int d0 = base + lane * XW_KPL;
 #pragma unroll
         for (int k = 0; k < XW_KPL; ++k) {
             const int d = d0 + k;
-            th[k] = NEG; tl[k] = 0.f;
+            th[k] = NEG; tl[k] = 0.f; iv[k] = 1.f;
             if (d <= last && in_range(ROW_PADL + x + d, c.half, 15)) {
-                df::df_slope(c.H[x + d], c.Lo[x + d], hh, hl, d, th[k], tl[k]);
+                iv[k] = inv_d(c, d);
+                df::df_slope_iv(c.H[x + d], c.Lo[x + d], hh, hl, d, iv[k], th[k], tl[k]);
                 if (df::df_gt(th[k], tl[k], mh, ml)) { mh = th[k]; ml = tl[k]; md = d; }
             }
         }
@@ -625,6 +653,7 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
         float cl = __shfl_up_sync(0xffffffffu, pl, 1);
         int cd = __shfl_up_sync(0xffffffffu, pd, 1);
         if (lane == 0 || df::df_gt(rh, rl, ch, cl)) { ch = rh; cl = rl; cd = rd; }
+        float icd = inv_d(c, cd);
 #pragma unroll
         for (int k = 0; k < XW_KPL; ++k) {
             const int d = d0 + k;
@@ -634,14 +663,13 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
                 float s, e;
                 df::two_sum(th[k], -ch, s, e);
                 const float dh = __fadd_rn(s, __fadd_rn(e, __fsub_rn(tl[k], cl)));
-                const float marg = __fmaf_rn(0x1p-40f, fabsf(th[k]) + fabsf(ch),
-                                             4.04f * c.eta * (__frcp_rn((float)d) + __frcp_rn((float)cd))) +
+                const float marg = __fmaf_rn(0x1p-40f, fabsf(th[k]) + fabsf(ch), 4.04f * c.eta * (iv[k] + icd)) +
                                    0x1p-120f;
                 if (!(fabsf(dh) > marg)) esc = true;
                 v = dh > 0.f;
             }
             if (v) acc += 2 * d + 1;
-            if (df::df_gt(th[k], tl[k], ch, cl)) { ch = th[k]; cl = tl[k]; cd = d; }
+            if (df::df_gt(th[k], tl[k], ch, cl)) { ch = th[k]; cl = tl[k]; cd = d; icd = iv[k]; }
         }
         const float lh = __shfl_sync(0xffffffffu, ph, 31);
         const float ll = __shfl_sync(0xffffffffu, pl, 31);
@@ -680,8 +708,10 @@ struct FlagList {
 __device__ __noinline__ void drain_flags(FlagList& fl, const ExactCtx& c, int lane)
 {
     __syncwarp();
+    const long long t0 = clock64();
     for (int i = 0; i < fl.count; ++i) exact_walk(c, fl.list[i], lane);
     fl.count = 0;
+    if (lane == 0) atomicAdd(&g_sweep_stats[2], (unsigned long long)(clock64() - t0));
     __syncwarp();
 }
 
@@ -705,33 +735,58 @@ __device__ __forceinline__ void flag_push(FlagList& fl, const ExactCtx& c, unsig
     __syncwarp();
 }
 
-// U certified steps of one lane's P POVs (see the derivation above).  y[m] is
-// the window's target x0 + e + m relative to R, g[q] the POV's height relative
-// to R.  mn[q] keeps the smallest |s| of the POV's steps: the block's margin
-// test (mn < delta) runs once at its end.
+// min(a, |b|, |c|).  TVS_CERT_MIN3 selects the three-input minimum of
+// sm_100+ (one instruction for two steps of a POV) or two chained minima.
+#ifndef TVS_CERT_MIN3
+#define TVS_CERT_MIN3 1
+#endif
+__device__ __forceinline__ float min_abs2(float a, float b, float c)
+{
+#if TVS_CERT_MIN3
+    float r;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(r) : "f"(a), "f"(fabsf(b)), "f"(fabsf(c)));
+    return r;
+#else
+    return fminf(fminf(a, fabsf(b)), fabsf(c));
+#endif
+}
+
+// U certified steps of one lane's P POVs (see the derivation above), two
+// steps at a time.  y[m] is the window's target x0 + e + m relative to R,
+// g[q] the POV's height relative to R.  mn[q] keeps the smallest |s| of the
+// POV's steps: the block's margin test (mn < delta) runs once at its end.
 template <int P, int U, bool MASKED, bool FAR>
 __device__ __forceinline__ void cert_block(const float* y, const float4* __restrict__ tab, int e, const float* g,
                                            float2* M2, float2* acc2, float* mn, int nvalid)
 {
+    static_assert(U % 2 == 0, "steps go in pairs");
 #pragma unroll
-    for (int u = 0; u < U; ++u) {
-        const float4 t4 = FAR ? dist_entry(e + u + 1) : tab[u];
-        const float2 iv = make_float2(t4.x, t4.y);
-        float2 cp = make_float2(t4.z, t4.w);
-        if (MASKED && u >= nvalid) cp = make_float2(0.f, 0.f);
+    for (int u = 0; u < U; u += 2) {
+        float2 sv[2][P / 2];
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int w = u + k;
+            const float4 t4 = FAR ? dist_entry(e + w + 1) : tab[w + w / TAB_SKEW];
+            const float2 iv = make_float2(t4.x, t4.y);
+            float2 cp = make_float2(t4.z, t4.w);
+            if (MASKED && w >= nvalid) cp = make_float2(0.f, 0.f);
+#pragma unroll
+            for (int q = 0; q < P; q += 2) {
+                const float2 d = make_float2(__fsub_rn(y[q + w + 1], g[q]), __fsub_rn(y[q + w + 2], g[q + 1]));
+                const float2 x = __fmul2_rn(d, iv);
+                const float2 sp = __ffma2_rn(make_float2(-1.f, -1.f), M2[q / 2], x);
+                const float2 v = make_float2(sat_pos(sp.x), sat_pos(sp.y));
+                acc2[q / 2] = __ffma2_rn(v, cp, acc2[q / 2]);
+                M2[q / 2].x = fmaxf(M2[q / 2].x, x.x);
+                M2[q / 2].y = fmaxf(M2[q / 2].y, x.y);
+                // a masked step's |s| is +inf: it takes no part in the test
+                sv[k][q / 2] = (MASKED && w >= nvalid) ? make_float2(pos_inf(), pos_inf()) : sp;
+            }
+        }
 #pragma unroll
         for (int q = 0; q < P; q += 2) {
-            const float2 d = make_float2(__fsub_rn(y[q + u + 1], g[q]), __fsub_rn(y[q + u + 2], g[q + 1]));
-            const float2 x = __fmul2_rn(d, iv);
-            const float2 s = __ffma2_rn(make_float2(-1.f, -1.f), M2[q / 2], x);
-            const float2 v = make_float2(sat_pos(s.x), sat_pos(s.y));
-            acc2[q / 2] = __ffma2_rn(v, cp, acc2[q / 2]);
-            M2[q / 2].x = fmaxf(M2[q / 2].x, x.x);
-            M2[q / 2].y = fmaxf(M2[q / 2].y, x.y);
-            if (!MASKED || u < nvalid) {
-                mn[q] = fminf(mn[q], fabsf(s.x));
-                mn[q + 1] = fminf(mn[q + 1], fabsf(s.y));
-            }
+            mn[q] = min_abs2(mn[q], sv[0][q / 2].x, sv[1][q / 2].x);
+            mn[q + 1] = min_abs2(mn[q + 1], sv[0][q / 2].y, sv[1][q / 2].y);
         }
     }
 }
@@ -759,6 +814,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                                                int tabn, int* __restrict__ spill, float eg0, FlagList& fl, int lane)
 {
     static_assert(P % 4 == 0 && U % 4 == 0, "window loads must stay 16-byte aligned");
+    static_assert(U % TAB_SKEW == 0, "a block's table entries must sit at one skewed offset");
     const unsigned FULL = 0xffffffffu;
     const unsigned below = (1u << lane) - 1u;
     const float NEG = neg_inf();
@@ -770,7 +826,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
     float g[P], ia[P];
     float2 M2[P / 2], acc2[P / 2];   // running maxima of POV pairs (packed x - M)
 #define CERT_M(q) ((q) % 2 ? M2[(q) / 2].y : M2[(q) / 2].x)
-    float Rh = 0.f, Rl = 0.f, gmin = 0.f, c2e = 0.f;
+    float Rh = 0.f, gmin = 0.f, c2e = 0.f;
     unsigned mask = 0u;
     int gi = lane, next = 32;
     int x0 = 0, e = 0, dlim = -1, seg = FLUSH_STEPS;
@@ -803,7 +859,6 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             return;
         }
         Rh = H[x0];
-        Rl = Lo[x0];
         float gmax = 0.f;
         gmin = pos_inf();
 #pragma unroll
@@ -811,7 +866,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             const int x = x0 + q;
             float gq = 0.f;
             if (x <= L - 2) {
-                gq = __fadd_rn(__fadd_rn(__fsub_rn(H[x], Rh), __fsub_rn(Lo[x], Rl)), xc.h0h);
+                gq = __fadd_rn(__fadd_rn(__fsub_rn(H[x], Rh), Lo[x]), xc.h0h);
                 gmin = fminf(gmin, gq);
             }
             g[q] = gq;
@@ -824,7 +879,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             // area): M starts just below its slope, so that target is visible
             // and outside its margin, and the maximum then is its slope exactly
             const int x = x0 + q;
-            const float y1 = __fadd_rn(__fsub_rn(H[x + 1], Rh), __fsub_rn(Lo[x + 1], Rl));
+            const float y1 = __fadd_rn(__fsub_rn(H[x + 1], Rh), Lo[x + 1]);
             const float x1 = __fsub_rn(y1, g[q]);
             const float C = __fmaf_rn(0x1p-6f, fabsf(x1), __fmaf_rn(4.f, c2e, 0x1p-16f));
             // a POV with no target that adds area (x >= L - 2) starts at +inf:
@@ -873,7 +928,8 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             // margins of this block.  The bounds are formed branch-free: a
             // window or suffix of sentinels only (-inf) gives 0.
             const bool far = LONG && e + U > tabn;
-            const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tab[e].x;
+            const float4* __restrict__ tb = tab + e + e / TAB_SKEW;
+            const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tb->x;
             const float Bw = bound_slope(WM[(x0 + e) >> 2], Rh, gmin, c2e, ive);
             const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
             float dl[P], Ms[P], mn[P];
@@ -893,27 +949,25 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             // the window, relative to R
             float y[P + U];
             {
-                const float2 nRh = make_float2(-Rh, -Rh), nRl = make_float2(-Rl, -Rl);
+                const float2 nRh = make_float2(-Rh, -Rh);
                 const float* bh = H + x0 + e;
                 const float* bl = Lo + x0 + e;
 #pragma unroll
                 for (int m = 0; m < P + U; m += 4) {
                     const float4 a = *reinterpret_cast<const float4*>(bh + m);
                     const float4 b = *reinterpret_cast<const float4*>(bl + m);
-                    const float2 y0 = __fadd2_rn(__fadd2_rn(make_float2(a.x, a.y), nRh),
-                                                 __fadd2_rn(make_float2(b.x, b.y), nRl));
-                    const float2 y1 = __fadd2_rn(__fadd2_rn(make_float2(a.z, a.w), nRh),
-                                                 __fadd2_rn(make_float2(b.z, b.w), nRl));
+                    const float2 y0 = __fadd2_rn(__fadd2_rn(make_float2(a.x, a.y), nRh), make_float2(b.x, b.y));
+                    const float2 y1 = __fadd2_rn(__fadd2_rn(make_float2(a.z, a.w), nRh), make_float2(b.z, b.w));
                     y[m] = y0.x; y[m + 1] = y0.y; y[m + 2] = y1.x; y[m + 3] = y1.y;
                 }
             }
             const bool masked = klimited && e + U > dlim;
             if (masked) {
                 if (far) cert_block<P, U, true, true>(y, tab, e, g, M2, acc2, mn, dlim - e);
-                else cert_block<P, U, true, false>(y, tab + e, e, g, M2, acc2, mn, dlim - e);
+                else cert_block<P, U, true, false>(y, tb, e, g, M2, acc2, mn, dlim - e);
             } else {
                 if (far) cert_block<P, U, false, true>(y, tab, e, g, M2, acc2, mn, U);
-                else cert_block<P, U, false, false>(y, tab + e, e, g, M2, acc2, mn, U);
+                else cert_block<P, U, false, false>(y, tb, e, g, M2, acc2, mn, U);
             }
 #pragma unroll
             for (int q = 0; q < P; ++q) mask |= mn[q] < dl[q] ? 1u << q : 0u;
@@ -943,10 +997,7 @@ __device__ __forceinline__ void sweep_item_cert(const ItemRow& it, const ExactCt
                                                 const float* WM, const float4* tab, int tabn, int* spill, float eg0,
                                                 FlagList& fl, int lane)
 {
-    if (it.pov == SMALL_POV)
-        sweep_row_cert<SMALL_POV, SMALL_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
-    else
-        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
+    sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
 }
 
 // PRUNE: exact horizon pruning; LONG: the launch holds rows with walks of
@@ -954,12 +1005,13 @@ __device__ __forceinline__ void sweep_item_cert(const ItemRow& it, const ExactCt
 // certified decisions.  Per warp, shared memory holds the staged row (hi
 // parts; CERT: lo parts after them), the suffix maxima (PRUNE), the window
 // maxima and the flagged-POV list (CERT), and the long-walk spill (LONG).
-// Warps per CTA of the certified kernels: their per-lane state (8 POVs'
+// Warps per CTA of the certified kernels: their per-lane state (4 POVs'
 // maxima, heights, margins and last-visible bounds, the window relative to
-// the group) needs more than 128 registers, and at 2000-sample rows the two
-// staged arrays already limit a CTA to about 8 warps of shared memory.
+// the group) takes about 160 registers, which 12 warps still leave every
+// thread; at 2000-sample rows the two staged arrays limit a CTA to 8 warps of
+// shared memory anyway.
 #ifndef TVS_CERT_MAX_WARPS
-#define TVS_CERT_MAX_WARPS 8
+#define TVS_CERT_MAX_WARPS 12
 #endif
 constexpr int CERT_MAX_WARPS = TVS_CERT_MAX_WARPS;
 
@@ -968,9 +1020,9 @@ __global__ void __launch_bounds__((CERT ? CERT_MAX_WARPS : SWEEP_MAX_WARPS) * 32
 {
     extern __shared__ __align__(16) float smem[];
     float4* tab = reinterpret_cast<float4*>(smem);
-    int* istart = reinterpret_cast<int*>(smem + 4 * sp.inv_len);
+    int* istart = reinterpret_cast<int*>(smem + 4 * sp.tab_slots);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    float* Fh = smem + 4 * sp.inv_len + sp.istart_len + warp * sp.per_warp;
+    float* Fh = smem + 4 * sp.tab_slots + sp.istart_len + warp * sp.per_warp;
     float* Fl = Fh + sp.half;
     float* ZS = Fh + (CERT ? 2 : 1) * sp.half;
     float* WM = ZS + sp.zs_len;
@@ -980,11 +1032,12 @@ __global__ void __launch_bounds__((CERT ? CERT_MAX_WARPS : SWEEP_MAX_WARPS) * 32
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
         const float r = __frcp_rn((float)(m + 1));
         const float c = (float)(2 * m + 3);
-        tab[m] = make_float4(r, r, c, c);
+        tab[CERT ? m + m / TAB_SKEW : m] = make_float4(r, r, c, c);
     }
     for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
     __syncthreads();
     FlagList fl{flist, 0};
+    const long long t_start = CERT ? clock64() : 0;
 
     int next = 0;
     if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
@@ -1023,6 +1076,8 @@ __global__ void __launch_bounds__((CERT ? CERT_MAX_WARPS : SWEEP_MAX_WARPS) * 32
             xc.half = sp.half;
             xc.zs_len = sp.zs_len;
             xc.wm_len = sp.wm_len;
+            xc.tab = tab;
+            xc.tabn = sp.inv_len;
             const float u = 0x1p-24f;
             const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
             sweep_item_cert<LONG, PRUNE>(it, xc, ZS, WM, tab, sp.inv_len, spill, eg0, fl, lane);
@@ -1030,6 +1085,7 @@ __global__ void __launch_bounds__((CERT ? CERT_MAX_WARPS : SWEEP_MAX_WARPS) * 32
             sweep_item<LONG, PRUNE>(it, Fh, ZS, tab, sp.inv_len, cvrow, spill, lane);
         }
     }
+    if (CERT && lane == 0) atomicAdd(&g_sweep_stats[3], (unsigned long long)(clock64() - t_start));
 }
 
 }  // namespace
@@ -1053,6 +1109,7 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     // the distance table is read up to d = dmax + U (a walk of at most
     // min(K, W) - 1 steps, rounded up to U); dmax <= wmax
     sp.inv_len = (std::min(dmax, wmax) + 2 * U + 8 + 1) & ~1;
+    sp.tab_slots = tab_slots_for(sp.inv_len, cert != 0);
     sp.istart_len = (ndir + 1 + 3) & ~3;
     sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
     const bool longw = wmax - 2 > LONG_WALK && dmax - 1 > LONG_WALK;
@@ -1068,7 +1125,7 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
         kern = prune ? (longw ? sweep_kernel<true, true, false> : sweep_kernel<true, false, false>)
                      : (longw ? sweep_kernel<false, true, false> : sweep_kernel<false, false, false>);
     const size_t per_warp = (size_t)sp.per_warp * 4;
-    size_t fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
+    size_t fixed = (size_t)(4 * sp.tab_slots + sp.istart_len) * 4;
     if (longw && fixed + (size_t)LONG_MIN_WARPS * per_warp > (size_t)smem_optin) {
         // Rows of more than about 10^4 samples: the whole table and several
         // staged rows do not fit together.  Keep LONG_MIN_WARPS warps (or as
@@ -1076,11 +1133,15 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
         // entries); the long-walk sweep computes the entries past its end.
         const size_t base = (size_t)sp.istart_len * 4;
         int w = LONG_MIN_WARPS;
-        while (w > 1 && base + (size_t)MIN_TABLE * 16 + (size_t)w * per_warp > (size_t)smem_optin) --w;
-        if (base + (size_t)w * per_warp >= (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+        const size_t min_tab = (size_t)tab_slots_for(MIN_TABLE, cert != 0) * 16;
+        while (w > 1 && base + min_tab + (size_t)w * per_warp > (size_t)smem_optin) --w;
+        if (base + 16 * 4 + (size_t)w * per_warp >= (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+        // slots that fit, and the most entries whose slots do
         const size_t room = ((size_t)smem_optin - base - (size_t)w * per_warp) / 16;
-        sp.inv_len = (int)std::min<size_t>((size_t)sp.inv_len, room) & ~1;
-        fixed = (size_t)(4 * sp.inv_len + sp.istart_len) * 4;
+        const size_t fit = cert ? (room - 2) * TAB_SKEW / (TAB_SKEW + 1) : room;
+        sp.inv_len = (int)std::min<size_t>((size_t)sp.inv_len, fit) & ~1;
+        sp.tab_slots = tab_slots_for(sp.inv_len, cert != 0);
+        fixed = (size_t)(4 * sp.tab_slots + sp.istart_len) * 4;
     }
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
     // As many resident warps as shared memory and registers allow, in one CTA per SM
@@ -1105,9 +1166,9 @@ extern "C" int tvs_debug_sweep_stats(uint64_t* out, int clear)
 {
     if (!out) return TVS_ERR_ARG;
     cudaError_t e = cudaDeviceSynchronize();
-    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, tvs::g_sweep_stats, sizeof(unsigned long long) * 2);
+    if (e == cudaSuccess) e = cudaMemcpyFromSymbol(out, tvs::g_sweep_stats, sizeof(unsigned long long) * 4);
     if (e == cudaSuccess && clear) {
-        const unsigned long long zero[2] = {0, 0};
+        const unsigned long long zero[4] = {0, 0, 0, 0};
         e = cudaMemcpyToSymbol(tvs::g_sweep_stats, zero, sizeof(zero));
     }
     return e == cudaSuccess ? TVS_OK : TVS_ERR_CUDA;
