@@ -1008,15 +1008,19 @@ __device__ __forceinline__ void sweep_item_cert(const ItemRow& it, const ExactCt
 // Warps per CTA of the certified kernels: their per-lane state (4 POVs'
 // maxima, heights, margins and last-visible bounds, the window relative to
 // the group) takes about 160 registers, which 12 warps still leave every
-// thread; at 2000-sample rows the two staged arrays limit a CTA to 8 warps of
-// shared memory anyway.
+// thread.  Rows short enough for CERT_WIDE_WARPS staged rows per CTA (about
+// 1000 samples and fewer) take a second instantiation bounded to 128
+// registers: the extra warps hide more latency than its few spills of the
+// group-restart path cost (measured: 1000^2, 52.3 -> 47.7 ms).  At 2000
+// samples the two staged arrays limit a CTA to 9 warps of shared memory.
 #ifndef TVS_CERT_MAX_WARPS
 #define TVS_CERT_MAX_WARPS 12
 #endif
 constexpr int CERT_MAX_WARPS = TVS_CERT_MAX_WARPS;
+constexpr int CERT_WIDE_WARPS = 16;
 
-template <bool PRUNE, bool LONG, bool CERT>
-__global__ void __launch_bounds__((CERT ? CERT_MAX_WARPS : SWEEP_MAX_WARPS) * 32, 1) sweep_kernel(SweepParams sp)
+template <bool PRUNE, bool LONG, bool CERT, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
 {
     extern __shared__ __align__(16) float smem[];
     float4* tab = reinterpret_cast<float4*>(smem);
@@ -1117,13 +1121,14 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     sp.wm_len = cert ? ((wmax + 3) / 4 + 4) & ~3 : 0;
     sp.fl_cap = cert ? FLAG_CAP : 0;
     sp.per_warp = (cert ? 2 : 1) * sp.half + sp.zs_len + sp.wm_len + sp.fl_cap + (longw ? 32 * LARGE_POV : 0);
+    constexpr int CW = CERT_MAX_WARPS, FW = SWEEP_MAX_WARPS;
     void (*kern)(SweepParams);
     if (cert)
-        kern = prune ? (longw ? sweep_kernel<true, true, true> : sweep_kernel<true, false, true>)
-                     : (longw ? sweep_kernel<false, true, true> : sweep_kernel<false, false, true>);
+        kern = prune ? (longw ? sweep_kernel<true, true, true, CW> : sweep_kernel<true, false, true, CW>)
+                     : (longw ? sweep_kernel<false, true, true, CW> : sweep_kernel<false, false, true, CW>);
     else
-        kern = prune ? (longw ? sweep_kernel<true, true, false> : sweep_kernel<true, false, false>)
-                     : (longw ? sweep_kernel<false, true, false> : sweep_kernel<false, false, false>);
+        kern = prune ? (longw ? sweep_kernel<true, true, false, FW> : sweep_kernel<true, false, false, FW>)
+                     : (longw ? sweep_kernel<false, true, false, FW> : sweep_kernel<false, false, false, FW>);
     const size_t per_warp = (size_t)sp.per_warp * 4;
     size_t fixed = (size_t)(4 * sp.tab_slots + sp.istart_len) * 4;
     if (longw && fixed + (size_t)LONG_MIN_WARPS * per_warp > (size_t)smem_optin) {
@@ -1146,9 +1151,14 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
     // As many resident warps as shared memory and registers allow, in one CTA per SM
     // (each warp stages its own row; the 1/d table is shared by the CTA).
-    const int most = cert ? CERT_MAX_WARPS : SWEEP_MAX_WARPS;
+    int most = cert ? CERT_MAX_WARPS : SWEEP_MAX_WARPS;
+    const size_t fit = (smem_optin - fixed) / per_warp;
+    if (cert && !longw && fit >= (size_t)CERT_WIDE_WARPS && (max_warps == 0 || max_warps >= CERT_WIDE_WARPS)) {
+        most = CERT_WIDE_WARPS;
+        kern = prune ? sweep_kernel<true, false, true, CERT_WIDE_WARPS> : sweep_kernel<false, false, true, CERT_WIDE_WARPS>;
+    }
     const int cap = max_warps > 0 ? std::min(max_warps, most) : most;
-    int warps = (int)std::min<size_t>((smem_optin - fixed) / per_warp, (size_t)cap);
+    int warps = (int)std::min<size_t>(fit, (size_t)cap);
     const size_t smem = fixed + (size_t)warps * per_warp;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
