@@ -201,8 +201,8 @@ int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, d
     TVS_CUDA(launch_rowmap(d_dir, 1, v.R, d_lo, d_hi, s), "rowmap launch");
     TVS_CUDA(cudaMemsetAsync(d_cnt, 0, sizeof(unsigned), s), "reset work counter");
     TVS_CUDA(launch_sweep(d_dir, d_jobs, reinterpret_cast<const int*>(ws + L.istart), 1, c.items, d_lo, d_hi, d_cv,
-                          d_cb, v.W, v.K, h->tuning.prune, !h->tuning.fp32_decisions, d_cnt, h->num_sms,
-                          h->smem_optin, h->tuning.sweep_max_warps, s),
+                          d_cb, v.W, v.K, h->tuning.prune, !h->tuning.fp32_decisions, d_cnt, nullptr, nullptr, 0,
+                          h->num_sms, h->smem_optin, h->tuning.sweep_max_warps, s),
              "sweep launch");
     std::vector<int> slab(c.slab_elems), slabb(c.slab_elems), lo(v.R), hi(v.R);
     TVS_CUDA(cudaMemcpyAsync(slab.data(), d_cv, c.slab_elems * 4, cudaMemcpyDeviceToHost, s), "copy cv");
@@ -461,8 +461,8 @@ extern "C" int tvs_total_viewshed_device_noalloc(const float* d_dem, int rows, i
         // the shared array keeps the previous call's contents: the work counter must start at zero
         TVS_CUDA(cudaMemsetAsync(d_counter, 0, sizeof(unsigned), s), "reset work counter");
         TVS_CUDA(launch_sweep(cd, d_job, d_istart + at, nd, istart[at + nd], d_rowlo, d_rowhi, d_cvf, d_cvb, wmax,
-                              dmax, tn.prune, !tn.fp32_decisions, d_counter, num_sms, smem_optin,
-                              tn.sweep_max_warps, s),
+                              dmax, tn.prune, !tn.fp32_decisions, d_counter, nullptr, nullptr, 0, num_sms,
+                              smem_optin, tn.sweep_max_warps, s),
                  "sweep launch");
         TVS_CUDA(launch_unskew(d_cvf, d_cvb, d_job, cd, d_cj + c, 1, tiles, cjs[c].nsplit, d_part, s),
                  "unskew launch");
@@ -541,13 +541,14 @@ int tvs_batch_create(tvs_handle h, const tvs_job* jobs, int njobs, size_t hbm_bu
     if (rc) return rc;
     DeviceGuard g(h->device);
     const size_t budget = hbm_budget_bytes ? hbm_budget_bytes : h->budget;
-    const size_t fixed = fixed_bytes(specs, false, h->num_sms);
+    const size_t mf = budget_flags(budget);
+    const size_t fixed = fixed_bytes(specs, false, h->num_sms, mf);
     if (fixed >= budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
     tvs_batch* b = new tvs_batch();
     b->h = h;
     rc = plan_batch(specs, budget - fixed, h->num_sms, h->tuning, &b->plan);
     if (rc) { delete b; return rc; }
-    b->L = make_layout(b->plan, false);
+    b->L = make_layout(b->plan, false, mf);
     cudaError_t e = cudaMalloc(&b->ws, b->L.total);
     if (e != cudaSuccess) {
         cudaGetLastError();

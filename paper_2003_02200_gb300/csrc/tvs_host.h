@@ -149,12 +149,15 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
 // block, uploaded with one copy.
 struct Layout {
     size_t hdr, dirs, jobs, cj, istart, hdr_bytes;
-    size_t io_dem, io_out, counter, acc, part, rowlo, rowhi, cvf, cvb, total;
+    size_t io_dem, io_out, counter, flags, flag_cap, acc, part, rowlo, rowhi, cvf, cvb, total;
 };
 
-Layout make_layout(const BatchPlan& plan, bool host_io);
+// max_flags bounds the flagged-walk buffer's entries (see flag_entries).
+Layout make_layout(const BatchPlan& plan, bool host_io, size_t max_flags = FLAG_BUF_ENTRIES);
 // Bytes a batch needs besides its chunks' slabs.
-size_t fixed_bytes(const std::vector<JobSpec>& jobs, bool host_io, int num_sms);
+size_t fixed_bytes(const std::vector<JobSpec>& jobs, bool host_io, int num_sms, size_t max_flags);
+// The flagged-walk buffer entries a scratch budget allows: a sixteenth of it.
+size_t budget_flags(size_t budget);
 // Host image of the header for the scratch at `base`.
 void build_header(const BatchPlan& plan, const Layout& L, char* base, bool host_io, std::vector<char>* img);
 

@@ -127,11 +127,17 @@ cudaError_t launch_colmap(const DirDev* d_dir, int* dest, unsigned* frac, cudaSt
 // direction (items 2p and 2p + 1 of a direction are row p forward and
 // backward), its row gathered from the job's DEM; `prune` turns exact horizon
 // pruning on, `cert` certified (exact) visibility decisions instead of FP32
-// ones.
+// ones.  With cert and a flag buffer (flag_cap entries, flag_count two
+// counters) the walks the sweep cannot certify are walked exactly by a second
+// kernel on the same stream; without one (or once it is full) the sweep's
+// warps walk them themselves.
 cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* d_item_start, int ndir,
                          int total_items, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd, int wmax,
-                         int dmax, int prune, int cert, unsigned* counter, int num_sms, int smem_optin,
-                         int max_warps, cudaStream_t stream);
+                         int dmax, int prune, int cert, unsigned* counter, int4* flag_buf, unsigned* flag_count,
+                         int flag_cap, int num_sms, int smem_optin, int max_warps, cudaStream_t stream);
+// Entries of a launch's flagged-walk buffer (16 bytes each), at most.
+constexpr int FLAG_BUF_ENTRIES = 1 << 24;
+constexpr int FLAG_ENTRY_BYTES = 16;
 // Unskew of a chunk: `total_tiles` flattened cell tiles over the chunk's jobs
 // (ncj entries of d_cj, sorted by tile_beg), `max_split` the largest nsplit.
 cudaError_t launch_unskew(const int* cv_fwd, const int* cv_bwd, const JobDev* d_jobs, const DirDev* d_dirs,

@@ -18,8 +18,6 @@ namespace tvs {
 
 namespace {
 
-__device__ __forceinline__ float neg_inf() { return __int_as_float(0xff800000); }
-
 __device__ __forceinline__ int dest_of(unsigned long long t_fx, int j)
 {
     return (int)(((unsigned long long)j * t_fx) >> 32);

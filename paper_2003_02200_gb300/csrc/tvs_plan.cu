@@ -474,7 +474,26 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
     return TVS_OK;
 }
 
-Layout make_layout(const BatchPlan& plan, bool host_io)
+// Entries of the flagged-walk buffer for these jobs: 1 in 64 of their walks
+// (flags run between 1 in 700 and 1 in 250 on fractal terrain; walks beyond
+// the buffer are walked in the sweep itself, at a cost), at least 4096, at
+// most `cap` and FLAG_BUF_ENTRIES.
+size_t flag_entries(const std::vector<JobSpec>& jobs, size_t cap)
+{
+    double walks = 0.0;
+    for (const JobSpec& J : jobs) {
+        const int nd = J.k1 > J.k0 ? J.k1 - J.k0 : J.n;   // the job's directions in this call
+        walks += 2.0 * (double)J.rows * (double)J.cols * (double)nd;
+    }
+    return (size_t)std::min<double>((double)std::min<size_t>(cap, FLAG_BUF_ENTRIES), std::max(4096.0, walks / 64.0));
+}
+
+size_t budget_flags(size_t budget)
+{
+    return std::min<size_t>((size_t)FLAG_BUF_ENTRIES, budget / 16 / FLAG_ENTRY_BYTES);
+}
+
+Layout make_layout(const BatchPlan& plan, bool host_io, size_t max_flags)
 {
     Layout L{};
     size_t o = 0;
@@ -487,7 +506,9 @@ Layout make_layout(const BatchPlan& plan, bool host_io)
     const size_t cells = host_io ? (size_t)plan.jobs[0].rows * plan.jobs[0].cols : 0;
     L.io_dem = o;  o += align256(cells * 4);
     L.io_out = o;  o += align256(cells * 4);
-    L.counter = o; o += 256;
+    L.counter = o; o += 256;   // work counter at 0, flag-buffer counters at 64
+    L.flag_cap = flag_entries(plan.jobs, max_flags);
+    L.flags = o;   o += align256(L.flag_cap * FLAG_ENTRY_BYTES);
     L.acc = o;     o += align256((size_t)plan.acc_elems * 16);
     L.part = o;    o += align256((size_t)plan.max_part * 16);
     L.rowlo = o;   o += align256((size_t)plan.max_rows * 4);
@@ -500,13 +521,14 @@ Layout make_layout(const BatchPlan& plan, bool host_io)
 
 // Header, host copies of a single job, exact totals of every job, partials
 // bound, counter.
-size_t fixed_bytes(const std::vector<JobSpec>& jobs, bool host_io, int num_sms)
+size_t fixed_bytes(const std::vector<JobSpec>& jobs, bool host_io, int num_sms, size_t max_flags)
 {
     size_t ninst = 0, cells = 0;
     for (const JobSpec& J : jobs) { ninst += J.n; cells += (size_t)J.rows * J.cols; }
     size_t b = align256(ninst * sizeof(DirDev)) + align256(jobs.size() * sizeof(JobDev)) +
                align256((jobs.size() + ninst) * sizeof(ChunkJob)) + align256((2 * ninst + 1) * 4) + 4096;
     if (host_io) b += 2 * align256((size_t)jobs[0].rows * jobs[0].cols * 4);
+    b += align256(flag_entries(jobs, max_flags) * FLAG_ENTRY_BYTES);
     return b + align256(cells * 16) + part_bound(num_sms);
 }
 
@@ -540,6 +562,8 @@ int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* bas
     const ChunkJob* d_cj = reinterpret_cast<const ChunkJob*>(base + L.cj);
     const int* d_istart = reinterpret_cast<const int*>(base + L.istart);
     unsigned* d_counter = reinterpret_cast<unsigned*>(base + L.counter);
+    unsigned* d_fcount = reinterpret_cast<unsigned*>(base + L.counter + 64);
+    int4* d_flags = reinterpret_cast<int4*>(base + L.flags);
     __int128* d_part = reinterpret_cast<__int128*>(base + L.part);
     int* d_rowlo = reinterpret_cast<int*>(base + L.rowlo);
     int* d_rowhi = reinterpret_cast<int*>(base + L.rowhi);
@@ -557,8 +581,8 @@ int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* bas
         {
             Timer t(h, K_SWEEP, s, c.evals);
             TVS_CUDA(launch_sweep(cd, d_jobs, d_istart + c.istart_at, nd, c.items, d_rowlo, d_rowhi, d_cvf, d_cvb,
-                                  c.wmax, c.dmax, tn.prune, !tn.fp32_decisions, d_counter, num_sms, smem_optin,
-                                  tn.sweep_max_warps, s),
+                                  c.wmax, c.dmax, tn.prune, !tn.fp32_decisions, d_counter, d_flags, d_fcount,
+                                  (int)L.flag_cap, num_sms, smem_optin, tn.sweep_max_warps, s),
                      "sweep launch");
         }
         if (before_unskew) {
@@ -605,12 +629,13 @@ int upload_header(tvs_ctx* h, const std::vector<char>& img, void* dst, cudaStrea
 int run_batch(tvs_ctx* h, const std::vector<JobSpec>& jobs, cudaStream_t s, bool host_io, const float* host_dem,
               float* host_out)
 {
-    const size_t fixed = fixed_bytes(jobs, host_io, h->num_sms);
+    const size_t mf = budget_flags(h->budget);
+    const size_t fixed = fixed_bytes(jobs, host_io, h->num_sms, mf);
     if (fixed >= h->budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
     BatchPlan plan;
     int rc = plan_batch(jobs, h->budget - fixed, h->num_sms, h->tuning, &plan);
     if (rc) return rc;
-    const Layout L = make_layout(plan, host_io);
+    const Layout L = make_layout(plan, host_io, mf);
     rc = ensure_scratch(h, L.total);
     if (rc) return rc;
     char* base = h->ws;

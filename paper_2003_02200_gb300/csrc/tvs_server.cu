@@ -268,12 +268,21 @@ std::vector<Slice> pick_slices(tvs_server* S, size_t slot_avail)
     return out;
 }
 
-// Bytes of a lane's scratch that the header, counter and partials may take.
-size_t lane_fixed_bytes(int num_sms)
+// Entries of a lane's flagged-walk buffer: an eighth of the lane, at most
+// FLAG_BUF_ENTRIES.
+size_t lane_flags(size_t lane_bytes)
+{
+    return std::min<size_t>((size_t)FLAG_BUF_ENTRIES, lane_bytes / 8 / FLAG_ENTRY_BYTES);
+}
+
+// Bytes of a lane's scratch that the header, counters, flagged-walk buffer
+// and partials may take.
+size_t lane_fixed_bytes(int num_sms, size_t lane_bytes)
 {
     return align256((size_t)kMaxChunkDirs * sizeof(DirDev)) + align256((size_t)kMaxStepJobs * sizeof(JobDev)) +
            align256((size_t)(kMaxStepJobs + kMaxChunkDirs) * sizeof(ChunkJob)) +
-           align256((size_t)(2 * kMaxChunkDirs + 2) * 4) + 256 + part_bound(num_sms) + 4096;
+           align256((size_t)(2 * kMaxChunkDirs + 2) * 4) + 256 + align256(lane_flags(lane_bytes) * FLAG_ENTRY_BYTES) +
+           part_bound(num_sms) + 4096;
 }
 
 // Plan and enqueue one step on a free lane.  Called with the lock held.
@@ -290,10 +299,10 @@ int enqueue_step(tvs_server* S, Lane& lane, const std::vector<Slice>& slices)
         jobs.push_back(J);
     }
     BatchPlan plan;
-    const size_t fixed = lane_fixed_bytes(S->num_sms);
+    const size_t fixed = lane_fixed_bytes(S->num_sms, lane.bytes);
     int rc = plan_batch(jobs, lane.bytes - fixed, S->num_sms, S->tuning, &plan);
     if (rc) return rc;
-    const Layout L = make_layout(plan, false);
+    const Layout L = make_layout(plan, false, lane_flags(lane.bytes));
     if (L.total > lane.bytes) return fail(TVS_ERR_OOM, "step does not fit its lane");
     std::vector<char> img;
     build_header(plan, L, lane.scratch, false, &img);
@@ -367,7 +376,8 @@ void scheduler_loop(tvs_server* S)
                     break;
                 }
         if (work && free_lane) {
-            const std::vector<Slice> slices = pick_slices(S, free_lane->bytes - lane_fixed_bytes(S->num_sms));
+            const std::vector<Slice> slices =
+                pick_slices(S, free_lane->bytes - lane_fixed_bytes(S->num_sms, free_lane->bytes));
             const int rc = enqueue_step(S, *free_lane, slices);
             if (rc) break_server(S, "step enqueue failed: " + g_err);
             continue;
@@ -517,7 +527,7 @@ int tvs_server_create(int device, const tvs_server_config* cfg_in, tvs_server_ha
     if (cfg.rate_hint == 0) cfg.rate_hint = 5e12;
     if (cfg.max_active == 0) cfg.max_active = 256;
     const int num_sms = prop.multiProcessorCount;
-    if (cfg.step_slot_bytes < lane_fixed_bytes(num_sms) + ((size_t)1 << 20))
+    if (cfg.step_slot_bytes < lane_fixed_bytes(num_sms, cfg.step_slot_bytes) + ((size_t)1 << 20))
         return fail(TVS_ERR_ARG, "step_slot_bytes is too small for a step");
     const size_t lanes_bytes = cfg.step_slot_bytes * (size_t)cfg.lanes;
     if (cfg.hbm_budget_bytes <= lanes_bytes + ((size_t)1 << 20))
@@ -599,7 +609,7 @@ int tvs_server_submit(tvs_server_handle S, const float* dem, int rows, int cols,
                                                r->cum_rows[k + 1] - r->cum_rows[g0], k + 1 - g0));
         }
     }
-    if (worst_group + lane_fixed_bytes(S->num_sms) > S->cfg.step_slot_bytes)
+    if (worst_group + lane_fixed_bytes(S->num_sms, S->cfg.step_slot_bytes) > S->cfg.step_slot_bytes)
         return fail(TVS_ERR_OOM, "8 directions of this DEM do not fit a step slot (raise step_slot_bytes)");
     {
         DeviceGuard g(S->device);

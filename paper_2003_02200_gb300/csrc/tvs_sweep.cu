@@ -70,12 +70,16 @@ struct SweepParams {
     int* cv_fwd;       // forward measure of every sample (slab layout)
     int* cv_bwd;       // backward measure of every sample (slab layout)
     unsigned* counter;
+    int4* flag_buf;    // certified: flagged walks for the exact pass (NULL: walked in the sweep)
+    unsigned* flag_count;
+    int flag_cap;
     int ndir;
     int total_items;
     int inv_len;       // entries of the per-distance table (float4 each)
     int tab_slots;     // float4 slots the table takes (the certified kernels skew it)
     int istart_len;    // ints of the item-start table (multiple of 4)
     int half;          // floats of one staged row array (multiple of 4)
+    int per_pair;      // floats of a warp pair's shared area (certified)
     int zs_len;        // floats of the row's suffix maxima (0 without pruning)
     int wm_len;        // floats of the row's window maxima (certified only)
     int fl_cap;        // entries of the flagged-POV list (certified only)
@@ -138,14 +142,18 @@ __device__ __forceinline__ bool decode_item(const SweepParams& sp, const int* is
     return it->L > 0;
 }
 
-// Stages the item's row (reversed for backward items) from the DEM: FP32
-// heights into Fh, or with CERT hi parts into Fh and lo parts into Fl.  The
-// last sample and ROW_PADR samples after it hold -inf (lo 0): the last target
-// of a walk never adds area, so it may be a sentinel that is never visible.
-// Returns (CERT) the row's largest |elevation| read, for the blend's error
-// bound.
+// Stages the item's row from the DEM: FP32 heights into Fh, or with CERT hi
+// parts into Fh and lo parts into Fl, reversed for backward items unless
+// rev_ok is false (rows that both walk directions share stay in row order).  The last sample and ROW_PADR samples after
+// it hold -inf (lo 0): the last target of a walk never adds area, so it may be
+// a sentinel that is never visible.  With CERT the first sample and the
+// ROW_PADL samples before it are sentinels too (the last target of a backward
+// walk), and the real hi and lo parts of the two end samples, which are POVs,
+// go to ends[0..3] (first hi, first lo, last hi, last lo).  Returns (CERT) the
+// row's largest |elevation| read, for the blend's error bound.
 template <bool CERT>
-__device__ __forceinline__ float stage_row(const SweepParams& sp, const ItemRow& it, float* Fh, float* Fl, int lane)
+__device__ __forceinline__ float stage_row(const SweepParams& sp, const ItemRow& it, float* Fh, float* Fl,
+                                           float* ends, int lane, int part = 0, int parts = 1, bool rev_ok = true)
 {
     const DirDev& d = sp.dirs[it.dir];
     const float* __restrict__ dem = sp.jobs[d.job].dem;
@@ -153,10 +161,11 @@ __device__ __forceinline__ float stage_row(const SweepParams& sp, const ItemRow&
     const long long cells = (long long)sp.jobs[d.job].rows * cols;
     const int b = it.p - d.D;
     const unsigned long long t_fx = d.t_fx;
+    const bool rev = rev_ok && it.rev;
     const float NEG = neg_inf();
     float zmax = 0.f;
     constexpr int B = 4;
-    for (int x0 = lane; x0 < it.L; x0 += 32 * B) {
+    for (int x0 = lane + 32 * B * part; x0 < it.L; x0 += 32 * B * parts) {
         float va[B], vb[B];
         unsigned fr[B];
 #pragma unroll
@@ -164,7 +173,7 @@ __device__ __forceinline__ float stage_row(const SweepParams& sp, const ItemRow&
             const int x = x0 + 32 * k;
             va[k] = 0.f; vb[k] = 0.f; fr[k] = 0u;
             if (x < it.L) {
-                const int j = it.jlo + (it.rev ? it.L - 1 - x : x);
+                const int j = it.jlo + (rev ? it.L - 1 - x : x);
                 const unsigned long long y = (unsigned long long)j * t_fx;
                 const int a = b + (int)(y >> 32);
                 fr[k] = (unsigned)y;
@@ -181,20 +190,24 @@ __device__ __forceinline__ float stage_row(const SweepParams& sp, const ItemRow&
             if (CERT) {
                 float zh, zl;
                 df::df_blend(va[k], vb[k], fr[k], zh, zl);
-                Fh[ROW_PADL + x] = x == it.L - 1 ? NEG : zh;
-                Fl[ROW_PADL + x] = x == it.L - 1 ? 0.f : zl;
+                const bool end = x == 0 || x == it.L - 1;
+                if (x == 0) { ends[0] = zh; ends[1] = zl; }
+                if (x == it.L - 1) { ends[2] = zh; ends[3] = zl; }
+                Fh[ROW_PADL + x] = end ? NEG : zh;
+                Fl[ROW_PADL + x] = end ? 0.f : zl;
                 zmax = fmaxf(zmax, fmaxf(fabsf(va[k]), fabsf(vb[k])));
             } else {
                 Fh[ROW_PADL + x] = x == it.L - 1 ? NEG : blend32(va[k], vb[k], fr[k]);
             }
         }
     }
-    for (int m = lane; m < ROW_PADR; m += 32) {
+    for (int m = lane; part == 0 && m < ROW_PADR; m += 32) {
         if (!in_range(ROW_PADL + it.L + m, sp.half, 4)) continue;
         Fh[ROW_PADL + it.L + m] = NEG;
         if (CERT) Fl[ROW_PADL + it.L + m] = 0.f;
     }
     if (CERT) {
+        if (part == 0 && lane < ROW_PADL) { Fh[lane] = NEG; Fl[lane] = 0.f; }
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) zmax = fmaxf(zmax, __shfl_xor_sync(0xffffffffu, zmax, o));
     }
@@ -418,6 +431,33 @@ __device__ __forceinline__ void suffix_max(const float* __restrict__ F, float* _
     }
 }
 
+// Prefix maxima of the staged row F (row order, certified backward walks) at
+// every ZS_STRIDE-th sample: ZP[j] = max F[x] over x <= ZS_STRIDE * j +
+// ZS_STRIDE - 1, for j <= (L - 1) / ZS_STRIDE.  Lane l scans its own segment,
+// a warp scan joins the segments.
+__device__ __forceinline__ void prefix_max(const float* __restrict__ F, float* __restrict__ ZP, int L, int lane)
+{
+    const float NEG = neg_inf();
+    const int seglen = ((L + 31) / 32 + ZS_STRIDE - 1) / ZS_STRIDE * ZS_STRIDE;
+    const int a = lane * seglen, b = min(a + seglen, L);
+    float m = NEG;
+    for (int x = a; x < b; ++x) m = fmaxf(m, F[ROW_PADL + x]);
+    // inclusive prefix scan of the segment maxima over the lanes
+    float s = m;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const float t = __shfl_up_sync(0xffffffffu, s, o);
+        if (lane >= o) s = fmaxf(s, t);
+    }
+    float before = __shfl_up_sync(0xffffffffu, s, 1);   // maximum of the earlier segments
+    if (lane == 0) before = NEG;
+    float run = before;
+    for (int x = a; x < b; ++x) {
+        run = fmaxf(run, F[ROW_PADL + x]);
+        if (x % ZS_STRIDE == ZS_STRIDE - 1 || x == L - 1) ZP[x / ZS_STRIDE] = run;
+    }
+}
+
 // ------------------------------------------------ certified decisions --
 //
 // The fast path of a group of P POVs x0 .. x0 + P - 1 works on differences
@@ -498,17 +538,21 @@ __device__ __forceinline__ float sat_pos(float s)
     return v;
 }
 
-__device__ __forceinline__ void window_max(const float* __restrict__ H, float* __restrict__ WM, int L, int half,
-                                           int wm_len, int lane)
+// Window maxima of the padded staged row (certified walks): WM[k] = max
+// Fh[4k .. 4k + WM_SPAN) in padded coordinates (sample x at ROW_PADL + x),
+// for k < (ROW_PADL + L + 3) / 4; a block's window of either walk direction
+// starts at a multiple of 4 and spans at most WM_SPAN samples.
+__device__ __forceinline__ void window_max(const float* __restrict__ Fh, float* __restrict__ WM, int L, int half,
+                                           int wm_len, int lane, int part = 0, int parts = 1)
 {
     const float NEG = neg_inf();
-    const int nk = (L + 3) / 4;
-    for (int k = lane; k < nk; k += 32) {
+    const int nk = (ROW_PADL + L + 3) / 4;
+    for (int k = lane + 32 * part; k < nk; k += 32 * parts) {
         float m = NEG;
 #pragma unroll
         for (int i = 0; i < WM_SPAN; i += 4) {
-            if (!in_range(ROW_PADL + 4 * k + i + 3, half, 5)) continue;
-            const float4 v = *reinterpret_cast<const float4*>(H + 4 * k + i);
+            if (!in_range(4 * k + i + 3, half, 5)) continue;
+            const float4 v = *reinterpret_cast<const float4*>(Fh + 4 * k + i);
             m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
         }
         if (in_range(k, wm_len, 6)) WM[k] = m;
@@ -523,7 +567,11 @@ struct ExactCtx {
     float h0h, h0l;      // h0 = h0h + h0l (to 2^-48)
     float eta;           // bound of the staged heights' error, plus h0's split
     int* cvrow;
-    bool rev;
+    bool bwd;            // walks go toward lower sample indices
+    bool from_dem;       // samples blended from the DEM as needed (no staged row)
+    bool rev_staged;     // the staged row is reversed: staged x is row sample L - 1 - x
+    float eh0, el0;      // hi and lo parts of the first sample (a sentinel in H, Lo)
+    float ehL, elL;      // and of the last one
     const DirDev* dir;
     const JobDev* job;
     int p, jlo;
@@ -540,12 +588,39 @@ __device__ __forceinline__ float inv_d(const ExactCtx& c, int d)
     return m < c.tabn ? c.tab[m + m / TAB_SKEW].x : __frcp_rn((float)d);
 }
 
-// FP64 height of staged sample xs exactly as the FP64 definition forms it:
-// (1 - r) * a + r * b with r = fr / 2^32, every operation rounded.
+// Hi and lo parts of sample xs (row order) blended from the DEM, as the
+// staging forms them.
+__device__ __forceinline__ void dem_hl(const ExactCtx& c, int xs, float& hi, float& lo)
+{
+    const DirDev& d = *c.dir;
+    const int j = c.jlo + (c.rev_staged ? c.L - 1 - xs : xs);
+    const unsigned long long y = (unsigned long long)j * d.t_fx;
+    const int a = c.p - d.D + (int)(y >> 32);
+    const unsigned fr = (unsigned)y;
+    int st;
+    const long long idx = view_index(d, c.job->cols, a, j, &st);
+    const long long cells = (long long)c.job->rows * c.job->cols;
+    const float va = in_range(idx, cells, 16) ? c.job->dem[idx] : 0.f;
+    const float vb = fr != 0u ? (in_range(idx + st, cells, 17) ? c.job->dem[idx + st] : 0.f) : va;
+    df::df_blend(va, vb, fr, hi, lo);
+}
+
+// Hi and lo parts of POV x's ground height (the end samples are sentinels in
+// the staged arrays; their real parts are kept aside).
+__device__ __forceinline__ void pov_hl(const ExactCtx& c, int x, float& hi, float& lo)
+{
+    if (c.from_dem) dem_hl(c, x, hi, lo);
+    else if (x == 0) { hi = c.eh0; lo = c.el0; }
+    else if (x == c.L - 1) { hi = c.ehL; lo = c.elL; }
+    else { hi = c.H[x]; lo = c.Lo[x]; }
+}
+
+// FP64 height of staged sample xs (row order) exactly as the FP64 definition
+// forms it: (1 - r) * a + r * b with r = fr / 2^32, every operation rounded.
 __device__ __forceinline__ double z64_at(const ExactCtx& c, int xs)
 {
     const DirDev& d = *c.dir;
-    const int j = c.jlo + (c.rev ? c.L - 1 - xs : xs);
+    const int j = c.jlo + (c.rev_staged ? c.L - 1 - xs : xs);
     const unsigned long long y = (unsigned long long)j * d.t_fx;
     const int a = c.p - d.D + (int)(y >> 32);
     const unsigned fr = (unsigned)y;
@@ -575,6 +650,7 @@ __device__ __forceinline__ int warp_sum(int v)
 __device__ __noinline__ int fp64_walk(const ExactCtx& c, int x, int last, int lane)
 {
     const double h = __dadd_rn(z64_at(c, x), c.job->h0);
+    const int dir = c.bwd ? -1 : 1;
     double run = -__longlong_as_double(0x7ff0000000000000LL);
     int acc = 0;
     for (int base = 1; base <= last; base += 32 * XW_KPL) {
@@ -584,7 +660,7 @@ __device__ __noinline__ int fp64_walk(const ExactCtx& c, int x, int last, int la
 #pragma unroll
         for (int k = 0; k < XW_KPL; ++k) {
             const int d = d0 + k;
-            th[k] = d <= last ? __ddiv_rn(__dsub_rn(z64_at(c, x + d), h), (double)d) : run;
+            th[k] = d <= last ? __ddiv_rn(__dsub_rn(z64_at(c, x + dir * d), h), (double)d) : run;
             m = fmax(m, th[k]);
         }
         double incl = m;
@@ -613,11 +689,14 @@ __device__ __noinline__ int fp64_walk(const ExactCtx& c, int x, int last, int la
 __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane, bool* esc_out)
 {
     const float NEG = neg_inf();
+    const int dir = c.bwd ? -1 : 1;
     float hh, hl;
     {
+        float zh, zl;
+        pov_hl(c, x, zh, zl);
         float s, e;
-        df::two_sum(c.H[x], c.h0h, s, e);
-        e = __fadd_rn(e, __fadd_rn(c.Lo[x], c.h0l));
+        df::two_sum(zh, c.h0h, s, e);
+        e = __fadd_rn(e, __fadd_rn(zl, c.h0l));
         df::two_sum(s, e, hh, hl);
     }
     float rh = NEG, rl = 0.f;
@@ -633,9 +712,12 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
         for (int k = 0; k < XW_KPL; ++k) {
             const int d = d0 + k;
             th[k] = NEG; tl[k] = 0.f; iv[k] = 1.f;
-            if (d <= last && in_range(ROW_PADL + x + d, c.half, 15)) {
+            if (d <= last && (c.from_dem || in_range(ROW_PADL + x + dir * d, c.half, 15))) {
                 iv[k] = inv_d(c, d);
-                df::df_slope_iv(c.H[x + d], c.Lo[x + d], hh, hl, d, iv[k], th[k], tl[k]);
+                float zh, zl;
+                if (c.from_dem) dem_hl(c, x + dir * d, zh, zl);
+                else { zh = c.H[x + dir * d]; zl = c.Lo[x + dir * d]; }
+                df::df_slope_iv(zh, zl, hh, hl, d, iv[k], th[k], tl[k]);
                 if (df::df_gt(th[k], tl[k], mh, ml)) { mh = th[k]; ml = tl[k]; md = d; }
             }
         }
@@ -683,7 +765,7 @@ __device__ __noinline__ int df_walk(const ExactCtx& c, int x, int last, int lane
 // Exact measure of POV x of the staged row, written by lane 0.
 __device__ __noinline__ void exact_walk(const ExactCtx& c, int x, int lane)
 {
-    const int n = min(c.L - 1 - x, c.K);
+    const int n = min(c.bwd ? x : c.L - 1 - x, c.K);
     int cv;
     if (n < 2) {
         cv = n < 1 ? 0 : 1;
@@ -696,13 +778,18 @@ __device__ __noinline__ void exact_walk(const ExactCtx& c, int x, int lane)
             if (esc) atomicAdd(&g_sweep_stats[1], 1ull);
         }
     }
-    if (lane == 0 && in_range(x, c.L, 14)) c.cvrow[c.rev ? c.L - 1 - x : x] = cv;
+    if (lane == 0 && in_range(x, c.L, 14)) c.cvrow[c.rev_staged ? c.L - 1 - x : x] = cv;
 }
 
 // The warp's list of flagged POVs (positions in the staged row).
 struct FlagList {
     int* list;
     int count;
+    int4* gbuf;          // the launch's flagged-walk buffer (NULL: walk every flag here)
+    unsigned* gcount;    // its fill counter
+    int gcap;            // its capacity
+    int item;            // the current row's work item
+    float zmax;          // and its largest |elevation| (for the staged heights' error bound)
 };
 
 __device__ __noinline__ void drain_flags(FlagList& fl, const ExactCtx& c, int lane)
@@ -727,6 +814,28 @@ __device__ __forceinline__ void flag_push(FlagList& fl, const ExactCtx& c, unsig
         if (lane >= o) incl += t;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (fl.gbuf) {
+        // hand the walks to the exact pass after the sweep: (item, sample)
+        // entries; when the buffer is full they are walked here instead
+        unsigned at = 0u;
+        if (lane == 0) at = atomicAdd(fl.gcount, (unsigned)total);
+        at = __shfl_sync(0xffffffffu, at, 0);
+        if ((unsigned long long)at + (unsigned long long)total <= (unsigned long long)fl.gcap) {
+            unsigned pos = at + (unsigned)(incl - cnt);
+            for (unsigned m = fm; m; m &= m - 1, ++pos)
+                if (in_range(pos, fl.gcap, 20)) {
+                    const int xs = x0 + __ffs(m) - 1;   // staged sample; the entry holds the row's
+                    fl.gbuf[pos] = make_int4(fl.item, c.rev_staged ? c.L - 1 - xs : xs, __float_as_int(fl.zmax), 0);
+                }
+            __syncwarp();
+            return;
+        }
+        // full: the slots reserved below the capacity are marked empty
+        for (unsigned long long pos = (unsigned long long)at + lane;
+             pos < (unsigned long long)at + (unsigned long long)total && pos < (unsigned long long)fl.gcap; pos += 32)
+            fl.gbuf[pos] = make_int4(-1, -1, 0, 0);
+        __syncwarp();
+    }
     if (fl.count + total > FLAG_CAP) drain_flags(fl, c, lane);
     int pos = fl.count + incl - cnt;
     for (unsigned m = fm; m; m &= m - 1, ++pos)
@@ -806,9 +915,18 @@ __device__ __forceinline__ float bound_slope(float z, float Rh, float gmin, floa
 // Certified sweep of one staged row (the lane queue of sweep_row).  eg0 =
 // 2.01u |h0| + |h0 - float(h0)| + 4 eta (the parts of Eg that do not depend
 // on the group).  With PRUNE a group stops once, for every POV q, the
-// remaining targets' largest possible exact slope (from the suffix maxima)
-// is at most M_q - 2 delta_q: they are then not above theta_a exactly.
-template <int P, int U, bool LONG, bool PRUNE>
+// remaining targets' largest possible exact slope (from the suffix maxima,
+// or the prefix maxima of a backward walk) is at most M_q - 2 delta_q: they
+// are then not above theta_a exactly.
+//
+// The row is staged in row order for both walk directions.  A group covers
+// the samples x0 .. x0 + P - 1 (x0 a multiple of 4, so that every window is
+// 16-byte aligned); its POV q is sample x0 + q walking forward, or sample
+// x0 + P - 1 - q walking backward, so that in either direction POV q's step
+// w meets the window's element q + w + 1: a backward block's window is
+// loaded from x0 - e - U and stored reversed.  Backward groups are taken
+// from the row's end (the longest walks first).
+template <int P, int U, bool LONG, bool PRUNE, bool BWD>
 __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* __restrict__ ZS,
                                                const float* __restrict__ WM, const float4* __restrict__ tab,
                                                int tabn, int* __restrict__ spill, float eg0, FlagList& fl, int lane)
@@ -831,10 +949,15 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
     int gi = lane, next = 32;
     int x0 = 0, e = 0, dlim = -1, seg = FLUSH_STEPS;
     bool klimited = false;
+    // sample of POV q of the current group, and its walk's target count
+    auto pov_x = [&](int q) { return BWD ? x0 + P - 1 - q : x0 + q; };
+    auto walk_n = [&](int x) { return min(BWD ? x : L - 1 - x, K); };
 
     auto start = [&]() {
-        x0 = gi * P;
-        const int rowlim = L - 2 - x0;
+        x0 = (BWD ? G - 1 - gi : gi) * P;
+        // the group's longest walk: its first existing POV in walk order
+        const int xl = BWD ? min(x0 + P - 1, L - 1) : x0;
+        const int rowlim = BWD ? xl - 1 : L - 2 - xl;
         dlim = min(klim, rowlim);
         klimited = klim < rowlim;
         e = 0;
@@ -846,27 +969,35 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
 #pragma unroll
             for (int q = 0; q < P; ++q) spill[32 * q] = 0;
         }
-        if (dlim < 1) return;                 // no block runs (x0 <= L - 3 below)
+        if (dlim < 1) return;                 // no block runs
         // every index the group's blocks use, checked once: the last block
-        // starts below dlim
+        // starts at elast < dlim
         const int elast = (dlim - 1) / U * U;
-        if (!in_range(ROW_PADL + x0 + elast + P + U - 1, xc.half, 19) ||
-            !in_range((x0 + elast) >> 2, xc.wm_len, 8) ||
-            (PRUNE && !in_range((x0 + elast + 1) / ZS_STRIDE, xc.zs_len, 9)) ||
+        const int wlo = BWD ? x0 - elast - U : x0;           // lowest window start
+        const int whi = BWD ? x0 - U : x0 + elast;           // highest window start
+        const int zsi = BWD ? (x0 + P - 2) / ZS_STRIDE : (x0 + elast + 1) / ZS_STRIDE;
+        if (!in_range(ROW_PADL + wlo, xc.half, 19) || !in_range(ROW_PADL + whi + P + U - 1, xc.half, 19) ||
+            !in_range((ROW_PADL + wlo) >> 2, xc.wm_len, 8) || !in_range((ROW_PADL + whi) >> 2, xc.wm_len, 8) ||
+            (PRUNE && !in_range(zsi, xc.zs_len, 9)) ||
             (!(LONG && elast + U > tabn) && !in_range(elast + U - 1, tabn, 11))) {
             dlim = 0;
-            mask = L - x0 >= P ? (1u << P) - 1u : (1u << (L - x0)) - 1u;   // walked exactly instead
+            const unsigned all = L - x0 >= P ? (1u << P) - 1u : (1u << (L - x0)) - 1u;   // bits by sample
+            mask = BWD ? __brev(all) >> (32 - P) : all;                                   // bits by POV q
             return;
         }
-        Rh = H[x0];
+        float Rl;
+        pov_hl(xc, x0, Rh, Rl);
+        (void)Rl;
         float gmax = 0.f;
         gmin = pos_inf();
 #pragma unroll
         for (int q = 0; q < P; ++q) {
-            const int x = x0 + q;
+            const int x = pov_x(q);
             float gq = 0.f;
-            if (x <= L - 2) {
-                gq = __fadd_rn(__fadd_rn(__fsub_rn(H[x], Rh), Lo[x]), xc.h0h);
+            if (BWD ? (x >= 1 && x <= L - 1) : x <= L - 2) {   // POVs with a target
+                float zh, zl;
+                pov_hl(xc, x, zh, zl);
+                gq = __fadd_rn(__fadd_rn(__fsub_rn(zh, Rh), zl), xc.h0h);
                 gmin = fminf(gmin, gq);
             }
             g[q] = gq;
@@ -878,14 +1009,16 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             // target 1 (a sentinel, -inf, when the POV has no target adding
             // area): M starts just below its slope, so that target is visible
             // and outside its margin, and the maximum then is its slope exactly
-            const int x = x0 + q;
-            const float y1 = __fadd_rn(__fsub_rn(H[x + 1], Rh), Lo[x + 1]);
+            const int x = pov_x(q);
+            const int t = BWD ? x - 1 : x + 1;
+            const float y1 = __fadd_rn(__fsub_rn(H[t], Rh), Lo[t]);
             const float x1 = __fsub_rn(y1, g[q]);
             const float C = __fmaf_rn(0x1p-6f, fabsf(x1), __fmaf_rn(4.f, c2e, 0x1p-16f));
-            // a POV with no target that adds area (x >= L - 2) starts at +inf:
-            // nothing is visible to it, no step is inside its margin, and it
-            // never holds back pruning
-            CERT_M(q) = x <= L - 3 ? __fsub_rn(x1, C) : pos_inf();
+            // a POV with no target that adds area starts at +inf: nothing is
+            // visible to it, no step is inside its margin, and it never holds
+            // back pruning
+            const bool area = BWD ? (x >= 2 && x <= L - 1) : x <= L - 3;
+            CERT_M(q) = area ? __fsub_rn(x1, C) : pos_inf();
             ia[q] = 1.f;
         }
     };
@@ -897,15 +1030,16 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             if (fin) {
 #pragma unroll
                 for (int q = 0; q < P; ++q) {
-                    const int x = x0 + q;
+                    const int x = pov_x(q);
                     if (x < L && !((mask >> q) & 1u)) {
-                        const int n = min(L - 1 - x, K);
+                        const int n = walk_n(x);
                         const float s = q % 2 ? acc2[q / 2].y : acc2[q / 2].x;
-                        xc.cvrow[xc.rev ? L - 1 - x : x] = n >= 1 ? 1 + (int)s + (LONG ? spill[32 * q] : 0) : 0;
+                        xc.cvrow[xc.rev_staged ? L - 1 - x : x] = n >= 1 ? 1 + (int)s + (LONG ? spill[32 * q] : 0) : 0;
                     }
                 }
             }
-            const unsigned fm = fin ? mask : 0u;
+            // flagged POVs as bits by sample (x0 + bit)
+            const unsigned fm = fin ? (BWD ? __brev(mask) >> (32 - P) : mask) : 0u;
             if (__any_sync(FULL, fm != 0u)) flag_push(fl, xc, fm, x0, lane);
             if (fin) {
                 gi = next + __popc(need & below);
@@ -927,10 +1061,11 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             }
             // margins of this block.  The bounds are formed branch-free: a
             // window or suffix of sentinels only (-inf) gives 0.
+            const int ws = BWD ? x0 - e - U : x0 + e;       // the window's first sample
             const bool far = LONG && e + U > tabn;
             const float4* __restrict__ tb = tab + e + e / TAB_SKEW;
             const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tb->x;
-            const float Bw = bound_slope(WM[(x0 + e) >> 2], Rh, gmin, c2e, ive);
+            const float Bw = bound_slope(WM[(ROW_PADL + ws) >> 2], Rh, gmin, c2e, ive);
             const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
             float dl[P], Ms[P], mn[P];
 #pragma unroll
@@ -940,25 +1075,30 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                 mn[q] = pos_inf();
             }
             if (PRUNE) {
-                const float Bp = bound_slope(ZS[(x0 + e + 1) / ZS_STRIDE], Rh, gmin, 2.f * c2e, ive);
+                // the remaining targets: samples from x0 + e + 1 on (forward),
+                // up to x0 + P - 2 - e (backward)
+                const int zi = BWD ? max(x0 + P - 2 - e, 0) / ZS_STRIDE : (x0 + e + 1) / ZS_STRIDE;
+                const float Bp = bound_slope(ZS[zi], Rh, gmin, 2.f * c2e, ive);
                 float m = pos_inf();
 #pragma unroll
                 for (int q = 0; q < P; ++q) m = fminf(m, __fmaf_rn(-2.f, dl[q], CERT_M(q)));
                 if (m >= Bp) { e = dlim; continue; }
             }
-            // the window, relative to R
+            // the window, relative to R (reversed for a backward walk)
             float y[P + U];
             {
                 const float2 nRh = make_float2(-Rh, -Rh);
-                const float* bh = H + x0 + e;
-                const float* bl = Lo + x0 + e;
+                const float* bh = H + ws;
+                const float* bl = Lo + ws;
 #pragma unroll
                 for (int m = 0; m < P + U; m += 4) {
                     const float4 a = *reinterpret_cast<const float4*>(bh + m);
                     const float4 b = *reinterpret_cast<const float4*>(bl + m);
                     const float2 y0 = __fadd2_rn(__fadd2_rn(make_float2(a.x, a.y), nRh), make_float2(b.x, b.y));
                     const float2 y1 = __fadd2_rn(__fadd2_rn(make_float2(a.z, a.w), nRh), make_float2(b.z, b.w));
-                    y[m] = y0.x; y[m + 1] = y0.y; y[m + 2] = y1.x; y[m + 3] = y1.y;
+                    const float v[4] = {y0.x, y0.y, y1.x, y1.y};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) y[BWD ? P + U - 1 - (m + i) : m + i] = v[i];
                 }
             }
             const bool masked = klimited && e + U > dlim;
@@ -992,34 +1132,26 @@ __device__ __forceinline__ void sweep_item(const ItemRow& it, const float* F, co
                                                        lane);
 }
 
-template <bool LONG, bool PRUNE>
-__device__ __forceinline__ void sweep_item_cert(const ItemRow& it, const ExactCtx& xc, const float* ZS,
-                                                const float* WM, const float4* tab, int tabn, int* spill, float eg0,
-                                                FlagList& fl, int lane)
-{
-    sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE>(xc, ZS, WM, tab, tabn, spill, eg0, fl, lane);
-}
 
-// PRUNE: exact horizon pruning; LONG: the launch holds rows with walks of
-// more than LONG_WALK steps (every row then takes the flushing walk); CERT:
-// certified decisions.  Per warp, shared memory holds the staged row (hi
-// parts; CERT: lo parts after them), the suffix maxima (PRUNE), the window
-// maxima and the flagged-POV list (CERT), and the long-walk spill (LONG).
-// Warps per CTA of the certified kernels: their per-lane state (4 POVs'
-// maxima, heights, margins and last-visible bounds, the window relative to
-// the group) takes about 160 registers, which 12 warps still leave every
-// thread.  Rows short enough for CERT_WIDE_WARPS staged rows per CTA (about
-// 1000 samples and fewer) take a second instantiation bounded to 128
-// registers: the extra warps hide more latency than its few spills of the
-// group-restart path cost (measured: 1000^2, 52.3 -> 47.7 ms).  At 2000
-// samples the two staged arrays limit a CTA to 9 warps of shared memory.
+// Warps per CTA of the certified kernels (pairs of warps, below): their
+// per-lane state (4 POVs' maxima, heights, margins and last-visible bounds,
+// the window relative to the group) takes about 160 registers, which 12 warps
+// still leave every thread.  When shared memory holds CERT_WIDE_WARPS warps, a
+// second instantiation bounded to 128 registers runs them: the extra warps
+// hide more latency than the few spills of its group-restart path cost.
 #ifndef TVS_CERT_MAX_WARPS
 #define TVS_CERT_MAX_WARPS 12
 #endif
 constexpr int CERT_MAX_WARPS = TVS_CERT_MAX_WARPS;
 constexpr int CERT_WIDE_WARPS = 16;
+static_assert(CERT_MAX_WARPS % 2 == 0 && CERT_WIDE_WARPS % 2 == 0, "certified warps come in pairs");
 
-template <bool PRUNE, bool LONG, bool CERT, int WARPS>
+// The FP32-decision sweep.  PRUNE: exact horizon pruning; LONG: the launch
+// holds rows with walks of more than LONG_WALK steps (every row then takes
+// the flushing walk).  Per warp, shared memory holds the staged row (reversed
+// for backward items), its suffix maxima (PRUNE) and the long-walk spill
+// (LONG).
+template <bool PRUNE, bool LONG, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
 {
     extern __shared__ __align__(16) float smem[];
@@ -1027,21 +1159,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
     int* istart = reinterpret_cast<int*>(smem + 4 * sp.tab_slots);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     float* Fh = smem + 4 * sp.tab_slots + sp.istart_len + warp * sp.per_warp;
-    float* Fl = Fh + sp.half;
-    float* ZS = Fh + (CERT ? 2 : 1) * sp.half;
-    float* WM = ZS + sp.zs_len;
-    int* flist = reinterpret_cast<int*>(WM + sp.wm_len);
-    int* spill = reinterpret_cast<int*>(WM + sp.wm_len) + sp.fl_cap + lane;
+    float* ZS = Fh + sp.half;
+    int* spill = reinterpret_cast<int*>(ZS + sp.zs_len) + lane;
     // per distance d = m + 1: (1/d, 1/d, 2d + 1, 2d + 1); 1/d correctly rounded
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
         const float r = __frcp_rn((float)(m + 1));
         const float c = (float)(2 * m + 3);
-        tab[CERT ? m + m / TAB_SKEW : m] = make_float4(r, r, c, c);
+        tab[m] = make_float4(r, r, c, c);
     }
     for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
     __syncthreads();
-    FlagList fl{flist, 0};
-    const long long t_start = CERT ? clock64() : 0;
 
     int next = 0;
     if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
@@ -1055,13 +1182,163 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
         next = __shfl_sync(0xffffffffu, next, 0);
         if (!nonempty) continue;
         __syncwarp();
-        const float zmax = stage_row<CERT>(sp, it, Fh, Fl, lane);
+        stage_row<false>(sp, it, Fh, nullptr, nullptr, lane);
+        __syncwarp();   // the staged row is visible to every lane
+        if (PRUNE) {
+            suffix_max(Fh, ZS, it.L, lane);
+            __syncwarp();
+        }
+        int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
+        sweep_item<LONG, PRUNE>(it, Fh, ZS, tab, sp.inv_len, cvrow, spill, lane);
+    }
+}
+
+// The certified sweep with one row per warp, for launches whose rows leave
+// room for CERT_WIDE_WARPS of them: a backward item's row is staged reversed
+// and walked forward, like the FP32 sweep's.  Per warp, shared memory holds
+// [Fh half][Fl half][suffix maxima][window maxima][flag list][spill][ends 4].
+template <bool PRUNE, bool LONG, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams sp)
+{
+    extern __shared__ __align__(16) float smem[];
+    float4* tab = reinterpret_cast<float4*>(smem);
+    int* istart = reinterpret_cast<int*>(smem + 4 * sp.tab_slots);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    float* Fh = smem + 4 * sp.tab_slots + sp.istart_len + warp * sp.per_warp;
+    float* Fl = Fh + sp.half;
+    float* ZS = Fl + sp.half;
+    float* WM = ZS + sp.zs_len;
+    int* flist = reinterpret_cast<int*>(WM + sp.wm_len);
+    int* spill = flist + sp.fl_cap + lane;
+    float* ends = Fh + sp.per_warp - 4;
+    for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
+        const float r = __frcp_rn((float)(m + 1));
+        const float c = (float)(2 * m + 3);
+        tab[m + m / TAB_SKEW] = make_float4(r, r, c, c);
+    }
+    for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
+    __syncthreads();
+    FlagList fl{flist, 0, sp.flag_buf, sp.flag_count, sp.flag_cap, 0, 0.f};
+    const long long t_start = clock64();
+
+    int next = 0;
+    if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
+    next = __shfl_sync(0xffffffffu, next, 0);
+    for (;;) {
+        const int item = next;
+        if (item >= sp.total_items) break;
+        ItemRow it;
+        const bool nonempty = decode_item(sp, istart, item, &it);
+        if (lane == 0) next = (int)atomicAdd(sp.counter, 1u);
+        next = __shfl_sync(0xffffffffu, next, 0);
+        if (!nonempty) continue;
+        __syncwarp();
+        const float zmax = stage_row<true>(sp, it, Fh, Fl, ends, lane);
         __syncwarp();   // the staged row is visible to every lane
         if (PRUNE) suffix_max(Fh, ZS, it.L, lane);
-        if (CERT) window_max(Fh + ROW_PADL, WM, it.L, sp.half, sp.wm_len, lane);
-        if (PRUNE || CERT) __syncwarp();
-        int* cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
-        if (CERT) {
+        window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane);
+        __syncwarp();
+        fl.item = item;
+        fl.zmax = zmax;
+        const DirDev* d = sp.dirs + it.dir;
+        ExactCtx xc;
+        xc.H = Fh + ROW_PADL;
+        xc.Lo = Fl + ROW_PADL;
+        xc.L = it.L;
+        xc.K = it.K;
+        xc.h0h = it.h0;
+        xc.h0l = d->h0_lo;
+        xc.eta = 0x1p-42f * (zmax + fabsf(it.h0)) + 0x1p-126f;
+        xc.cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
+        xc.bwd = false;
+        xc.from_dem = false;
+        xc.rev_staged = it.rev;
+        xc.eh0 = ends[0];
+        xc.el0 = ends[1];
+        xc.ehL = ends[2];
+        xc.elL = ends[3];
+        xc.dir = d;
+        xc.job = sp.jobs + d->job;
+        xc.p = it.p;
+        xc.jlo = it.jlo;
+        xc.half = sp.half;
+        xc.zs_len = sp.zs_len;
+        xc.wm_len = sp.wm_len;
+        xc.tab = tab;
+        xc.tabn = sp.inv_len;
+        const float u = 0x1p-24f;
+        const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
+        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false>(xc, ZS, WM, tab, sp.inv_len, spill, eg0, fl, lane);
+    }
+    if (lane == 0) atomicAdd(&g_sweep_stats[3], (unsigned long long)(clock64() - t_start));
+}
+
+// Barrier of the two warps of pair `pair` (named barrier 1 + pair).
+__device__ __forceinline__ void pair_sync(int pair)
+{
+    asm volatile("bar.sync %0, %1;" :: "r"(1 + pair), "r"(64) : "memory");
+}
+
+// The certified sweep with one staged row per pair of warps: warp 2k walks
+// every row of the pair forward and warp 2k + 1 walks the same row backward
+// (items 2p and 2p + 1), so a row's double-float samples, window maxima and
+// end samples are staged once and held once for both directions (half the
+// shared memory per warp of one row per warp, and room for twice the warps
+// at 2000-sample rows).  Both warps stage half of the row and compute half of
+// its window maxima; the forward warp its suffix maxima, the backward warp
+// its prefix maxima (pruning).  Each warp runs one direction's code only.
+// Per pair, shared memory holds [Fh half][Fl half][suffix maxima][prefix
+// maxima][window maxima][ends 4][exchange 4]; per warp the flagged-POV list
+// and the long-walk spill.
+template <bool PRUNE, bool LONG, int WARPS>
+__global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams sp)
+{
+    extern __shared__ __align__(16) float smem[];
+    float4* tab = reinterpret_cast<float4*>(smem);
+    int* istart = reinterpret_cast<int*>(smem + 4 * sp.tab_slots);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int pair = warp >> 1, bwd = warp & 1;
+    const int npairs = blockDim.x >> 6;
+    float* base = smem + 4 * sp.tab_slots + sp.istart_len;
+    float* Fh = base + pair * sp.per_pair;
+    float* Fl = Fh + sp.half;
+    float* ZS = Fl + sp.half + bwd * sp.zs_len;            // this warp's suffix or prefix maxima
+    float* WM = Fl + sp.half + 2 * sp.zs_len;
+    float* ends = WM + sp.wm_len;                            // 4 floats
+    float* xch = ends + 4;                                   // item number and the halves' zmax
+    float* own = base + npairs * sp.per_pair + warp * sp.per_warp;
+    int* flist = reinterpret_cast<int*>(own);
+    int* spill = reinterpret_cast<int*>(own) + sp.fl_cap + lane;
+    for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
+        const float r = __frcp_rn((float)(m + 1));
+        const float c = (float)(2 * m + 3);
+        tab[m + m / TAB_SKEW] = make_float4(r, r, c, c);
+    }
+    for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
+    __syncthreads();
+    FlagList fl{flist, 0, sp.flag_buf, sp.flag_count, sp.flag_cap, 0, 0.f};
+    const long long t_start = clock64();
+
+    for (;;) {
+        if (bwd == 0 && lane == 0) reinterpret_cast<int*>(xch)[0] = (int)atomicAdd(sp.counter, 2u);
+        pair_sync(pair);
+        const int pitem = reinterpret_cast<const int*>(xch)[0];   // items pitem (forward), pitem + 1
+        if (pitem >= sp.total_items) break;
+        ItemRow it;
+        const bool nonempty = decode_item(sp, istart, pitem + bwd, &it);
+        fl.item = pitem + bwd;
+        if (nonempty) {
+            const float zpart = stage_row<true>(sp, it, Fh, Fl, ends, lane, bwd, 2, false);
+            if (lane == 0) xch[1 + bwd] = zpart;
+            pair_sync(pair);   // the staged row is complete
+            if (PRUNE) {
+                if (bwd) prefix_max(Fh, ZS, it.L, lane);
+                else suffix_max(Fh, ZS, it.L, lane);
+            }
+            window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane, bwd, 2);
+            pair_sync(pair);   // the maxima are complete
+            const float zmax = fmaxf(xch[1], xch[2]);
+            fl.zmax = zmax;
             const DirDev* d = sp.dirs + it.dir;
             ExactCtx xc;
             xc.H = Fh + ROW_PADL;
@@ -1071,8 +1348,14 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
             xc.h0h = it.h0;
             xc.h0l = d->h0_lo;
             xc.eta = 0x1p-42f * (zmax + fabsf(it.h0)) + 0x1p-126f;
-            xc.cvrow = cvrow;
-            xc.rev = it.rev;
+            xc.cvrow = (bwd ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
+            xc.bwd = bwd != 0;
+            xc.from_dem = false;
+            xc.rev_staged = false;
+            xc.eh0 = ends[0];
+            xc.el0 = ends[1];
+            xc.ehL = ends[2];
+            xc.elL = ends[3];
             xc.dir = d;
             xc.job = sp.jobs + d->job;
             xc.p = it.p;
@@ -1084,12 +1367,68 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
             xc.tabn = sp.inv_len;
             const float u = 0x1p-24f;
             const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
-            sweep_item_cert<LONG, PRUNE>(it, xc, ZS, WM, tab, sp.inv_len, spill, eg0, fl, lane);
-        } else {
-            sweep_item<LONG, PRUNE>(it, Fh, ZS, tab, sp.inv_len, cvrow, spill, lane);
+            if (bwd)
+                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, true>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
+                                                                         fl, lane);
+            else
+                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
+                                                                          fl, lane);
         }
+        pair_sync(pair);   // both walks are done with the row (and with the exchange slot)
     }
-    if (CERT && lane == 0) atomicAdd(&g_sweep_stats[3], (unsigned long long)(clock64() - t_start));
+    if (lane == 0) atomicAdd(&g_sweep_stats[3], (unsigned long long)(clock64() - t_start));
+}
+
+// The exact pass of a certified launch: every walk the sweep flagged and
+// handed over (an (item, sample, row |elevation| bound) entry of the flag
+// buffer) is walked again exactly (double-float, FP64 past its margin) by one
+// warp, which blends the walk's samples from the DEM as the staging does
+// (the DEM is L2-resident while the sweep runs).  Warps claim one entry at a
+// time; flag_count[0] is the buffer's fill, flag_count[1] the claim counter.
+constexpr int EXACT_WARPS = 16;
+
+__global__ void __launch_bounds__(EXACT_WARPS * 32) exact_kernel(SweepParams sp)
+{
+    const int lane = threadIdx.x & 31;
+    const unsigned n = min(sp.flag_count[0], (unsigned)sp.flag_cap);
+    const long long t_start = clock64();
+    for (;;) {
+        unsigned i = 0u;
+        if (lane == 0) i = atomicAdd(sp.flag_count + 1, 1u);
+        i = __shfl_sync(0xffffffffu, i, 0);
+        if (i >= n) break;
+        const int4 en = sp.flag_buf[i];
+        if (en.x < 0) continue;                 // a slot of a push that did not fit
+        if (!in_range(en.x, sp.total_items, 22)) continue;
+        ItemRow it;
+        if (!decode_item(sp, sp.item_start, en.x, &it)) continue;
+        if (!in_range(en.y, it.L, 23)) continue;
+        const DirDev* d = sp.dirs + it.dir;
+        ExactCtx xc;
+        xc.H = nullptr;
+        xc.Lo = nullptr;
+        xc.L = it.L;
+        xc.K = it.K;
+        xc.h0h = it.h0;
+        xc.h0l = d->h0_lo;
+        xc.eta = 0x1p-42f * (__int_as_float(en.z) + fabsf(it.h0)) + 0x1p-126f;
+        xc.cvrow = (it.rev ? sp.cv_bwd : sp.cv_fwd) + it.rowbase;
+        xc.bwd = it.rev;
+        xc.from_dem = true;
+        xc.rev_staged = false;
+        xc.eh0 = xc.el0 = xc.ehL = xc.elL = 0.f;
+        xc.dir = d;
+        xc.job = sp.jobs + d->job;
+        xc.p = it.p;
+        xc.jlo = it.jlo;
+        xc.half = sp.half;
+        xc.zs_len = 0;
+        xc.wm_len = 0;
+        xc.tab = nullptr;
+        xc.tabn = 0;     // 1/d by __frcp_rn
+        exact_walk(xc, en.y, lane);
+    }
+    if (lane == 0) atomicAdd(&g_sweep_stats[2], (unsigned long long)(clock64() - t_start));
 }
 
 }  // namespace
@@ -1101,8 +1440,8 @@ constexpr int MIN_TABLE = 1024;
 
 cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* d_item_start, int ndir,
                          int total_items, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd, int wmax,
-                         int dmax, int prune, int cert, unsigned* counter, int num_sms, int smem_optin,
-                         int max_warps, cudaStream_t stream)
+                         int dmax, int prune, int cert, unsigned* counter, int4* flag_buf, unsigned* flag_count,
+                         int flag_cap, int num_sms, int smem_optin, int max_warps, cudaStream_t stream)
 {
     if (ndir <= 0 || total_items <= 0) return cudaSuccess;
     constexpr int U = LARGE_UNROLL;
@@ -1110,6 +1449,10 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     sp.dirs = d_dirs; sp.jobs = d_jobs; sp.item_start = d_item_start; sp.rowlo = rowlo;
     sp.rowhi = rowhi; sp.cv_fwd = cv_fwd; sp.cv_bwd = cv_bwd; sp.counter = counter; sp.ndir = ndir;
     sp.total_items = total_items;
+    const bool pass = cert && flag_buf && flag_count && flag_cap > 0;   // flagged walks in a second kernel
+    sp.flag_buf = pass ? flag_buf : nullptr;
+    sp.flag_count = pass ? flag_count : nullptr;
+    sp.flag_cap = pass ? flag_cap : 0;
     // the distance table is read up to d = dmax + U (a walk of at most
     // min(K, W) - 1 steps, rounded up to U); dmax <= wmax
     sp.inv_len = (std::min(dmax, wmax) + 2 * U + 8 + 1) & ~1;
@@ -1118,55 +1461,87 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
     const bool longw = wmax - 2 > LONG_WALK && dmax - 1 > LONG_WALK;
     sp.zs_len = prune ? ((wmax + ZS_STRIDE - 1) / ZS_STRIDE + 4) & ~3 : 0;
-    sp.wm_len = cert ? ((wmax + 3) / 4 + 4) & ~3 : 0;
+    sp.wm_len = cert ? ((ROW_PADL + wmax + 3) / 4 + 4) & ~3 : 0;
     sp.fl_cap = cert ? FLAG_CAP : 0;
-    sp.per_warp = (cert ? 2 : 1) * sp.half + sp.zs_len + sp.wm_len + sp.fl_cap + (longw ? 32 * LARGE_POV : 0);
-    constexpr int CW = CERT_MAX_WARPS, FW = SWEEP_MAX_WARPS;
-    void (*kern)(SweepParams);
-    if (cert)
-        kern = prune ? (longw ? sweep_kernel<true, true, true, CW> : sweep_kernel<true, false, true, CW>)
-                     : (longw ? sweep_kernel<false, true, true, CW> : sweep_kernel<false, false, true, CW>);
-    else
-        kern = prune ? (longw ? sweep_kernel<true, true, false, FW> : sweep_kernel<true, false, false, FW>)
-                     : (longw ? sweep_kernel<false, true, false, FW> : sweep_kernel<false, false, false, FW>);
-    const size_t per_warp = (size_t)sp.per_warp * 4;
+    const int lspill = longw ? 32 * LARGE_POV : 0;
+    // FP32 decisions: one row per warp.  Certified: one row per warp
+    // (reversed for backward walks) when CERT_WIDE_WARPS such warps fit, else
+    // one row per pair of warps (both staged arrays, suffix and prefix maxima,
+    // window maxima, the end samples and an exchange slot), and per warp its
+    // flag list and spill: a row's samples are then held once for both walk
+    // directions.
+    const int single_warp = 2 * sp.half + sp.zs_len + sp.wm_len + sp.fl_cap + 4;
+    const bool single = cert && !longw && (max_warps == 0 || max_warps >= CERT_WIDE_WARPS) &&
+                        (size_t)(4 * sp.tab_slots + sp.istart_len) * 4 +
+                                (size_t)CERT_WIDE_WARPS * single_warp * 4 <= (size_t)smem_optin;
+    const bool pairs = cert && !single;
+    sp.per_pair = pairs ? 2 * sp.half + 2 * sp.zs_len + sp.wm_len + 8 : 0;
+    sp.per_warp = single ? single_warp : pairs ? sp.fl_cap + lspill : sp.half + sp.zs_len + lspill;
+    // shared memory of one unit: a pair of warps or one warp
+    const int uw = pairs ? 2 : 1;
+    const size_t unit = (size_t)(sp.per_pair + uw * sp.per_warp) * 4;
     size_t fixed = (size_t)(4 * sp.tab_slots + sp.istart_len) * 4;
-    if (longw && fixed + (size_t)LONG_MIN_WARPS * per_warp > (size_t)smem_optin) {
+    if (longw && fixed + (size_t)(LONG_MIN_WARPS / uw) * unit > (size_t)smem_optin) {
         // Rows of more than about 10^4 samples: the whole table and several
         // staged rows do not fit together.  Keep LONG_MIN_WARPS warps (or as
         // many as fit) and a table of what is left (at least MIN_TABLE
         // entries); the long-walk sweep computes the entries past its end.
         const size_t base = (size_t)sp.istart_len * 4;
-        int w = LONG_MIN_WARPS;
+        int w = LONG_MIN_WARPS / uw;
         const size_t min_tab = (size_t)tab_slots_for(MIN_TABLE, cert != 0) * 16;
-        while (w > 1 && base + min_tab + (size_t)w * per_warp > (size_t)smem_optin) --w;
-        if (base + 16 * 4 + (size_t)w * per_warp >= (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+        while (w > 1 && base + min_tab + (size_t)w * unit > (size_t)smem_optin) --w;
+        if (base + 16 * 4 + (size_t)w * unit >= (size_t)smem_optin) return cudaErrorInvalidConfiguration;
         // slots that fit, and the most entries whose slots do
-        const size_t room = ((size_t)smem_optin - base - (size_t)w * per_warp) / 16;
+        const size_t room = ((size_t)smem_optin - base - (size_t)w * unit) / 16;
         const size_t fit = cert ? (room - 2) * TAB_SKEW / (TAB_SKEW + 1) : room;
         sp.inv_len = (int)std::min<size_t>((size_t)sp.inv_len, fit) & ~1;
         sp.tab_slots = tab_slots_for(sp.inv_len, cert != 0);
         fixed = (size_t)(4 * sp.tab_slots + sp.istart_len) * 4;
     }
-    if (fixed + per_warp > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
-    // As many resident warps as shared memory and registers allow, in one CTA per SM
-    // (each warp stages its own row; the 1/d table is shared by the CTA).
-    int most = cert ? CERT_MAX_WARPS : SWEEP_MAX_WARPS;
-    const size_t fit = (smem_optin - fixed) / per_warp;
-    if (cert && !longw && fit >= (size_t)CERT_WIDE_WARPS && (max_warps == 0 || max_warps >= CERT_WIDE_WARPS)) {
-        most = CERT_WIDE_WARPS;
-        kern = prune ? sweep_kernel<true, false, true, CERT_WIDE_WARPS> : sweep_kernel<false, false, true, CERT_WIDE_WARPS>;
+    if (fixed + unit > (size_t)smem_optin) return cudaErrorInvalidConfiguration;
+    // As many resident units as shared memory and registers allow, in one CTA
+    // per SM (the 1/d table is shared by the CTA).
+    const size_t fit = (smem_optin - fixed) / unit;
+    constexpr int CW = CERT_MAX_WARPS, WW = CERT_WIDE_WARPS, FW = SWEEP_MAX_WARPS;
+    void (*kern)(SweepParams);
+    int most;
+    if (single) {
+        most = WW;
+        kern = prune ? sweep_cert_kernel<true, false, WW> : sweep_cert_kernel<false, false, WW>;
+    } else if (pairs) {
+        const bool wide = !longw && fit * 2 >= (size_t)WW && (max_warps == 0 || max_warps >= WW);
+        most = wide ? WW : CW;
+        if (wide) kern = prune ? sweep_pair_kernel<true, false, WW> : sweep_pair_kernel<false, false, WW>;
+        else kern = prune ? (longw ? sweep_pair_kernel<true, true, CW> : sweep_pair_kernel<true, false, CW>)
+                          : (longw ? sweep_pair_kernel<false, true, CW> : sweep_pair_kernel<false, false, CW>);
+    } else {
+        most = FW;
+        kern = prune ? (longw ? sweep_kernel<true, true, FW> : sweep_kernel<true, false, FW>)
+                     : (longw ? sweep_kernel<false, true, FW> : sweep_kernel<false, false, FW>);
     }
-    const int cap = max_warps > 0 ? std::min(max_warps, most) : most;
-    int warps = (int)std::min<size_t>(fit, (size_t)cap);
-    const size_t smem = fixed + (size_t)warps * per_warp;
+    const int cap = max_warps > 0 ? std::max(std::min(max_warps, most), uw) : most;
+    const int units = (int)std::min<size_t>(fit, (size_t)(cap / uw));
+    const int warps = units * uw;
+    const size_t smem = fixed + (size_t)units * unit;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     int per_sm = 0;
     err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, warps * 32, smem);
     if (err != cudaSuccess) return err;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    if (pass) {
+        err = cudaMemsetAsync(flag_count, 0, 2 * sizeof(unsigned), stream);
+        if (err != cudaSuccess) return err;
+    }
     kern<<<per_sm * num_sms, warps * 32, smem, stream>>>(sp);
+    err = cudaGetLastError();
+    if (err != cudaSuccess || !pass) return err;
+    // the exact pass: no shared memory, as many warps as registers allow
+    int xper = 0;
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&xper, exact_kernel, EXACT_WARPS * 32, 0);
+    if (err != cudaSuccess) return err;
+    if (xper < 1) return cudaErrorInvalidConfiguration;
+    exact_kernel<<<xper * num_sms, EXACT_WARPS * 32, 0, stream>>>(sp);
     return cudaGetLastError();
 }
 
