@@ -1144,6 +1144,11 @@ __device__ __forceinline__ void sweep_item(const ItemRow& it, const float* F, co
 #endif
 constexpr int CERT_MAX_WARPS = TVS_CERT_MAX_WARPS;
 constexpr int CERT_WIDE_WARPS = 16;
+// The fewest warps the one-row-per-warp certified kernel runs with; longer
+// rows go to warp pairs.
+#ifndef TVS_CERT_SINGLE_MIN
+#define TVS_CERT_SINGLE_MIN 12
+#endif
 static_assert(CERT_MAX_WARPS % 2 == 0 && CERT_WIDE_WARPS % 2 == 0, "certified warps come in pairs");
 
 // The FP32-decision sweep.  PRUNE: exact horizon pruning; LONG: the launch
@@ -1194,8 +1199,9 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
 }
 
 // The certified sweep with one row per warp, for launches whose rows leave
-// room for CERT_WIDE_WARPS of them: a backward item's row is staged reversed
-// and walked forward, like the FP32 sweep's.  Per warp, shared memory holds
+// room for at least TVS_CERT_SINGLE_MIN of them (16 warps when they fit, else
+// 12): a backward item's row is staged reversed and walked forward, like the
+// FP32 sweep's.  Per warp, shared memory holds
 // [Fh half][Fl half][suffix maxima][window maxima][flag list][spill][ends 4].
 template <bool PRUNE, bool LONG, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams sp)
@@ -1465,15 +1471,17 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     sp.fl_cap = cert ? FLAG_CAP : 0;
     const int lspill = longw ? 32 * LARGE_POV : 0;
     // FP32 decisions: one row per warp.  Certified: one row per warp
-    // (reversed for backward walks) when CERT_WIDE_WARPS such warps fit, else
+    // (reversed for backward walks) when TVS_CERT_SINGLE_MIN such warps fit, else
     // one row per pair of warps (both staged arrays, suffix and prefix maxima,
     // window maxima, the end samples and an exchange slot), and per warp its
     // flag list and spill: a row's samples are then held once for both walk
     // directions.
     const int single_warp = 2 * sp.half + sp.zs_len + sp.wm_len + sp.fl_cap + 4;
-    const bool single = cert && !longw && (max_warps == 0 || max_warps >= CERT_WIDE_WARPS) &&
-                        (size_t)(4 * sp.tab_slots + sp.istart_len) * 4 +
-                                (size_t)CERT_WIDE_WARPS * single_warp * 4 <= (size_t)smem_optin;
+    const size_t single_fit = ((size_t)smem_optin - (size_t)(4 * sp.tab_slots + sp.istart_len) * 4) /
+                              ((size_t)single_warp * 4);
+    const int single_min = TVS_CERT_SINGLE_MIN;
+    const bool single = cert && !longw && (max_warps == 0 || max_warps >= single_min) &&
+                        single_fit >= (size_t)single_min;
     const bool pairs = cert && !single;
     sp.per_pair = pairs ? 2 * sp.half + 2 * sp.zs_len + sp.wm_len + 8 : 0;
     sp.per_warp = single ? single_warp : pairs ? sp.fl_cap + lspill : sp.half + sp.zs_len + lspill;
@@ -1506,8 +1514,10 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     void (*kern)(SweepParams);
     int most;
     if (single) {
-        most = WW;
-        kern = prune ? sweep_cert_kernel<true, false, WW> : sweep_cert_kernel<false, false, WW>;
+        const bool wide = single_fit >= (size_t)WW && (max_warps == 0 || max_warps >= WW);
+        most = wide ? WW : CW;
+        if (wide) kern = prune ? sweep_cert_kernel<true, false, WW> : sweep_cert_kernel<false, false, WW>;
+        else kern = prune ? sweep_cert_kernel<true, false, CW> : sweep_cert_kernel<false, false, CW>;
     } else if (pairs) {
         const bool wide = !longw && fit * 2 >= (size_t)WW && (max_warps == 0 || max_warps >= WW);
         most = wide ? WW : CW;
