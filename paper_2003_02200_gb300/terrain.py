@@ -58,6 +58,10 @@ WORKLOADS = {
     # profiling size: the 2000^2 recipe at a quarter of the cells (a few GB of scratch)
     "tvs1000": dict(rows=1000, cols=1000, hurst=0.8, relief=1500.0, step=10.0, h0=1.5, n=180,
                     max_range=0.0, spike_frac=0.0, seed=SEED_BASE + 5),
+    # profiling size with the 2000^2 rows: the tvs2000 DEM with 24 of its directions' spacing
+    # (the same row lengths and kernels, under 1 GB of scratch)
+    "tvs2000n24": dict(rows=2000, cols=2000, hurst=0.8, relief=1500.0, step=10.0, h0=1.5, n=24,
+                       max_range=0.0, spike_frac=0.0, seed=SEED_BASE + 1),
 }
 
 
