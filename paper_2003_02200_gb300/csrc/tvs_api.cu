@@ -546,7 +546,7 @@ int tvs_batch_create(tvs_handle h, const tvs_job* jobs, int njobs, size_t hbm_bu
     if (fixed >= budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
     tvs_batch* b = new tvs_batch();
     b->h = h;
-    rc = plan_batch(specs, budget - fixed, h->num_sms, h->tuning, &b->plan);
+    rc = plan_batch(specs, budget - fixed, h->num_sms, h->tuning, &b->plan, -1, h->smem_optin);
     if (rc) { delete b; return rc; }
     b->L = make_layout(b->plan, false, mf);
     cudaError_t e = cudaMalloc(&b->ws, b->L.total);

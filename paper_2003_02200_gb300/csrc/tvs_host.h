@@ -142,7 +142,7 @@ size_t part_bound(int num_sms);
 // chunks whose scratch fits `avail` bytes.  only_k >= 0 keeps only direction
 // only_k of a single job (test hook).
 int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, const Tuning& tn, BatchPlan* plan,
-               int only_k = -1);
+               int only_k = -1, int smem_optin = 0);
 
 // Scratch layout of a planned batch (byte offsets from the scratch base).  The
 // header (directions, jobs, chunk-job entries, item tables) is one contiguous

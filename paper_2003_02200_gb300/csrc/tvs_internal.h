@@ -135,6 +135,12 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
                          int total_items, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd, int wmax,
                          int dmax, int prune, int cert, unsigned* counter, int4* flag_buf, unsigned* flag_count,
                          int flag_cap, int num_sms, int smem_optin, int max_warps, cudaStream_t stream);
+// Layout class of a certified sweep launch (rows up to wmax samples, walks
+// up to dmax steps, ndir directions): the warps of its one-row-per-warp
+// kernel (16 or 12), or 0 when its rows go to warp pairs.  Chunks of a batch
+// are cut where the class changes, so that short rows do not run in a launch
+// sized for long ones.
+int cert_sweep_class(int wmax, int dmax, int prune, int ndir, int smem_optin);
 // Entries of a launch's flagged-walk buffer (16 bytes each), at most.
 constexpr int FLAG_BUF_ENTRIES = 1 << 24;
 constexpr int FLAG_ENTRY_BYTES = 16;

@@ -262,15 +262,26 @@ size_t part_bound(int num_sms) { return align256((size_t)(8 * num_sms + 8) * UNS
 // allows, so a job's FP32 group sums (and, the totals being exact, its result)
 // do not depend on the chunking.
 int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, const Tuning& tn, BatchPlan* plan,
-               int only_k)
+               int only_k, int smem_optin)
 {
     plan->jobs = jobs;
     const int njobs = (int)jobs.size();
     std::vector<int> kend(njobs);
+    // instances are planned largest DEM first (stable), so that a chunk holds
+    // DEMs of similar row lengths; the results do not depend on the order
+    std::vector<int> order(njobs);
+    for (int j = 0; j < njobs; ++j) order[j] = j;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return std::max(jobs[a].rows, jobs[a].cols) > std::max(jobs[b].rows, jobs[b].cols);
+    });
     for (int j = 0; j < njobs; ++j) {
         const JobSpec& J = jobs[j];
         kend[j] = J.k1 < 0 ? J.n : J.k1;
         if (J.k0 < 0 || kend[j] > J.n || J.k0 > kend[j]) return fail(TVS_ERR_ARG, "direction range out of bounds");
+    }
+    for (int oj = 0; oj < njobs; ++oj) {
+        const int j = order[oj];
+        const JobSpec& J = jobs[j];
         for (int k = J.k0; k < kend[j]; ++k) {
             if (only_k >= 0 && k != only_k) continue;
             HostDir d;
@@ -301,11 +312,19 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
             t = u;
         }
     }
+    // a certified launch is sized for its longest rows: a chunk also ends
+    // where the next DEM's rows take another layout class of the sweep
+    auto job_class = [&](int j) {
+        if (smem_optin <= 0 || tn.fp32_decisions) return 0;
+        const int w = std::max(jobs[j].rows, jobs[j].cols);
+        return cert_sweep_class(w, w, tn.prune, 64, smem_optin);
+    };
     int i = 0;
     while (i < ninst) {
         size_t slab = 0, slab_ok = 0;
         long long nrows = 0, rows_ok = 0, items = 0;
         int ii = i, last_ok = -1;
+        const int cls = job_class(plan->inst_job[i]);
         while (ii < ninst) {
             const HostDir& d = plan->hdirs[ii];
             const size_t wp = (size_t)((d.W + 3) & ~3);
@@ -313,7 +332,8 @@ int plan_batch(const std::vector<JobSpec>& jobs, size_t avail, int num_sms, cons
             const long long r2 = nrows + d.R;
             const long long it2 = items + 2LL * d.R;
             if (ii > i && (chunk_bytes(s2, r2, ii - i + 1) > avail || ii - i >= kMaxChunkDirs ||
-                           it2 > kMaxChunkItems))
+                           it2 > kMaxChunkItems ||
+                           (plan->inst_job[ii] != plan->inst_job[ii - 1] && job_class(plan->inst_job[ii]) != cls)))
                 break;
             slab = s2;
             nrows = r2;
@@ -633,7 +653,7 @@ int run_batch(tvs_ctx* h, const std::vector<JobSpec>& jobs, cudaStream_t s, bool
     const size_t fixed = fixed_bytes(jobs, host_io, h->num_sms, mf);
     if (fixed >= h->budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
     BatchPlan plan;
-    int rc = plan_batch(jobs, h->budget - fixed, h->num_sms, h->tuning, &plan);
+    int rc = plan_batch(jobs, h->budget - fixed, h->num_sms, h->tuning, &plan, -1, h->smem_optin);
     if (rc) return rc;
     const Layout L = make_layout(plan, host_io, mf);
     rc = ensure_scratch(h, L.total);

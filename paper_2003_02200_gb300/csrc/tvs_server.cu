@@ -300,7 +300,7 @@ int enqueue_step(tvs_server* S, Lane& lane, const std::vector<Slice>& slices)
     }
     BatchPlan plan;
     const size_t fixed = lane_fixed_bytes(S->num_sms, lane.bytes);
-    int rc = plan_batch(jobs, lane.bytes - fixed, S->num_sms, S->tuning, &plan);
+    int rc = plan_batch(jobs, lane.bytes - fixed, S->num_sms, S->tuning, &plan, -1, S->smem_optin);
     if (rc) return rc;
     const Layout L = make_layout(plan, false, lane_flags(lane.bytes));
     if (L.total > lane.bytes) return fail(TVS_ERR_OOM, "step does not fit its lane");

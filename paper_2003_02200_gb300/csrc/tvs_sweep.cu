@@ -1444,6 +1444,30 @@ __global__ void __launch_bounds__(EXACT_WARPS * 32) exact_kernel(SweepParams sp)
 constexpr int LONG_MIN_WARPS = 2;
 constexpr int MIN_TABLE = 1024;
 
+// Certified one-row-per-warp sweep warps that shared memory holds for rows
+// of up to wmax samples and walks of up to dmax steps in a launch of ndir
+// directions (launch_sweep runs that kernel when the count reaches
+// TVS_CERT_SINGLE_MIN).
+static size_t cert_single_fit(int wmax, int dmax, int prune, int ndir, int smem_optin)
+{
+    const int inv_len = (std::min(dmax, wmax) + 2 * LARGE_UNROLL + 8 + 1) & ~1;
+    const int tab_slots = tab_slots_for(inv_len, true);
+    const int istart_len = (ndir + 1 + 3) & ~3;
+    const int half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
+    const int zs_len = prune ? ((wmax + ZS_STRIDE - 1) / ZS_STRIDE + 4) & ~3 : 0;
+    const int wm_len = ((ROW_PADL + wmax + 3) / 4 + 4) & ~3;
+    const int single_warp = 2 * half + zs_len + wm_len + FLAG_CAP + 4;
+    const size_t fixed = (size_t)(4 * tab_slots + istart_len) * 4;
+    return fixed >= (size_t)smem_optin ? 0 : ((size_t)smem_optin - fixed) / ((size_t)single_warp * 4);
+}
+
+int cert_sweep_class(int wmax, int dmax, int prune, int ndir, int smem_optin)
+{
+    if (wmax - 2 > LONG_WALK && dmax - 1 > LONG_WALK) return 0;
+    const size_t fit = cert_single_fit(wmax, dmax, prune, ndir, smem_optin);
+    return fit >= (size_t)CERT_WIDE_WARPS ? CERT_WIDE_WARPS : fit >= (size_t)TVS_CERT_SINGLE_MIN ? CERT_MAX_WARPS : 0;
+}
+
 cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* d_item_start, int ndir,
                          int total_items, const int* rowlo, const int* rowhi, int* cv_fwd, int* cv_bwd, int wmax,
                          int dmax, int prune, int cert, unsigned* counter, int4* flag_buf, unsigned* flag_count,
@@ -1477,8 +1501,7 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     // flag list and spill: a row's samples are then held once for both walk
     // directions.
     const int single_warp = 2 * sp.half + sp.zs_len + sp.wm_len + sp.fl_cap + 4;
-    const size_t single_fit = ((size_t)smem_optin - (size_t)(4 * sp.tab_slots + sp.istart_len) * 4) /
-                              ((size_t)single_warp * 4);
+    const size_t single_fit = cert ? cert_single_fit(wmax, dmax, prune, ndir, smem_optin) : 0;
     const int single_min = TVS_CERT_SINGLE_MIN;
     const bool single = cert && !longw && (max_warps == 0 || max_warps >= single_min) &&
                         single_fit >= (size_t)single_min;
