@@ -392,7 +392,7 @@ __device__ __noinline__ int walk_df(const LineRef& L, float hh, float hl, float 
     int sum = 0, n = 0, lastvis = 0;
     bool esc = false;
     for (int c = 0;; c += WALK_CHUNK) {
-        float th[WALK_TPL], tl[WALK_TPL];
+        float th[WALK_TPL], tl[WALK_TPL], iv[WALK_TPL];
         int firstbad = WALK_TPL;
         const int d0 = c + WALK_TPL * lane + 1;
 #pragma unroll
@@ -402,13 +402,14 @@ __device__ __noinline__ int walk_df(const LineRef& L, float hh, float hl, float 
             int j;
             const bool ok = line_target(L, d0 + m, &a, &fr, &j);
             th[m] = NEG; tl[m] = 0.f;
+            iv[m] = __frcp_rn((float)(d0 + m));
             if (ok) {
                 const float va = view_at(L.dem, L.cols, L.d, a, j);
                 const float vb = fr ? view_at(L.dem, L.cols, L.d, a + 1, j) : va;
                 float zh, zl;
                 df::df_blend(va, vb, fr, zh, zl);
                 zmax = fmaxf(zmax, fmaxf(fabsf(va), fabsf(vb)));
-                df::df_slope(zh, zl, hh, hl, d0 + m, th[m], tl[m]);
+                df::df_slope_iv(zh, zl, hh, hl, d0 + m, iv[m], th[m], tl[m]);
             }
             if (!ok && firstbad == WALK_TPL) firstbad = m;
         }
@@ -437,6 +438,7 @@ __device__ __noinline__ int walk_df(const LineRef& L, float hh, float hl, float 
         float cl = __shfl_up_sync(FULL, pl, 1);
         int cd = __shfl_up_sync(FULL, pd, 1);
         if (lane == 0 || df::df_gt(rh, rl, ch, cl)) { ch = rh; cl = rl; cd = rd; }
+        float icd = __frcp_rn((float)cd);
         unsigned vbits = 0u;
 #pragma unroll
         for (int m = 0; m < WALK_TPL; ++m) {
@@ -447,13 +449,12 @@ __device__ __noinline__ int walk_df(const LineRef& L, float hh, float hl, float 
                     float s, e;
                     df::two_sum(th[m], -ch, s, e);
                     const float dh = __fadd_rn(s, __fadd_rn(e, __fsub_rn(tl[m], cl)));
-                    const float marg = __fmaf_rn(0x1p-40f, fabsf(th[m]) + fabsf(ch),
-                                                 4.04f * eta * (__frcp_rn((float)dd) + __frcp_rn((float)cd))) +
+                    const float marg = __fmaf_rn(0x1p-40f, fabsf(th[m]) + fabsf(ch), 4.04f * eta * (iv[m] + icd)) +
                                        0x1p-120f;
                     if (!(fabsf(dh) > marg)) esc = true;
                     vis = dh > 0.f;
                 }
-                if (df::df_gt(th[m], tl[m], ch, cl)) { ch = th[m]; cl = tl[m]; cd = dd; }
+                if (df::df_gt(th[m], tl[m], ch, cl)) { ch = th[m]; cl = tl[m]; cd = dd; icd = iv[m]; }
                 if (vis) { sum += 2 * dd + 1; vbits |= 1u << m; }
                 if (flags && dd < cap) flags[dd] = vis ? 1 : 0;
             }
