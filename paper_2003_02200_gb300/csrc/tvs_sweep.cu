@@ -524,6 +524,29 @@ __host__ __device__ constexpr int tab_slots_for(int entries, bool skew)
 {
     return skew ? ((entries + entries / TAB_SKEW + 1 + 1) & ~1) : entries;
 }
+// Far from the POV one margin serves several window blocks: from step
+// CERT_NEAR on a margin block is 2 window blocks long, from CERT_FAR on 4 and
+// from CERT_FAR2 on 8 (while the group's walks have that many steps left), so
+// that the finish vote, the margins and the last-rise update are taken once
+// per 32, 64 or 128 steps.  Near the POV, where the margin's 1/(e+1) terms
+// fall fastest, every window block takes its own.
+#ifndef TVS_CERT_NEAR
+#define TVS_CERT_NEAR 64
+#endif
+#ifndef TVS_CERT_FAR
+#define TVS_CERT_FAR 256
+#endif
+#ifndef TVS_CERT_FAR2
+#define TVS_CERT_FAR2 (1 << 30)
+#endif
+#ifndef TVS_CERT_PACKADD
+#define TVS_CERT_PACKADD 1
+#endif
+constexpr int CERT_NEAR = TVS_CERT_NEAR;
+constexpr int CERT_FAR = TVS_CERT_FAR;
+constexpr int CERT_FAR2 = TVS_CERT_FAR2;
+// window maxima WM[k], WM[k + 8], WM[k + 16], WM[k + 24] cover 136 samples
+static_assert(CERT_POV + 8 * CERT_UNROLL - 1 <= WM_SPAN + 96, "a margin window is covered by four window maxima");
 // Entries of a warp's flagged-POV list (at least 32 lanes x LARGE_POV).
 constexpr int FLAG_CAP = 256;
 // Targets per lane per chunk of an exact walk.
@@ -862,10 +885,14 @@ __device__ __forceinline__ float min_abs2(float a, float b, float c)
 
 // U certified steps of one lane's P POVs (see the derivation above), two
 // steps at a time.  y[m] is the window's target x0 + e + m relative to R,
-// g[q] the POV's height relative to R.  mn[q] keeps the smallest |s| of the
-// POV's steps: the block's margin test (mn < delta) runs once at its end.
-template <int P, int U, bool MASKED, bool FAR>
-__device__ __forceinline__ void cert_block(const float* y, const float4* __restrict__ tab, int e, const float* g,
+// ng2 the POVs' heights relative to R, negated, in pairs (q, q + 1).  mn[q]
+// keeps the smallest |s| of the POV's steps: the block's margin test (mn <
+// delta) runs once at its end.  With PACK the differences of a pair of POVs
+// go through one packed add wherever their two targets form an aligned pair
+// of the window (y[2j], y[2j + 1]: every other step); y - g and y + (-g)
+// round alike.
+template <int P, int U, bool MASKED, bool FAR, bool PACK>
+__device__ __forceinline__ void cert_block(const float* y, const float4* __restrict__ tab, int e, const float2* ng2,
                                            float2* M2, float2* acc2, float* mn, int nvalid)
 {
     static_assert(U % 2 == 0, "steps go in pairs");
@@ -881,7 +908,10 @@ __device__ __forceinline__ void cert_block(const float* y, const float4* __restr
             if (MASKED && w >= nvalid) cp = make_float2(0.f, 0.f);
 #pragma unroll
             for (int q = 0; q < P; q += 2) {
-                const float2 d = make_float2(__fsub_rn(y[q + w + 1], g[q]), __fsub_rn(y[q + w + 2], g[q + 1]));
+                const float2 d = (PACK && (q + w + 1) % 2 == 0)
+                                     ? __fadd2_rn(make_float2(y[q + w + 1], y[q + w + 2]), ng2[q / 2])
+                                     : make_float2(__fadd_rn(y[q + w + 1], ng2[q / 2].x),
+                                                   __fadd_rn(y[q + w + 2], ng2[q / 2].y));
                 const float2 x = __fmul2_rn(d, iv);
                 const float2 sp = __ffma2_rn(make_float2(-1.f, -1.f), M2[q / 2], x);
                 const float2 v = make_float2(sat_pos(sp.x), sat_pos(sp.y));
@@ -941,9 +971,14 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
     const int L = xc.L, K = xc.K;
     const int G = (L + P - 1) / P;
     const int klim = K - 1;
-    float g[P], ia[P];
+    // a backward block's window is stored reversed, so its aligned register
+    // pairs hold (y[2j + 1], y[2j]) and only forward walks pack the differences
+    constexpr bool PACK = !BWD && TVS_CERT_PACKADD;
+    float ia[P];
+    float2 ng2[P / 2];               // -g of POV pairs
     float2 M2[P / 2], acc2[P / 2];   // running maxima of POV pairs (packed x - M)
 #define CERT_M(q) ((q) % 2 ? M2[(q) / 2].y : M2[(q) / 2].x)
+#define CERT_NG(q) ((q) % 2 ? ng2[(q) / 2].y : ng2[(q) / 2].x)
     float Rh = 0.f, gmin = 0.f, c2e = 0.f;
     unsigned mask = 0u;
     int gi = lane, next = 32;
@@ -1000,7 +1035,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                 gq = __fadd_rn(__fadd_rn(__fsub_rn(zh, Rh), zl), xc.h0h);
                 gmin = fminf(gmin, gq);
             }
-            g[q] = gq;
+            CERT_NG(q) = -gq;
             gmax = fmaxf(gmax, fabsf(gq));
         }
         c2e = CERT_ABS * __fmaf_rn(5.1f * 0x1p-24f, gmax, eg0);
@@ -1012,7 +1047,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             const int x = pov_x(q);
             const int t = BWD ? x - 1 : x + 1;
             const float y1 = __fadd_rn(__fsub_rn(H[t], Rh), Lo[t]);
-            const float x1 = __fsub_rn(y1, g[q]);
+            const float x1 = __fadd_rn(y1, CERT_NG(q));
             const float C = __fmaf_rn(0x1p-6f, fabsf(x1), __fmaf_rn(4.f, c2e, 0x1p-16f));
             // a POV with no target that adds area starts at +inf: nothing is
             // visible to it, no step is inside its margin, and it never holds
@@ -1059,13 +1094,24 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                     acc2[q / 2] = make_float2(0.f, 0.f);
                 }
             }
-            // margins of this block.  The bounds are formed branch-free: a
-            // window or suffix of sentinels only (-inf) gives 0.
-            const int ws = BWD ? x0 - e - U : x0 + e;       // the window's first sample
-            const bool far = LONG && e + U > tabn;
+            // margins of this margin block (nh window blocks of U steps).  The
+            // bounds are formed branch-free: a window or suffix of sentinels
+            // only (-inf) gives 0.  A margin block of several window blocks
+            // lies wholly before the group's last needed step (e + nh U <=
+            // dlim), so none of its window blocks is masked and every window
+            // and table entry it reads lies in the ranges start() checked.
+            const int nh = (LONG || e < CERT_NEAR) ? 1
+                         : (e >= CERT_FAR2 && e + 8 * U <= dlim) ? 8
+                         : (e >= CERT_FAR && e + 4 * U <= dlim) ? 4
+                         : (e + 2 * U <= dlim) ? 2 : 1;
+            const int ws = BWD ? x0 - e - nh * U : x0 + e;  // the margin block's first window sample
             const float4* __restrict__ tb = tab + e + e / TAB_SKEW;
             const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tb->x;
-            const float Bw = bound_slope(WM[(ROW_PADL + ws) >> 2], Rh, gmin, c2e, ive);
+            const int wk = (ROW_PADL + ws) >> 2;
+            float wz = WM[wk];
+            if (nh >= 4) wz = fmaxf(wz, WM[wk + 8]);
+            if (nh >= 8) wz = fmaxf(wz, fmaxf(WM[wk + 16], WM[wk + 24]));
+            const float Bw = bound_slope(wz, Rh, gmin, c2e, ive);
             const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
             float dl[P], Ms[P], mn[P];
 #pragma unroll
@@ -1084,40 +1130,48 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                 for (int q = 0; q < P; ++q) m = fminf(m, __fmaf_rn(-2.f, dl[q], CERT_M(q)));
                 if (m >= Bp) { e = dlim; continue; }
             }
-            // the window, relative to R (reversed for a backward walk)
-            float y[P + U];
-            {
-                const float2 nRh = make_float2(-Rh, -Rh);
-                const float* bh = H + ws;
-                const float* bl = Lo + ws;
+#pragma unroll 1
+            for (int h = 0; h < nh; ++h) {
+                const int eh = e + h * U;                    // this window block's first step
+                const int wsh = BWD ? x0 - eh - U : x0 + eh; // its window's first sample
+                const bool far = LONG && eh + U > tabn;
+                const float4* __restrict__ tbh = tab + eh + eh / TAB_SKEW;
+                // the window, relative to R (reversed for a backward walk)
+                float y[P + U];
+                {
+                    const float2 nRh = make_float2(-Rh, -Rh);
+                    const float* bh = H + wsh;
+                    const float* bl = Lo + wsh;
 #pragma unroll
-                for (int m = 0; m < P + U; m += 4) {
-                    const float4 a = *reinterpret_cast<const float4*>(bh + m);
-                    const float4 b = *reinterpret_cast<const float4*>(bl + m);
-                    const float2 y0 = __fadd2_rn(__fadd2_rn(make_float2(a.x, a.y), nRh), make_float2(b.x, b.y));
-                    const float2 y1 = __fadd2_rn(__fadd2_rn(make_float2(a.z, a.w), nRh), make_float2(b.z, b.w));
-                    const float v[4] = {y0.x, y0.y, y1.x, y1.y};
+                    for (int m = 0; m < P + U; m += 4) {
+                        const float4 a = *reinterpret_cast<const float4*>(bh + m);
+                        const float4 b = *reinterpret_cast<const float4*>(bl + m);
+                        const float2 y0 = __fadd2_rn(__fadd2_rn(make_float2(a.x, a.y), nRh), make_float2(b.x, b.y));
+                        const float2 y1 = __fadd2_rn(__fadd2_rn(make_float2(a.z, a.w), nRh), make_float2(b.z, b.w));
+                        const float v[4] = {y0.x, y0.y, y1.x, y1.y};
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) y[BWD ? P + U - 1 - (m + i) : m + i] = v[i];
+                        for (int i = 0; i < 4; ++i) y[BWD ? P + U - 1 - (m + i) : m + i] = v[i];
+                    }
                 }
-            }
-            const bool masked = klimited && e + U > dlim;
-            if (masked) {
-                if (far) cert_block<P, U, true, true>(y, tab, e, g, M2, acc2, mn, dlim - e);
-                else cert_block<P, U, true, false>(y, tb, e, g, M2, acc2, mn, dlim - e);
-            } else {
-                if (far) cert_block<P, U, false, true>(y, tab, e, g, M2, acc2, mn, U);
-                else cert_block<P, U, false, false>(y, tb, e, g, M2, acc2, mn, U);
+                const bool masked = klimited && eh + U > dlim;
+                if (masked) {
+                    if (far) cert_block<P, U, true, true, PACK>(y, tab, eh, ng2, M2, acc2, mn, dlim - eh);
+                    else cert_block<P, U, true, false, PACK>(y, tbh, eh, ng2, M2, acc2, mn, dlim - eh);
+                } else {
+                    if (far) cert_block<P, U, false, true, PACK>(y, tab, eh, ng2, M2, acc2, mn, U);
+                    else cert_block<P, U, false, false, PACK>(y, tbh, eh, ng2, M2, acc2, mn, U);
+                }
             }
 #pragma unroll
             for (int q = 0; q < P; ++q) mask |= mn[q] < dl[q] ? 1u << q : 0u;
 #pragma unroll
             for (int q = 0; q < P; ++q) ia[q] = CERT_M(q) > Ms[q] ? ive : ia[q];
-            e += U;
+            e += nh * U;
         }
     }
     if (fl.count > 0) drain_flags(fl, xc, lane);
 #undef CERT_M
+#undef CERT_NG
 }
 
 template <bool LONG, bool PRUNE>
@@ -1143,7 +1197,10 @@ __device__ __forceinline__ void sweep_item(const ItemRow& it, const float* F, co
 #define TVS_CERT_MAX_WARPS 12
 #endif
 constexpr int CERT_MAX_WARPS = TVS_CERT_MAX_WARPS;
-constexpr int CERT_WIDE_WARPS = 16;
+#ifndef TVS_CERT_WIDE_WARPS
+#define TVS_CERT_WIDE_WARPS 16
+#endif
+constexpr int CERT_WIDE_WARPS = TVS_CERT_WIDE_WARPS;
 // The fewest warps the one-row-per-warp certified kernel runs with; longer
 // rows go to warp pairs.
 #ifndef TVS_CERT_SINGLE_MIN
