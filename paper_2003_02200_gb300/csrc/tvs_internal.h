@@ -19,8 +19,10 @@ constexpr int LARGE_UNROLL = 28;
 #define TVS_SWEEP_MAX_WARPS 16
 #endif
 constexpr int SWEEP_MAX_WARPS = TVS_SWEEP_MAX_WARPS;
-// Left pad of a staged row (floats); a multiple of 4.
-constexpr int ROW_PADL = 16;
+// Left pad of a staged row (floats); a multiple of 4, at most 32 (one lane
+// per pad sample fills it), and at least a certified block's step count (a
+// backward block's window starts that many samples before its group).
+constexpr int ROW_PADL = 32;
 // Right pad: the last window of a block reads up to P + U floats past a target.
 constexpr int ROW_PADR = LARGE_POV + 2 * LARGE_UNROLL + 8;
 // Directions whose FP32 partial sums are added once into the FP64 total.

@@ -483,13 +483,13 @@ __device__ __forceinline__ void prefix_max(const float* __restrict__ F, float* _
 // (|theta| <= |x| (1 + 5.1u) + Eg / d, |x_t| <= |M| + |x_t - M|).  Per block
 // and POV the kernel takes
 //   delta = CERT_REL * Mb + CERT_ABS * Eg' * (1/(e+1) + ia) + CERT_FLOOR,
-// with Mb >= |M| over the whole block (|M| at its start, or the block
-// window's largest possible slope Bw when M can rise that far), 1/(e+1) >=
-// 1/d_t, ia >= 1/d_a (1/(e'+1) of the last block e' in which M rose; 1 at
-// first), Eg' >= Eg from the group's largest |g_q|.  Induction over the
-// targets then makes every unflagged decision the exact one.  A POV with a
-// step inside its margin is flagged: its fast-path measure is discarded and
-// it is walked again exactly.
+// with Mb >= |M| over the whole block (the test runs after the block's
+// steps, and M only rises within it, so Mb = max(|M| at its start, |M| at
+// its end)), 1/(e+1) >= 1/d_t, ia >= 1/d_a (1/(e'+1) of the last block e' in
+// which M rose; 1 at first), Eg' >= Eg from the group's largest |g_q|.
+// Induction over the targets then makes every unflagged decision the exact
+// one.  A POV with a step inside its margin is flagged: its fast-path
+// measure is discarded and it is walked again exactly.
 constexpr float CERT_REL = 10.2f * 0x1p-24f * 1.01f;
 constexpr float CERT_ABS = 1.03f * 1.01f;
 constexpr float CERT_FLOOR = 0x1p-99f;
@@ -512,6 +512,7 @@ constexpr int CERT_UNROLL = TVS_CERT_UNROLL;
 #endif
 constexpr int CERT_POV = TVS_CERT_POV;
 static_assert(CERT_POV + CERT_UNROLL <= WM_SPAN, "window span");
+static_assert(CERT_UNROLL <= ROW_PADL, "a backward block's window starts up to U samples before the row");
 static_assert(FLUSH_STEPS % CERT_UNROLL == 0, "long walks flush on block boundaries");
 // The certified kernels store distance entry m at slot m + m / TAB_SKEW.  A
 // lane reads entries e .. e + U - 1 of its own block start e (a multiple of
@@ -529,7 +530,11 @@ __host__ __device__ constexpr int tab_slots_for(int entries, bool skew)
 // from CERT_FAR2 on 8 (while the group's walks have that many steps left), so
 // that the finish vote, the margins and the last-rise update are taken once
 // per 32, 64 or 128 steps.  Near the POV, where the margin's 1/(e+1) terms
-// fall fastest, every window block takes its own.
+// fall fastest, every window block takes its own.  The lanes of a warp run
+// as many window blocks as the longest of their margin blocks (the others
+// wait), which pays only on long rows: the paired-warp kernel takes these
+// tiers, the one-row-per-warp kernel (shorter rows) one window block per
+// margin.
 #ifndef TVS_CERT_NEAR
 #define TVS_CERT_NEAR 64
 #endif
@@ -545,8 +550,7 @@ __host__ __device__ constexpr int tab_slots_for(int entries, bool skew)
 constexpr int CERT_NEAR = TVS_CERT_NEAR;
 constexpr int CERT_FAR = TVS_CERT_FAR;
 constexpr int CERT_FAR2 = TVS_CERT_FAR2;
-// window maxima WM[k], WM[k + 8], WM[k + 16], WM[k + 24] cover 136 samples
-static_assert(CERT_POV + 8 * CERT_UNROLL - 1 <= WM_SPAN + 96, "a margin window is covered by four window maxima");
+
 // Entries of a warp's flagged-POV list (at least 32 lanes x LARGE_POV).
 constexpr int FLAG_CAP = 256;
 // Targets per lane per chunk of an exact walk.
@@ -956,7 +960,7 @@ __device__ __forceinline__ float bound_slope(float z, float Rh, float gmin, floa
 // w meets the window's element q + w + 1: a backward block's window is
 // loaded from x0 - e - U and stored reversed.  Backward groups are taken
 // from the row's end (the longest walks first).
-template <int P, int U, bool LONG, bool PRUNE, bool BWD>
+template <int P, int U, bool LONG, bool PRUNE, bool BWD, bool TIERS>
 __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* __restrict__ ZS,
                                                const float* __restrict__ WM, const float4* __restrict__ tab,
                                                int tabn, int* __restrict__ spill, float eg0, FlagList& fl, int lane)
@@ -1094,40 +1098,44 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                     acc2[q / 2] = make_float2(0.f, 0.f);
                 }
             }
-            // margins of this margin block (nh window blocks of U steps).  The
-            // bounds are formed branch-free: a window or suffix of sentinels
-            // only (-inf) gives 0.  A margin block of several window blocks
-            // lies wholly before the group's last needed step (e + nh U <=
-            // dlim), so none of its window blocks is masked and every window
-            // and table entry it reads lies in the ranges start() checked.
-            const int nh = (LONG || e < CERT_NEAR) ? 1
+            // a margin block of nh window blocks of U steps.  The bounds are
+            // formed branch-free: a window or suffix of sentinels only (-inf)
+            // gives 0.  A margin block of several window blocks lies wholly
+            // before the group's last needed step (e + nh U <= dlim), so none
+            // of its window blocks is masked and every window and table entry
+            // it reads lies in the ranges start() checked.
+            const int nh = (!TIERS || LONG || e < CERT_NEAR) ? 1
                          : (e >= CERT_FAR2 && e + 8 * U <= dlim) ? 8
                          : (e >= CERT_FAR && e + 4 * U <= dlim) ? 4
                          : (e + 2 * U <= dlim) ? 2 : 1;
-            const int ws = BWD ? x0 - e - nh * U : x0 + e;  // the margin block's first window sample
             const float4* __restrict__ tb = tab + e + e / TAB_SKEW;
             const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tb->x;
-            const int wk = (ROW_PADL + ws) >> 2;
-            float wz = WM[wk];
-            if (nh >= 4) wz = fmaxf(wz, WM[wk + 8]);
-            if (nh >= 8) wz = fmaxf(wz, fmaxf(WM[wk + 16], WM[wk + 24]));
-            const float Bw = bound_slope(wz, Rh, gmin, c2e, ive);
-            const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
-            float dl[P], Ms[P], mn[P];
+            float Ms[P], mn[P];
 #pragma unroll
             for (int q = 0; q < P; ++q) {
                 Ms[q] = CERT_M(q);
-                dl[q] = __fmaf_rn(CERT_REL, fmaxf(fabsf(CERT_M(q)), Bw), __fmaf_rn(c2e, ia[q], ce));
                 mn[q] = pos_inf();
             }
             if (PRUNE) {
-                // the remaining targets: samples from x0 + e + 1 on (forward),
-                // up to x0 + P - 2 - e (backward)
+                // the margins at the block's start, with M bounded over the
+                // block by the window's largest possible slope Bw; the
+                // remaining targets: samples from x0 + e + 1 on (forward), up
+                // to x0 + P - 2 - e (backward)
+                const int ws = BWD ? x0 - e - nh * U : x0 + e;   // the margin block's first window sample
+                // WM[wk + 8j] covers the window's samples 32j .. 32j + WM_SPAN - 1
+                const int wk = (ROW_PADL + ws) >> 2;
+                float wz = WM[wk];
+                for (int j = 1; 32 * j + WM_SPAN - 32 < P + nh * U - 1; ++j) wz = fmaxf(wz, WM[wk + 8 * j]);
+                const float Bw = bound_slope(wz, Rh, gmin, c2e, ive);
+                const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
                 const int zi = BWD ? max(x0 + P - 2 - e, 0) / ZS_STRIDE : (x0 + e + 1) / ZS_STRIDE;
                 const float Bp = bound_slope(ZS[zi], Rh, gmin, 2.f * c2e, ive);
                 float m = pos_inf();
 #pragma unroll
-                for (int q = 0; q < P; ++q) m = fminf(m, __fmaf_rn(-2.f, dl[q], CERT_M(q)));
+                for (int q = 0; q < P; ++q) {
+                    const float dq = __fmaf_rn(CERT_REL, fmaxf(fabsf(CERT_M(q)), Bw), __fmaf_rn(c2e, ia[q], ce));
+                    m = fminf(m, __fmaf_rn(-2.f, dq, CERT_M(q)));
+                }
                 if (m >= Bp) { e = dlim; continue; }
             }
 #pragma unroll 1
@@ -1162,8 +1170,16 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                     else cert_block<P, U, false, false, PACK>(y, tbh, eh, ng2, M2, acc2, mn, U);
                 }
             }
+            // the margin test, once the block's last M is known: M only rises
+            // within the block, so max(|M| at its start, |M| at its end)
+            // bounds |M| at every one of its steps
+            const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
 #pragma unroll
-            for (int q = 0; q < P; ++q) mask |= mn[q] < dl[q] ? 1u << q : 0u;
+            for (int q = 0; q < P; ++q) {
+                const float dq =
+                    __fmaf_rn(CERT_REL, fmaxf(fabsf(Ms[q]), fabsf(CERT_M(q))), __fmaf_rn(c2e, ia[q], ce));
+                mask |= mn[q] < dq ? 1u << q : 0u;
+            }
 #pragma unroll
             for (int q = 0; q < P; ++q) ia[q] = CERT_M(q) > Ms[q] ? ive : ia[q];
             e += nh * U;
@@ -1298,8 +1314,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams s
         __syncwarp();
         const float zmax = stage_row<true>(sp, it, Fh, Fl, ends, lane);
         __syncwarp();   // the staged row is visible to every lane
-        if (PRUNE) suffix_max(Fh, ZS, it.L, lane);
-        window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane);
+        if (PRUNE) {   // the window maxima bound a block's slopes for the pruning test only
+            suffix_max(Fh, ZS, it.L, lane);
+            window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane);
+        }
         __syncwarp();
         fl.item = item;
         fl.zmax = zmax;
@@ -1331,7 +1349,8 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams s
         xc.tabn = sp.inv_len;
         const float u = 0x1p-24f;
         const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
-        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false>(xc, ZS, WM, tab, sp.inv_len, spill, eg0, fl, lane);
+        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false, false>(xc, ZS, WM, tab, sp.inv_len, spill, eg0, fl,
+                                                                         lane);
     }
     if (lane == 0) atomicAdd(&g_sweep_stats[3], (unsigned long long)(clock64() - t_start));
 }
@@ -1394,12 +1413,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams s
             const float zpart = stage_row<true>(sp, it, Fh, Fl, ends, lane, bwd, 2, false);
             if (lane == 0) xch[1 + bwd] = zpart;
             pair_sync(pair);   // the staged row is complete
-            if (PRUNE) {
+            if (PRUNE) {   // the window maxima bound a block's slopes for the pruning test only
                 if (bwd) prefix_max(Fh, ZS, it.L, lane);
                 else suffix_max(Fh, ZS, it.L, lane);
+                window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane, bwd, 2);
+                pair_sync(pair);   // the maxima are complete
             }
-            window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane, bwd, 2);
-            pair_sync(pair);   // the maxima are complete
             const float zmax = fmaxf(xch[1], xch[2]);
             fl.zmax = zmax;
             const DirDev* d = sp.dirs + it.dir;
@@ -1431,10 +1450,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams s
             const float u = 0x1p-24f;
             const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
             if (bwd)
-                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, true>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
+                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, true, true>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
                                                                          fl, lane);
             else
-                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
+                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false, true>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
                                                                           fl, lane);
         }
         pair_sync(pair);   // both walks are done with the row (and with the exchange slot)
