@@ -81,7 +81,6 @@ struct SweepParams {
     int half;          // floats of one staged row array (multiple of 4)
     int per_pair;      // floats of a warp pair's shared area (certified)
     int zs_len;        // floats of the row's suffix maxima (0 without pruning)
-    int wm_len;        // floats of the row's window maxima (certified only)
     int fl_cap;        // entries of the flagged-POV list (certified only)
     int per_warp;      // floats of a warp's shared area
 };
@@ -493,11 +492,6 @@ __device__ __forceinline__ void prefix_max(const float* __restrict__ F, float* _
 constexpr float CERT_REL = 10.2f * 0x1p-24f * 1.01f;
 constexpr float CERT_ABS = 1.03f * 1.01f;
 constexpr float CERT_FLOOR = 0x1p-99f;
-// Window maxima WM[k] = max Fh over [4k, 4k + WM_SPAN): a block window starts
-// at a multiple of 4 and reaches at most P + U - 1 <= WM_SPAN - 1 samples on.
-constexpr int WM_SPAN = 40;
-static_assert(LARGE_POV + LARGE_UNROLL <= WM_SPAN && SMALL_POV + SMALL_UNROLL <= WM_SPAN, "window span");
-static_assert(WM_SPAN + 4 <= ROW_PADR, "window maxima read into the right pad");
 // Group size and steps per unrolled block of every certified walk.  A
 // certified step takes about 40 % more instructions than an FP32 one and its
 // state per POV twice the registers: groups of 4 POVs, and blocks short
@@ -511,7 +505,7 @@ constexpr int CERT_UNROLL = TVS_CERT_UNROLL;
 #define TVS_CERT_POV SMALL_POV
 #endif
 constexpr int CERT_POV = TVS_CERT_POV;
-static_assert(CERT_POV + CERT_UNROLL <= WM_SPAN, "window span");
+static_assert(CERT_POV + CERT_UNROLL <= ROW_PADR, "a forward block's window reads up to P + U samples on");
 static_assert(CERT_UNROLL <= ROW_PADL, "a backward block's window starts up to U samples before the row");
 static_assert(FLUSH_STEPS % CERT_UNROLL == 0, "long walks flush on block boundaries");
 // The certified kernels store distance entry m at slot m + m / TAB_SKEW.  A
@@ -534,7 +528,9 @@ __host__ __device__ constexpr int tab_slots_for(int entries, bool skew)
 // as many window blocks as the longest of their margin blocks (the others
 // wait), which pays only on long rows: the paired-warp kernel takes these
 // tiers, the one-row-per-warp kernel (shorter rows) one window block per
-// margin.
+// margin.  A pruned walk checks its stopping bound once per margin block and
+// most pruned walks are short, so pruned launches keep one window block per
+// margin too.
 #ifndef TVS_CERT_NEAR
 #define TVS_CERT_NEAR 64
 #endif
@@ -565,27 +561,6 @@ __device__ __forceinline__ float sat_pos(float s)
     return v;
 }
 
-// Window maxima of the padded staged row (certified walks): WM[k] = max
-// Fh[4k .. 4k + WM_SPAN) in padded coordinates (sample x at ROW_PADL + x),
-// for k < (ROW_PADL + L + 3) / 4; a block's window of either walk direction
-// starts at a multiple of 4 and spans at most WM_SPAN samples.
-__device__ __forceinline__ void window_max(const float* __restrict__ Fh, float* __restrict__ WM, int L, int half,
-                                           int wm_len, int lane, int part = 0, int parts = 1)
-{
-    const float NEG = neg_inf();
-    const int nk = (ROW_PADL + L + 3) / 4;
-    for (int k = lane + 32 * part; k < nk; k += 32 * parts) {
-        float m = NEG;
-#pragma unroll
-        for (int i = 0; i < WM_SPAN; i += 4) {
-            if (!in_range(4 * k + i + 3, half, 5)) continue;
-            const float4 v = *reinterpret_cast<const float4*>(Fh + 4 * k + i);
-            m = fmaxf(m, fmaxf(fmaxf(v.x, v.y), fmaxf(v.z, v.w)));
-        }
-        if (in_range(k, wm_len, 6)) WM[k] = m;
-    }
-}
-
 // What the exact walks of a row need.
 struct ExactCtx {
     const float* H;      // staged hi parts (index 0 = first sample)
@@ -603,7 +578,7 @@ struct ExactCtx {
     const JobDev* job;
     int p, jlo;
     int half;            // floats of a staged row array (index bound, with ROW_PADL)
-    int zs_len, wm_len;  // entries of the suffix and window maxima
+    int zs_len;          // entries of the suffix maxima
     const float4* tab;   // the distance table (skewed: entry m at m + m / TAB_SKEW)
     int tabn;            // its entries
 };
@@ -962,7 +937,7 @@ __device__ __forceinline__ float bound_slope(float z, float Rh, float gmin, floa
 // from the row's end (the longest walks first).
 template <int P, int U, bool LONG, bool PRUNE, bool BWD, bool TIERS>
 __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* __restrict__ ZS,
-                                               const float* __restrict__ WM, const float4* __restrict__ tab,
+                                               const float4* __restrict__ tab,
                                                int tabn, int* __restrict__ spill, float eg0, FlagList& fl, int lane)
 {
     static_assert(P % 4 == 0 && U % 4 == 0, "window loads must stay 16-byte aligned");
@@ -1016,7 +991,6 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
         const int whi = BWD ? x0 - U : x0 + elast;           // highest window start
         const int zsi = BWD ? (x0 + P - 2) / ZS_STRIDE : (x0 + elast + 1) / ZS_STRIDE;
         if (!in_range(ROW_PADL + wlo, xc.half, 19) || !in_range(ROW_PADL + whi + P + U - 1, xc.half, 19) ||
-            !in_range((ROW_PADL + wlo) >> 2, xc.wm_len, 8) || !in_range((ROW_PADL + whi) >> 2, xc.wm_len, 8) ||
             (PRUNE && !in_range(zsi, xc.zs_len, 9)) ||
             (!(LONG && elast + U > tabn) && !in_range(elast + U - 1, tabn, 11))) {
             dlim = 0;
@@ -1104,7 +1078,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
             // before the group's last needed step (e + nh U <= dlim), so none
             // of its window blocks is masked and every window and table entry
             // it reads lies in the ranges start() checked.
-            const int nh = (!TIERS || LONG || e < CERT_NEAR) ? 1
+            const int nh = (!TIERS || PRUNE || LONG || e < CERT_NEAR) ? 1
                          : (e >= CERT_FAR2 && e + 8 * U <= dlim) ? 8
                          : (e >= CERT_FAR && e + 4 * U <= dlim) ? 4
                          : (e + 2 * U <= dlim) ? 2 : 1;
@@ -1117,23 +1091,17 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                 mn[q] = pos_inf();
             }
             if (PRUNE) {
-                // the margins at the block's start, with M bounded over the
-                // block by the window's largest possible slope Bw; the
-                // remaining targets: samples from x0 + e + 1 on (forward), up
-                // to x0 + P - 2 - e (backward)
-                const int ws = BWD ? x0 - e - nh * U : x0 + e;   // the margin block's first window sample
-                // WM[wk + 8j] covers the window's samples 32j .. 32j + WM_SPAN - 1
-                const int wk = (ROW_PADL + ws) >> 2;
-                float wz = WM[wk];
-                for (int j = 1; 32 * j + WM_SPAN - 32 < P + nh * U - 1; ++j) wz = fmaxf(wz, WM[wk + 8 * j]);
-                const float Bw = bound_slope(wz, Rh, gmin, c2e, ive);
+                // the remaining targets (samples from x0 + e + 1 on forward, up
+                // to x0 + P - 2 - e backward) have exact slopes of at most Bp;
+                // delta with Mb = |M| bounds |M - theta_a| now, so once M - 2
+                // delta >= Bp for every POV none of them rises above theta_a
                 const float ce = __fmaf_rn(c2e, ive, CERT_FLOOR);
                 const int zi = BWD ? max(x0 + P - 2 - e, 0) / ZS_STRIDE : (x0 + e + 1) / ZS_STRIDE;
                 const float Bp = bound_slope(ZS[zi], Rh, gmin, 2.f * c2e, ive);
                 float m = pos_inf();
 #pragma unroll
                 for (int q = 0; q < P; ++q) {
-                    const float dq = __fmaf_rn(CERT_REL, fmaxf(fabsf(CERT_M(q)), Bw), __fmaf_rn(c2e, ia[q], ce));
+                    const float dq = __fmaf_rn(CERT_REL, fabsf(CERT_M(q)), __fmaf_rn(c2e, ia[q], ce));
                     m = fminf(m, __fmaf_rn(-2.f, dq, CERT_M(q)));
                 }
                 if (m >= Bp) { e = dlim; continue; }
@@ -1275,7 +1243,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_kernel(SweepParams sp)
 // room for at least TVS_CERT_SINGLE_MIN of them (16 warps when they fit, else
 // 12): a backward item's row is staged reversed and walked forward, like the
 // FP32 sweep's.  Per warp, shared memory holds
-// [Fh half][Fl half][suffix maxima][window maxima][flag list][spill][ends 4].
+// [Fh half][Fl half][suffix maxima][flag list][spill][ends 4].
 template <bool PRUNE, bool LONG, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams sp)
 {
@@ -1286,8 +1254,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams s
     float* Fh = smem + 4 * sp.tab_slots + sp.istart_len + warp * sp.per_warp;
     float* Fl = Fh + sp.half;
     float* ZS = Fl + sp.half;
-    float* WM = ZS + sp.zs_len;
-    int* flist = reinterpret_cast<int*>(WM + sp.wm_len);
+    int* flist = reinterpret_cast<int*>(ZS + sp.zs_len);
     int* spill = flist + sp.fl_cap + lane;
     float* ends = Fh + sp.per_warp - 4;
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
@@ -1314,10 +1281,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams s
         __syncwarp();
         const float zmax = stage_row<true>(sp, it, Fh, Fl, ends, lane);
         __syncwarp();   // the staged row is visible to every lane
-        if (PRUNE) {   // the window maxima bound a block's slopes for the pruning test only
-            suffix_max(Fh, ZS, it.L, lane);
-            window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane);
-        }
+        if (PRUNE) suffix_max(Fh, ZS, it.L, lane);
         __syncwarp();
         fl.item = item;
         fl.zmax = zmax;
@@ -1344,13 +1308,11 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams s
         xc.jlo = it.jlo;
         xc.half = sp.half;
         xc.zs_len = sp.zs_len;
-        xc.wm_len = sp.wm_len;
         xc.tab = tab;
         xc.tabn = sp.inv_len;
         const float u = 0x1p-24f;
         const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
-        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false, false>(xc, ZS, WM, tab, sp.inv_len, spill, eg0, fl,
-                                                                         lane);
+        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false, false>(xc, ZS, tab, sp.inv_len, spill, eg0, fl, lane);
     }
     if (lane == 0) atomicAdd(&g_sweep_stats[3], (unsigned long long)(clock64() - t_start));
 }
@@ -1363,15 +1325,14 @@ __device__ __forceinline__ void pair_sync(int pair)
 
 // The certified sweep with one staged row per pair of warps: warp 2k walks
 // every row of the pair forward and warp 2k + 1 walks the same row backward
-// (items 2p and 2p + 1), so a row's double-float samples, window maxima and
-// end samples are staged once and held once for both directions (half the
-// shared memory per warp of one row per warp, and room for twice the warps
-// at 2000-sample rows).  Both warps stage half of the row and compute half of
-// its window maxima; the forward warp its suffix maxima, the backward warp
-// its prefix maxima (pruning).  Each warp runs one direction's code only.
-// Per pair, shared memory holds [Fh half][Fl half][suffix maxima][prefix
-// maxima][window maxima][ends 4][exchange 4]; per warp the flagged-POV list
-// and the long-walk spill.
+// (items 2p and 2p + 1), so a row's double-float samples and end samples are
+// staged once and held once for both directions (half the shared memory per
+// warp of one row per warp, and room for twice the warps at 2000-sample
+// rows).  Both warps stage half of the row; the forward warp computes its
+// suffix maxima, the backward warp its prefix maxima (pruning).  Each warp
+// runs one direction's code only.  Per pair, shared memory holds [Fh
+// half][Fl half][suffix maxima][prefix maxima][ends 4][exchange 4]; per warp
+// the flagged-POV list and the long-walk spill.
 template <bool PRUNE, bool LONG, int WARPS>
 __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams sp)
 {
@@ -1385,8 +1346,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams s
     float* Fh = base + pair * sp.per_pair;
     float* Fl = Fh + sp.half;
     float* ZS = Fl + sp.half + bwd * sp.zs_len;            // this warp's suffix or prefix maxima
-    float* WM = Fl + sp.half + 2 * sp.zs_len;
-    float* ends = WM + sp.wm_len;                            // 4 floats
+    float* ends = Fl + sp.half + 2 * sp.zs_len;              // 4 floats
     float* xch = ends + 4;                                   // item number and the halves' zmax
     float* own = base + npairs * sp.per_pair + warp * sp.per_warp;
     int* flist = reinterpret_cast<int*>(own);
@@ -1413,11 +1373,10 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams s
             const float zpart = stage_row<true>(sp, it, Fh, Fl, ends, lane, bwd, 2, false);
             if (lane == 0) xch[1 + bwd] = zpart;
             pair_sync(pair);   // the staged row is complete
-            if (PRUNE) {   // the window maxima bound a block's slopes for the pruning test only
+            if (PRUNE) {   // each warp's own suffix or prefix maxima
                 if (bwd) prefix_max(Fh, ZS, it.L, lane);
                 else suffix_max(Fh, ZS, it.L, lane);
-                window_max(Fh, WM, it.L, sp.half, sp.wm_len, lane, bwd, 2);
-                pair_sync(pair);   // the maxima are complete
+                __syncwarp();
             }
             const float zmax = fmaxf(xch[1], xch[2]);
             fl.zmax = zmax;
@@ -1444,17 +1403,16 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams s
             xc.jlo = it.jlo;
             xc.half = sp.half;
             xc.zs_len = sp.zs_len;
-            xc.wm_len = sp.wm_len;
-            xc.tab = tab;
+                xc.tab = tab;
             xc.tabn = sp.inv_len;
             const float u = 0x1p-24f;
             const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
             if (bwd)
-                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, true, true>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
-                                                                         fl, lane);
+                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, true, true>(xc, ZS, tab, sp.inv_len, spill, eg0, fl,
+                                                                               lane);
             else
-                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false, true>(xc, ZS, WM, tab, sp.inv_len, spill, eg0,
-                                                                          fl, lane);
+                sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false, true>(xc, ZS, tab, sp.inv_len, spill, eg0, fl,
+                                                                                lane);
         }
         pair_sync(pair);   // both walks are done with the row (and with the exchange slot)
     }
@@ -1505,7 +1463,6 @@ __global__ void __launch_bounds__(EXACT_WARPS * 32) exact_kernel(SweepParams sp)
         xc.jlo = it.jlo;
         xc.half = sp.half;
         xc.zs_len = 0;
-        xc.wm_len = 0;
         xc.tab = nullptr;
         xc.tabn = 0;     // 1/d by __frcp_rn
         exact_walk(xc, en.y, lane);
@@ -1531,8 +1488,7 @@ static size_t cert_single_fit(int wmax, int dmax, int prune, int ndir, int smem_
     const int istart_len = (ndir + 1 + 3) & ~3;
     const int half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
     const int zs_len = prune ? ((wmax + ZS_STRIDE - 1) / ZS_STRIDE + 4) & ~3 : 0;
-    const int wm_len = ((ROW_PADL + wmax + 3) / 4 + 4) & ~3;
-    const int single_warp = 2 * half + zs_len + wm_len + FLAG_CAP + 4;
+    const int single_warp = 2 * half + zs_len + FLAG_CAP + 4;
     const size_t fixed = (size_t)(4 * tab_slots + istart_len) * 4;
     return fixed >= (size_t)smem_optin ? 0 : ((size_t)smem_optin - fixed) / ((size_t)single_warp * 4);
 }
@@ -1567,22 +1523,21 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
     sp.half = (ROW_PADL + 4 + wmax + ROW_PADR + 3) & ~3;
     const bool longw = wmax - 2 > LONG_WALK && dmax - 1 > LONG_WALK;
     sp.zs_len = prune ? ((wmax + ZS_STRIDE - 1) / ZS_STRIDE + 4) & ~3 : 0;
-    sp.wm_len = cert ? ((ROW_PADL + wmax + 3) / 4 + 4) & ~3 : 0;
     sp.fl_cap = cert ? FLAG_CAP : 0;
     const int lspill = longw ? 32 * LARGE_POV : 0;
     // FP32 decisions: one row per warp.  Certified: one row per warp
     // (reversed for backward walks) when TVS_CERT_SINGLE_MIN such warps fit, else
     // one row per pair of warps (both staged arrays, suffix and prefix maxima,
-    // window maxima, the end samples and an exchange slot), and per warp its
+    // the end samples and an exchange slot), and per warp its
     // flag list and spill: a row's samples are then held once for both walk
     // directions.
-    const int single_warp = 2 * sp.half + sp.zs_len + sp.wm_len + sp.fl_cap + 4;
+    const int single_warp = 2 * sp.half + sp.zs_len + sp.fl_cap + 4;
     const size_t single_fit = cert ? cert_single_fit(wmax, dmax, prune, ndir, smem_optin) : 0;
     const int single_min = TVS_CERT_SINGLE_MIN;
     const bool single = cert && !longw && (max_warps == 0 || max_warps >= single_min) &&
                         single_fit >= (size_t)single_min;
     const bool pairs = cert && !single;
-    sp.per_pair = pairs ? 2 * sp.half + 2 * sp.zs_len + sp.wm_len + 8 : 0;
+    sp.per_pair = pairs ? 2 * sp.half + 2 * sp.zs_len + 8 : 0;
     sp.per_warp = single ? single_warp : pairs ? sp.fl_cap + lspill : sp.half + sp.zs_len + lspill;
     // shared memory of one unit: a pair of warps or one warp
     const int uw = pairs ? 2 : 1;
