@@ -368,6 +368,41 @@ def test_tvs4000_range_limited_sampled_parity(ctx, orc):
     assert got.max() <= math.pi * w["max_range"] ** 2 * 1.01
 
 
+@pytest.mark.parametrize("rng", [0.0, 7000.0, 2345.0])
+def test_direction_cv_paired_rows_unpruned(orc, rng):
+    """2400-sample rows run the paired-warp kernel (one staged row for a
+    forward and a backward warp); without pruning one margin test there
+    covers 2 or 4 window blocks far from the POV, and the range may end a
+    walk inside such a stretch: every per-sample measure equals the FP64
+    oracle's (the flagged walks re-walked by the sweep's own warps)."""
+    dem = make_dem(3, 2400, "frac", seed=41)
+    with tvs.Context(0) as c:
+        c.set_tuning(prune=0)
+        got = c.debug_direction_cv(dem, 10.0, 1.5, 8, rng, 0)
+    want = oracle_cv_slab(orc, dem, 10.0, 1.5, 8, rng, 0, 64)
+    assert got.shape == want.shape
+    bad = np.argwhere(got != want)
+    assert bad.size == 0, f"{len(bad)} samples differ, first {bad[:5].tolist()}"
+
+
+@pytest.mark.parametrize("prune", [0, 1])
+def test_paired_rows_sampled_parity(orc, prune):
+    """A 300 x 2400 DEM, 16 directions: its 2400-sample rows put the whole
+    launch on the paired-warp kernel, with the launch's flag buffer and the
+    exact pass after it; without pruning (margin tests over several window
+    blocks) and with it, 150 sampled cells against the FP64 oracle."""
+    dem = make_dem(300, 2400, "frac", seed=43)
+    cells = sample_cells(300, 2400, 150, seed=13)
+    o64 = orc.total_viewshed(dem, 10.0, 1.5, 16, 0.0, prec=64, cells=cells)
+    with tvs.Context(0) as c:
+        c.set_tuning(prune=prune)
+        tvs.sweep_stats(clear=True)
+        got = c.total_viewshed(dem, 10.0, 1.5, 16, 0.0).ravel()
+        st = tvs.sweep_stats()
+    assert_certified(got[cells], o64, 10.0)
+    assert st["exact_walks"] > 0   # the exact pass ran
+
+
 @pytest.mark.parametrize("rows,cols,n", [(3, 16384, 8), (16384, 3, 8)])
 def test_longest_rows_sampled_parity(ctx, ctx32, orc, rows, cols, n):
     """Rows of the longest supported length (16384 samples): walks beyond
