@@ -500,24 +500,35 @@ constexpr float CERT_FLOOR = 0x1p-99f;
 #ifndef TVS_CERT_UNROLL
 #define TVS_CERT_UNROLL 16
 #endif
-constexpr int CERT_UNROLL = TVS_CERT_UNROLL;
+// The one-row-per-warp kernel (shorter rows, every walk staged forward)
+// takes longer blocks: its lanes keep one margin per window block, and 24
+// steps spread that block's overhead further (1000^2: 3 % faster); on the
+// paired kernel's 2000-sample rows 24-step blocks were 4 % slower.
+#ifndef TVS_CERT_UNROLL_SINGLE
+#define TVS_CERT_UNROLL_SINGLE 24
+#endif
+constexpr int CERT_UNROLL = TVS_CERT_UNROLL;                 // paired-warp kernel
+constexpr int CERT_UNROLL_SINGLE = TVS_CERT_UNROLL_SINGLE;   // one-row-per-warp kernel
 #ifndef TVS_CERT_POV
 #define TVS_CERT_POV SMALL_POV
 #endif
 constexpr int CERT_POV = TVS_CERT_POV;
-static_assert(CERT_POV + CERT_UNROLL <= ROW_PADR, "a forward block's window reads up to P + U samples on");
+static_assert(CERT_POV + CERT_UNROLL <= ROW_PADR && CERT_POV + CERT_UNROLL_SINGLE <= ROW_PADR,
+              "a forward block's window reads up to P + U samples on");
 static_assert(CERT_UNROLL <= ROW_PADL, "a backward block's window starts up to U samples before the row");
 static_assert(FLUSH_STEPS % CERT_UNROLL == 0, "long walks flush on block boundaries");
-// The certified kernels store distance entry m at slot m + m / TAB_SKEW.  A
-// lane reads entries e .. e + U - 1 of its own block start e (a multiple of
-// U = TAB_SKEW); groups of different lengths leave the lanes of a warp at
+// A certified kernel with U-step blocks stores distance entry m at slot m +
+// m / U.  A lane reads entries e .. e + U - 1 of its own block start e (a
+// multiple of U); groups of different lengths leave the lanes of a warp at
 // different e, and unskewed such reads would fall on a few of the eight
 // 16-byte bank groups.  Skewed, entry u of block k sits in bank group
-// ((U + 1) k + u) mod 8, which spreads blocks k over all eight.
-constexpr int TAB_SKEW = CERT_UNROLL;
+// ((U + 1) k + u) mod 8 (U a multiple of 8), which spreads blocks k over all
+// eight.  Tables are sized for the shorter block, which needs the most slots.
+constexpr int TAB_SKEW_MIN = CERT_UNROLL < CERT_UNROLL_SINGLE ? CERT_UNROLL : CERT_UNROLL_SINGLE;
+static_assert(CERT_UNROLL % 8 == 0 && CERT_UNROLL_SINGLE % 8 == 0, "skewed blocks cover the eight bank groups");
 __host__ __device__ constexpr int tab_slots_for(int entries, bool skew)
 {
-    return skew ? ((entries + entries / TAB_SKEW + 1 + 1) & ~1) : entries;
+    return skew ? ((entries + entries / TAB_SKEW_MIN + 1 + 1) & ~1) : entries;
 }
 // Far from the POV one margin serves several window blocks: from step
 // CERT_NEAR on a margin block is 2 window blocks long, from CERT_FAR on 4 and
@@ -579,15 +590,16 @@ struct ExactCtx {
     int p, jlo;
     int half;            // floats of a staged row array (index bound, with ROW_PADL)
     int zs_len;          // entries of the suffix maxima
-    const float4* tab;   // the distance table (skewed: entry m at m + m / TAB_SKEW)
+    const float4* tab;   // the distance table (skewed: entry m at m + m / tskew)
     int tabn;            // its entries
+    int tskew;           // its skew: the block length of the kernel that built it
 };
 
 // fl(1/d), correctly rounded: from the distance table while it reaches d.
 __device__ __forceinline__ float inv_d(const ExactCtx& c, int d)
 {
     const int m = d - 1;
-    return m < c.tabn ? c.tab[m + m / TAB_SKEW].x : __frcp_rn((float)d);
+    return m < c.tabn ? c.tab[m + m / c.tskew].x : __frcp_rn((float)d);
 }
 
 // Hi and lo parts of sample xs (row order) blended from the DEM, as the
@@ -881,7 +893,7 @@ __device__ __forceinline__ void cert_block(const float* y, const float4* __restr
 #pragma unroll
         for (int k = 0; k < 2; ++k) {
             const int w = u + k;
-            const float4 t4 = FAR ? dist_entry(e + w + 1) : tab[w + w / TAB_SKEW];
+            const float4 t4 = FAR ? dist_entry(e + w + 1) : tab[w + w / U];
             const float2 iv = make_float2(t4.x, t4.y);
             float2 cp = make_float2(t4.z, t4.w);
             if (MASKED && w >= nvalid) cp = make_float2(0.f, 0.f);
@@ -941,7 +953,6 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                                                int tabn, int* __restrict__ spill, float eg0, FlagList& fl, int lane)
 {
     static_assert(P % 4 == 0 && U % 4 == 0, "window loads must stay 16-byte aligned");
-    static_assert(U % TAB_SKEW == 0, "a block's table entries must sit at one skewed offset");
     const unsigned FULL = 0xffffffffu;
     const unsigned below = (1u << lane) - 1u;
     const float NEG = neg_inf();
@@ -1082,7 +1093,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                          : (e >= CERT_FAR2 && e + 8 * U <= dlim) ? 8
                          : (e >= CERT_FAR && e + 4 * U <= dlim) ? 4
                          : (e + 2 * U <= dlim) ? 2 : 1;
-            const float4* __restrict__ tb = tab + e + e / TAB_SKEW;
+            const float4* __restrict__ tb = tab + e + e / U;
             const float ive = (LONG && e >= tabn) ? __frcp_rn((float)(e + 1)) : tb->x;
             float Ms[P], mn[P];
 #pragma unroll
@@ -1111,7 +1122,7 @@ __device__ __forceinline__ void sweep_row_cert(const ExactCtx& xc, const float* 
                 const int eh = e + h * U;                    // this window block's first step
                 const int wsh = BWD ? x0 - eh - U : x0 + eh; // its window's first sample
                 const bool far = LONG && eh + U > tabn;
-                const float4* __restrict__ tbh = tab + eh + eh / TAB_SKEW;
+                const float4* __restrict__ tbh = tab + eh + eh / U;
                 // the window, relative to R (reversed for a backward walk)
                 float y[P + U];
                 {
@@ -1260,7 +1271,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams s
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
         const float r = __frcp_rn((float)(m + 1));
         const float c = (float)(2 * m + 3);
-        tab[m + m / TAB_SKEW] = make_float4(r, r, c, c);
+        tab[m + m / CERT_UNROLL_SINGLE] = make_float4(r, r, c, c);
     }
     for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
     __syncthreads();
@@ -1309,10 +1320,12 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_cert_kernel(SweepParams s
         xc.half = sp.half;
         xc.zs_len = sp.zs_len;
         xc.tab = tab;
+        xc.tskew = CERT_UNROLL_SINGLE;
         xc.tabn = sp.inv_len;
         const float u = 0x1p-24f;
         const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
-        sweep_row_cert<CERT_POV, CERT_UNROLL, LONG, PRUNE, false, false>(xc, ZS, tab, sp.inv_len, spill, eg0, fl, lane);
+        sweep_row_cert<CERT_POV, CERT_UNROLL_SINGLE, LONG, PRUNE, false, false>(xc, ZS, tab, sp.inv_len, spill, eg0,
+                                                                                fl, lane);
     }
     if (lane == 0) atomicAdd(&g_sweep_stats[3], (unsigned long long)(clock64() - t_start));
 }
@@ -1354,7 +1367,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams s
     for (int m = threadIdx.x; m < sp.inv_len; m += blockDim.x) {
         const float r = __frcp_rn((float)(m + 1));
         const float c = (float)(2 * m + 3);
-        tab[m + m / TAB_SKEW] = make_float4(r, r, c, c);
+        tab[m + m / CERT_UNROLL] = make_float4(r, r, c, c);
     }
     for (int m = threadIdx.x; m <= sp.ndir; m += blockDim.x) istart[m] = sp.item_start[m];
     __syncthreads();
@@ -1404,6 +1417,7 @@ __global__ void __launch_bounds__(WARPS * 32, 1) sweep_pair_kernel(SweepParams s
             xc.half = sp.half;
             xc.zs_len = sp.zs_len;
                 xc.tab = tab;
+                xc.tskew = CERT_UNROLL;
             xc.tabn = sp.inv_len;
             const float u = 0x1p-24f;
             const float eg0 = 2.01f * u * fabsf(it.h0) + fabsf(d->h0_lo) * 1.0001f + 4.04f * xc.eta;
@@ -1465,6 +1479,7 @@ __global__ void __launch_bounds__(EXACT_WARPS * 32) exact_kernel(SweepParams sp)
         xc.zs_len = 0;
         xc.tab = nullptr;
         xc.tabn = 0;     // 1/d by __frcp_rn
+        xc.tskew = 1;
         exact_walk(xc, en.y, lane);
     }
     if (lane == 0) atomicAdd(&g_sweep_stats[2], (unsigned long long)(clock64() - t_start));
@@ -1555,7 +1570,7 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
         if (base + 16 * 4 + (size_t)w * unit >= (size_t)smem_optin) return cudaErrorInvalidConfiguration;
         // slots that fit, and the most entries whose slots do
         const size_t room = ((size_t)smem_optin - base - (size_t)w * unit) / 16;
-        const size_t fit = cert ? (room - 2) * TAB_SKEW / (TAB_SKEW + 1) : room;
+        const size_t fit = cert ? (room - 2) * TAB_SKEW_MIN / (TAB_SKEW_MIN + 1) : room;
         sp.inv_len = (int)std::min<size_t>((size_t)sp.inv_len, fit) & ~1;
         sp.tab_slots = tab_slots_for(sp.inv_len, cert != 0);
         fixed = (size_t)(4 * sp.tab_slots + sp.istart_len) * 4;
