@@ -922,7 +922,7 @@ __device__ __forceinline__ void cert_block(const float* y, const float4* __restr
 }
 
 // Upper bound of the slopes a POV of the group can meet among targets whose
-// hi heights are at most z (a window or suffix maximum): max(0, z + slack -
+// hi heights are at most z (a suffix or prefix maximum): max(0, z + slack -
 // Rh - gmin) / (e + 1), with slack covering the hi / lo split, the rounding of
 // the differences and of g (2^-20 relative, plus eg).  z = -inf (sentinels
 // only) gives 0.
