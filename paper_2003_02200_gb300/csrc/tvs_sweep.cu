@@ -1588,9 +1588,12 @@ cudaError_t launch_sweep(const DirDev* d_dirs, const JobDev* d_jobs, const int* 
         if (wide) kern = prune ? sweep_cert_kernel<true, false, WW> : sweep_cert_kernel<false, false, WW>;
         else kern = prune ? sweep_cert_kernel<true, false, CW> : sweep_cert_kernel<false, false, CW>;
     } else if (pairs) {
-        const bool wide = !longw && fit * 2 >= (size_t)WW && (max_warps == 0 || max_warps >= WW);
+        // pruned walks are short and restart groups often: the 12-warp
+        // instantiation (no spills) beats 16 warps there (2000^2: 210.9
+        // against 218.4 ms), while unpruned walks favour 16 (351 against 365)
+        const bool wide = !longw && !prune && fit * 2 >= (size_t)WW && (max_warps == 0 || max_warps >= WW);
         most = wide ? WW : CW;
-        if (wide) kern = prune ? sweep_pair_kernel<true, false, WW> : sweep_pair_kernel<false, false, WW>;
+        if (wide) kern = sweep_pair_kernel<false, false, WW>;
         else kern = prune ? (longw ? sweep_pair_kernel<true, true, CW> : sweep_pair_kernel<true, false, CW>)
                           : (longw ? sweep_pair_kernel<false, true, CW> : sweep_pair_kernel<false, false, CW>);
     } else {
