@@ -201,7 +201,9 @@ void tvs_batch_destroy(tvs_batch_handle b);
  *   4-POV step costs p4_cost_pct percent of an 8-POV step per POV (default
  *   107; 1 << 20 keeps every such row on 8; 0 in tvs_set_tuning = default);
  * sweep_max_warps: warps per sweep CTA, 0 = as many as shared memory allows,
- *   at most 16 (default 0);
+ *   at most 16 (default 0; certified launches whose rows need one staged row
+ *   per pair of warps take at most 12 when pruning, where the 12-warp build
+ *   runs without register spills and was measured faster);
  * unskew_ctas_per_sm: a chunk whose DEMs have fewer cell tiles than this many
  *   per SM splits its directions into ranges across CTAs (1 to 4, default 2);
  * prune: exact horizon pruning in the sweep (1, default) or none (0): a group
