@@ -248,6 +248,25 @@ int tvs_direction(int n_sectors, int k, int rows, int cols, double step_m, doubl
  * min(L_fwd, K) + min(L_bwd, K).  Host only; returns a negative code on bad args. */
 int64_t tvs_count_evals(int rows, int cols, int n_sectors, double step_m, double max_range_m);
 
+/* Host-only test hook of the batch planner (no GPU): plans njobs whole jobs
+ * -- job j a rows[j] x cols[j] DEM with n_sectors[j] directions, step_m[j]
+ * and max_range_m[j] (the observer height does not change a plan) -- the way
+ * tvs_total_viewshed_batch does on the device path under a scratch budget of
+ * budget_bytes on a GPU of num_sms SMs with smem_optin bytes of opt-in shared
+ * memory per CTA (0: the planner ignores the sweep's shared-memory layouts),
+ * with exact pruning `prune` (0/1) and FP32 decisions `fp32_decisions` (0/1).
+ * Writes, for every planned (job, direction) instance in launch order, its
+ * job inst_job[i], its direction inst_k[i] and its chunk inst_chunk[i]
+ * (chunks are launched in order, each one pass of the pipeline), and the
+ * counts *ninst and *nchunks.  The three arrays are the caller's, of
+ * inst_cap entries, at least the jobs' total number of directions.  Errors:
+ * TVS_ERR_ARG (NULL pointers, bad job arguments, inst_cap too small),
+ * TVS_ERR_OOM (a direction does not fit the budget). */
+int tvs_debug_plan(const int32_t* rows, const int32_t* cols, const int32_t* n_sectors, const double* step_m,
+                   const double* max_range_m, int njobs, uint64_t budget_bytes, int num_sms, int smem_optin,
+                   int prune, int fp32_decisions, int32_t* inst_job, int32_t* inst_k, int32_t* inst_chunk,
+                   int inst_cap, int32_t* ninst, int32_t* nchunks);
+
 /* Row map of direction k computed by the device kernel that the sweep uses,
  * copied to host arrays: dest[j], frac[j] for j < W (integer row shift and
  * 32-bit fraction of j*t), jlo[p], jhi[p] for p < R (usable columns of skewed

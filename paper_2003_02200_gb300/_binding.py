@@ -130,6 +130,8 @@ def load(build_if_missing: bool = True) -> C.CDLL:
             "tvs_count_evals": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double], C.c_int64),
             "tvs_count_point_evals": ([C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, vp, C.c_int, C.c_int],
                                       C.c_int64),
+            "tvs_debug_plan": ([vp, vp, vp, vp, vp, C.c_int, C.c_uint64, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp,
+                                vp, C.c_int, i32p, i32p], C.c_int),
             "tvs_debug_rowmap": ([vp, C.c_int, C.c_int, C.c_int, C.c_int, vp, vp, vp, vp, i32p], C.c_int),
             "tvs_debug_direction_cv": ([vp, vp, C.c_int, C.c_int, C.c_double, C.c_double, C.c_int,
                                         C.c_double, C.c_int, vp, i32p, i32p], C.c_int),
@@ -201,6 +203,28 @@ def count_evals(rows: int, cols: int, n_sectors: int, step_m: float = 1.0, max_r
     if E < 0:
         _check(int(E))
     return int(E)
+
+
+def debug_plan(jobs, budget_bytes: int, num_sms: int = 152, smem_optin: int = 0, prune: int = 1,
+               fp32_decisions: int = 0):
+    """tvs_debug_plan: the batch planner run on the host (no GPU) for jobs
+    given as (rows, cols, n_sectors, step_m, max_range_m) tuples; returns
+    the job, direction and chunk of every planned instance in launch order."""
+    J = list(jobs)
+    rows = np.array([j[0] for j in J], np.int32)
+    cols = np.array([j[1] for j in J], np.int32)
+    nsec = np.array([j[2] for j in J], np.int32)
+    step = np.array([j[3] for j in J], np.float64)
+    rng = np.array([j[4] for j in J], np.float64)
+    cap = int(nsec.sum())
+    ij, ik, ic = (np.zeros(max(cap, 1), np.int32) for _ in range(3))
+    ninst, nchunks = C.c_int32(0), C.c_int32(0)
+    _check(load().tvs_debug_plan(rows.ctypes.data, cols.ctypes.data, nsec.ctypes.data, step.ctypes.data,
+                                 rng.ctypes.data, len(J), int(budget_bytes), num_sms, smem_optin, prune,
+                                 fp32_decisions, ij.ctypes.data, ik.ctypes.data, ic.ctypes.data, cap,
+                                 C.byref(ninst), C.byref(nchunks)))
+    n = ninst.value
+    return ij[:n].copy(), ik[:n].copy(), ic[:n].copy()
 
 
 def count_point_evals(rows: int, cols: int, n_sectors: int, povs, step_m: float = 1.0, max_range_m: float = 0.0,

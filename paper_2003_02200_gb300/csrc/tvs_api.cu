@@ -164,6 +164,46 @@ int tvs_debug_rowmap(tvs_handle h, int rows, int cols, int n_sectors, int k, int
     return TVS_OK;
 }
 
+int tvs_debug_plan(const int32_t* rows, const int32_t* cols, const int32_t* n_sectors, const double* step_m,
+                   const double* max_range_m, int njobs, uint64_t budget_bytes, int num_sms, int smem_optin,
+                   int prune, int fp32_decisions, int32_t* inst_job, int32_t* inst_k, int32_t* inst_chunk,
+                   int inst_cap, int32_t* ninst, int32_t* nchunks)
+{
+    if (!rows || !cols || !n_sectors || !step_m || !max_range_m || !inst_job || !inst_k || !inst_chunk || !ninst ||
+        !nchunks)
+        return fail(TVS_ERR_ARG, "NULL argument");
+    if (njobs <= 0 || num_sms <= 0 || smem_optin < 0) return fail(TVS_ERR_ARG, "njobs and num_sms must be positive");
+    std::vector<JobSpec> jobs;
+    long long total = 0;
+    for (int j = 0; j < njobs; ++j) {
+        const int rc = check_job(rows[j], cols[j], step_m[j], 0.0, n_sectors[j], max_range_m[j]);
+        if (rc) return rc;
+        jobs.push_back(JobSpec{nullptr, nullptr, rows[j], cols[j], n_sectors[j], step_m[j], 0.0, max_range_m[j]});
+        total += n_sectors[j];
+    }
+    if (total > inst_cap) return fail(TVS_ERR_ARG, "inst_cap is below the jobs' total number of directions");
+    Tuning tn;
+    tn.prune = prune != 0;
+    tn.fp32_decisions = fp32_decisions != 0;
+    // the budget split of a batch call (run_batch): fixed parts first, the rest for chunks
+    const size_t budget = (size_t)budget_bytes;
+    const size_t fixed = fixed_bytes(jobs, false, num_sms, budget_flags(budget));
+    if (fixed >= budget) return fail(TVS_ERR_OOM, "the DEMs do not fit the HBM budget");
+    BatchPlan plan;
+    const int rc = plan_batch(jobs, budget - fixed, num_sms, tn, &plan, -1, smem_optin);
+    if (rc) return rc;
+    const int n = (int)plan.inst_job.size();
+    for (int q = 0; q < (int)plan.chunks.size(); ++q)
+        for (int t = plan.chunks[q].i0; t < plan.chunks[q].i1; ++t) {
+            inst_job[t] = plan.inst_job[t];
+            inst_k[t] = plan.inst_k[t];
+            inst_chunk[t] = q;
+        }
+    *ninst = n;
+    *nchunks = (int)plan.chunks.size();
+    return TVS_OK;
+}
+
 int tvs_debug_direction_cv(tvs_handle h, const float* dem, int rows, int cols, double step_m,
                            double obs_height_m, int n_sectors, double max_range_m, int k,
                            int32_t* cv, int32_t* R, int32_t* W)

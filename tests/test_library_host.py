@@ -148,3 +148,77 @@ def test_point_eval_count_matches_brute_walks(orc, rows, cols, n, step, rng):
                         base = i - (y0 >> 32) - v
                         want += sum(_walk_len(i, j0, s, H, W, t_fx, K, base, False) for s in (1, -1))
         assert tvs.count_point_evals(rows, cols, n, povs, step, rng, mode) == want, mode
+
+
+# ------------------------------------------------------ batch planner (host) --
+
+SMEM_OPTIN = 232448   # opt-in shared memory per CTA (227 KiB) the sweep layouts are sized for
+
+
+def job_blocks(ij):
+    """Runs of consecutive instances of one job, as (job, start, end)."""
+    runs, s = [], 0
+    for i in range(1, len(ij) + 1):
+        if i == len(ij) or ij[i] != ij[s]:
+            runs.append((int(ij[s]), s, i))
+            s = i
+    return runs
+
+
+def test_plan_covers_every_direction_once_largest_first():
+    jobs = [(300, 300, 90, 10.0, 0.0), (2000, 2000, 36, 10.0, 0.0), (800, 650, 45, 5.0, 900.0),
+            (500, 2000, 24, 10.0, 0.0), (64, 64, 7, 10.0, 0.0)]
+    ij, ik, ic = tvs._binding.debug_plan(jobs, 16 << 30, 152, SMEM_OPTIN, 1, 0)
+    assert sorted(zip(ij.tolist(), ik.tolist())) == [(j, k) for j, J in enumerate(jobs) for k in range(J[2])]
+    assert ic[0] == 0 and np.all(np.diff(ic) >= 0)
+    runs = job_blocks(ij)
+    assert len(runs) == len(jobs)                       # each job's directions stay together
+    for j, s, e in runs:
+        assert np.array_equal(ik[s:e], np.arange(jobs[j][2]))   # in direction order
+    sides = [max(jobs[j][0], jobs[j][1]) for j, _, _ in runs]
+    assert sides == sorted(sides, reverse=True)          # largest DEM first
+
+
+def test_plan_cuts_chunks_on_direction_groups():
+    """A budget that holds some but not all directions of a 2000 x 2000 job:
+    every chunk but the last ends on a multiple of 8 directions (the FP32
+    group sums, and so the results, do not depend on the budget)."""
+    ij, ik, ic = tvs._binding.debug_plan([(2000, 2000, 180, 10.0, 0.0)], 1 << 30, 152, SMEM_OPTIN, 1, 0)
+    assert ic.max() >= 2
+    starts = np.flatnonzero(np.diff(ic)) + 1
+    assert np.all(ik[starts] % 8 == 0)
+    assert np.array_equal(ik, np.arange(180))
+
+
+def test_plan_separates_sweep_layouts_for_certified_decisions():
+    """Certified launches size their shared memory for their longest rows, so
+    a 2000-sample DEM (a row per pair of warps) and a 300-sample one (a row
+    per warp) take separate chunks; FP32 decisions, or no layout information,
+    let them share one."""
+    jobs = [(300, 300, 180, 10.0, 0.0), (2000, 2000, 180, 10.0, 0.0), (280, 310, 90, 10.0, 0.0)]
+    ij, _, ic = tvs._binding.debug_plan(jobs, 64 << 30, 152, SMEM_OPTIN, 1, 0)
+    for c in np.unique(ic):
+        sides = {max(jobs[j][0], jobs[j][1]) >= 1500 for j in ij[ic == c]}
+        assert len(sides) == 1
+    assert ic.max() == 1
+    for fp32, smem in ((1, SMEM_OPTIN), (0, 0)):
+        _, _, ic2 = tvs._binding.debug_plan(jobs, 64 << 30, 152, smem, 1, fp32)
+        assert ic2.max() == 0
+
+
+def test_plan_errors():
+    with pytest.raises(tvs.TvsError):                    # one direction does not fit
+        tvs._binding.debug_plan([(2000, 2000, 180, 10.0, 0.0)], 64 << 20, 152, SMEM_OPTIN)
+    with pytest.raises(tvs.TvsError):                    # bad job
+        tvs._binding.debug_plan([(1, 2000, 180, 10.0, 0.0)], 1 << 30, 152, SMEM_OPTIN)
+    lib = tvs.load()
+    one = np.array([100], np.int32)
+    n = np.array([16], np.int32)
+    d = np.array([10.0])
+    z = np.array([0.0])
+    out = np.zeros(16, np.int32)
+    cnt = C.c_int32(0)
+    rc = lib.tvs_debug_plan(one.ctypes.data, one.ctypes.data, n.ctypes.data, d.ctypes.data, z.ctypes.data, 1,
+                            1 << 30, 152, 0, 1, 0, out.ctypes.data, out.ctypes.data, out.ctypes.data, 15,
+                            C.byref(cnt), C.byref(cnt))
+    assert rc == tvs._binding.TVS_ERR_ARG               # inst_cap below the number of directions
