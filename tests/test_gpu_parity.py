@@ -7,15 +7,15 @@ target's elevation angle with the running maximum) one of two ways:
   it, which is what the FP64 definition decides.  Every per-sample measure cv
   must equal the FP64 oracle's bit for bit, and every cell's area may differ
   from the FP64 oracle's only by the single-precision blend and sums of the
-  unskew (rtol FP32_RTOL).  The benchmark spec's tolerance (per-POV relative error
-  <= 1e-4 on 99.9 % of POVs and <= 1e-2 on every POV, denominator
-  max(|oracle|, step^2)) is checked beside it;
+  unskew (rtol FP32_RTOL).  The FP64 tolerance of the total viewshed (per-POV
+  relative error <= 1e-4 on 99.9 % of POVs and <= 1e-2 on every POV,
+  denominator max(|oracle|, step^2)) is checked beside it;
 * FP32 decisions (tuning fp32_decisions = 1), as the paper's kernels declare
   heights and slopes (float in Alg. 6-8): cv bit for bit equal to the
   oracle's FP32-decision mode (prec = 32), areas within FP32_RTOL of it.  A
   near-tie between a target's slope and the running maximum decides
   differently in FP32 and FP64; each such flip moves a half-line's measure by
-  2d + 1, so this mode misses the benchmark spec's tolerance on a few percent of
+  2d + 1, so this mode misses that FP64 tolerance on a few percent of
   paper-scale cells (reported, not gated).
 """
 import math
@@ -31,7 +31,7 @@ pytestmark = pytest.mark.gpu
 # FP32 per-direction blend + FP32 sums over groups of 8 directions: each cell's
 # value carries at most ~10 single-precision roundings relative to the FP64 sum.
 FP32_RTOL = 4e-6
-# The benchmark spec's bar against the FP64 oracle.
+# The FP64 tolerance against the FP64 oracle: share of POVs within 1e-4, and the largest error.
 FP64_SHARE_FLOOR = 0.999
 FP64_MAX_REL = 1e-2
 
@@ -67,7 +67,7 @@ def assert_fp64_tolerance(got, want, step, floor=FP64_SHARE_FLOOR):
 
 def assert_certified(got, o64, step):
     """Certified decisions: areas equal the FP64 oracle's up to FP32 sums, and
-    therefore meet the benchmark spec's tolerance."""
+    therefore meet the FP64 tolerance."""
     np.testing.assert_allclose(got, o64, rtol=FP32_RTOL, atol=0)
     assert_fp64_tolerance(got, o64, step)
 
