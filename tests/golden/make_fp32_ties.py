@@ -12,8 +12,8 @@ fraction fr of Alg. 6,
     th = fl(fl(z - h) * fl(1 / d))
 
 and decides "visible" iff th is strictly above the running maximum (Alg. 8),
-a segment closing with d^2 - open^2 (readings 1-4: visible at the start,
-above recomputed per target, the open segment closed at the last target).
+a segment closing with d^2 - open^2 (visible at the start, above
+recomputed per target, the open segment closed at the last target).
 The FP64 reading takes the same steps in double precision with a true
 division, r = fr / 2^32 exactly and h0 unrounded.
 
@@ -71,7 +71,7 @@ def f64(x: Q) -> Q:
 
 
 def t_fx() -> int:
-    # llround(tan(alpha) * 2^32) of the direction table (reading 10)
+    # llround(tan(alpha) * 2^32), as the direction table rounds it
     return int(math.floor(math.tan(math.pi * (2 * K) / (2.0 * N)) * TWO32 + 0.5))
 
 
@@ -239,7 +239,7 @@ def main():
     lines = [
         "# Near-tie lines of sight pinning the oracle's FP32-decision mode (prec=32)",
         "# against exact rational arithmetic; written by make_fp32_ties.py (see its",
-        "# docstring for the operation order, reading 19 of the design notes).",
+        "# docstring for the operation order).",
         f"# Every case: direction k = {K} of n = {N}, DEM {ROWS} x {COLS}, step 1, no range,",
         "# line b = 0; h0 (a double) and the dem rows (float32 values) are in hex;",
         "# cv32 / cv64 are the forward + backward measures of the POVs j = 0 .. 7",

@@ -554,9 +554,9 @@ def _fp32_tie_cases():
 def test_golden_fp32_near_ties(orc):
     """tests/golden/fp32_ties.txt: near-tie lines of sight (direction 1 of 8,
     blended samples) whose measures were derived in exact rational arithmetic
-    from the operation order of the FP32-decision reading (reading 19:
-    (1-r) a + r b, h = z + float(h0), (z - h) * rcp(d), all in single
-    precision) and of the FP64 reading.  The generator kept cases that a
+    from the operation order of the FP32-decision reading ((1-r) a + r b,
+    h = z + float(h0), (z - h) * rcp(d), all in single precision) and of the
+    FP64 reading.  The generator kept cases that a
     division instead of rcp, a fused blend, h0 added unrounded, or the blend
     weight taken from the exact r would each change, so any of those mistakes
     in the oracle's FP32 mode fails here."""
