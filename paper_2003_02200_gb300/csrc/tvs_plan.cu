@@ -615,7 +615,9 @@ int enqueue_chunks(tvs_ctx* h, const BatchPlan& plan, const Layout& L, char* bas
                                    d_part, s),
                      "unskew launch");
         }
-        launched += 3;
+        // row map, sweep, unskew, and the exact pass that a certified sweep
+        // with a flag buffer launches after itself
+        launched += (!tn.fp32_decisions && d_flags && L.flag_cap > 0) ? 4 : 3;
         if (c.max_split > 1) {
             Timer t(h, K_FINAL, s, c.final_bytes);
             TVS_CUDA(launch_unskew_finalize(d_jobs, d_cj + c.cj_beg, c.ncj, c.total_cells, d_part, s),
